@@ -1,0 +1,304 @@
+"""Benchmark: hexagonal cell-updates per second of the explicit finite-volume step on the
+large carved catchment (4096 x 4096 hexagons, edge 5 m, 16.7 M cells, land-cover classes,
+2 h double-peak storm, outlet hydrograph every 10 s), on GB300.
+
+One bench step = one time step of the whole hot path over the raster (edge fluxes, rain,
+implicit friction, state update, CFL reduction, ledger and clock on the device).
+
+Arms:
+  default            the CUDA path through the C ABI (libasx.so)
+  --impl reference   the FP64 CPU oracle on the host cores (a bounded crop per step)
+
+Prints one JSON line.  Under torchrun (N > 1) each rank runs an independent replica of
+the workload ("replicas only"); rank 0 prints the aggregate.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+METRIC = "hex cell-updates/s"
+UNIT = "cell-updates/s"
+BYTES_PER_CELL = 32            # read m, v1, v2, z, theta + write m, v1, v2 (float32)
+T_WARM = 2700.0                # start of the timed window: between the storm peaks [s]
+REF_CROP = 384                 # reference arm: crop side (cells) per oracle step
+
+
+def _peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            d = json.load(f)
+        return float(d["hbm_gbs"]), "measured"
+    except Exception:
+        return 6800.0, "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi clock / throttle samples while the timed region runs."""
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.proc = None
+        self.lines = []
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", f"--id={self.index}", f"--query-gpu={self.Q}",
+                                          "--format=csv,noheader,nounits", "-lms", "100"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except Exception:
+            self.proc = None
+        return self
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def __exit__(self, *a):
+        if self.proc:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except Exception:
+                self.proc.kill()
+
+    def summary(self):
+        sm, mx, reasons = [], None, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            p = [x.strip() for x in ln.split(",")]
+            if len(p) < 9:
+                continue
+            try:
+                sm.append(float(p[1]))
+                mx = float(p[2])
+            except ValueError:
+                continue
+            for nm, v in zip(names, p[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(nm)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"]}
+        return {"sm_mhz": float(np.median(sm)), "sm_max_mhz": mx, "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def _dist():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    return ws, rank
+
+
+def _workload_config(sc, k):
+    return {"workload": f"carved catchment {sc.rows}x{sc.cols} hex, edge {sc.l:g} m, "
+                        f"3 land-cover classes, double-peak storm, window from t={T_WARM:.0f} s",
+            "cells": sc.n, "rows": sc.rows, "cols": sc.cols, "steps_timed": k,
+            "l2": "state 0.74 GB > 129 MB L2 (no flush needed)", "parallelism": "replicas"}
+
+
+def run_cuda(args):
+    import torch
+    ws, rank = _dist()
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    if ws > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    from paper_2406_14933_gb300 import build as pb
+    pb.build()
+    from paper_2406_14933_gb300 import asx as A
+    from paper_2406_14933_gb300 import inputs
+    from paper_2406_14933_gb300.raster import Raster
+
+    sc = inputs.carved_catchment()
+    stream = torch.cuda.current_stream()
+    R = Raster(sc, device=local, stream=stream.cuda_stream)
+    R.run_until(T_WARM)
+    R.step(args.warmup)
+    n = sc.n
+
+    def barrier():
+        torch.cuda.synchronize()
+        if ws > 1:
+            import torch.distributed as dist
+            dist.barrier()
+            torch.cuda.synchronize()
+
+    # device-timed region: K steps with inputs resident in HBM
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    barrier()
+    with ClockSampler(local) as clk:
+        e0.record(stream)
+        R.step(args.steps)
+        e1.record(stream)
+        torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1)
+    barrier()
+    # end to end through the C ABI from pinned host buffers: upload the state, K steps,
+    # download the state and the ledger
+    mh, ml, v1, v2 = R.state()
+    t0c, _, s0 = R.clock()
+    led = R.ledger()
+    host = [torch.from_numpy(a).pin_memory() for a in (mh, ml, v1, v2)]
+    outs = [torch.empty_like(h).pin_memory() for h in host]
+    barrier()
+    w0 = time.perf_counter()
+    A.asx_set_state(R.handle, *[h.data_ptr() for h in host], A.ASX_PTR_HOST, t0c, s0, led)
+    R.step(args.steps)
+    A.asx_get_state(R.handle, *[o.data_ptr() for o in outs], A.ASX_PTR_HOST)
+    led2 = R.ledger()
+    barrier()
+    e2e_s = time.perf_counter() - w0
+    R.close()
+    if ws > 1:
+        import torch.distributed as dist
+        t = torch.tensor([ms, e2e_s], device="cuda", dtype=torch.float64)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms, e2e_s = float(t[0]), float(t[1])
+    if rank != 0:
+        return None
+    ms_step = ms / args.steps
+    value = ws * n * args.steps / (ms / 1e3)
+    peak, peak_kind = _peaks()
+    achieved = BYTES_PER_CELL * n / (ms_step / 1e3) / 1e9
+    traffic = _read_traffic()
+    out = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+        "data": "synthetic (seeded fBm catchment, carved channels, land-cover classes)",
+        "config": _workload_config(sc, args.steps),
+        "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                     "frac": achieved / peak, "traffic": traffic,
+                     "peak_source": f"{peak_kind} copy bandwidth",
+                     "note": "32 B algorithmic per cell-update / (step time incl. launch gap)"},
+        "e2e": {"value": ws * n * args.steps / e2e_s, "unit": UNIT,
+                "h2d_bytes_per_step": 16 * n / args.steps, "d2h_bytes_per_step": 16 * n / args.steps},
+        "gpu_launches": args.steps + 1,
+        "clocks": clk.summary(),
+        "mass_defect_rel": led2.defect_rel,
+    }
+    if not args.no_cpu_baseline:
+        out["cpu_baseline"] = cpu_baseline(sc, budget_s=args.cpu_budget)
+    return out
+
+
+def _read_traffic():
+    """DRAM bytes per step launch from a committed ncu summary, if one matches."""
+    path = os.path.join(ROOT, "profiles", "traffic_per_launch.json")
+    try:
+        with open(path) as f:
+            return float(json.load(f)["bytes_per_launch"])
+    except Exception:
+        return None
+
+
+def _film_state(sc, depth=0.005):
+    h = np.full((sc.rows, sc.cols), depth, np.float32)
+    return h, np.zeros_like(h), np.zeros_like(h)
+
+
+def cpu_baseline(sc, budget_s=15.0, crop=REF_CROP):
+    """The FP64 oracle on a crop of the same raster (a 5 mm film at t = 45 min), timed on
+    this host's cores for about budget_s seconds."""
+    import oracle
+    oracle.build()
+    r0 = (sc.rows - crop) // 2
+    c0 = (sc.cols - crop) // 2
+    sl = (slice(r0, r0 + crop), slice(c0, c0 + crop))
+    cls = sc.cls[sl]
+    p = oracle.Problem(crop, crop, sc.l, sc.z[sl], sc.class_theta[cls], sc.class_alpha_s[cls],
+                       sc.class_alpha_p[cls], bc=(0, 0, 1, 0), g=sc.g, cfl=sc.cfl,
+                       dt_max=sc.dt_max, rain_t=sc.rain_t, rain_r=sc.rain_r)
+    h, v1, v2 = _film_state(sc)
+    m = p.mass(h[sl])
+    a, b = v1[sl].ravel().astype(np.float64), v2[sl].ravel().astype(np.float64)
+    t = T_WARM
+    steps = 0
+    w0 = time.perf_counter()
+    while True:
+        res = p.run(m, a, b, t, 1e9, max_steps=5)
+        m, a, b, t = res["m"], res["v1"], res["v2"], res["t"]
+        steps += 5
+        if time.perf_counter() - w0 > budget_s:
+            break
+    el = time.perf_counter() - w0
+    return {"value": crop * crop * steps / el, "unit": UNIT, "cores": 1, "kind": "oracle",
+            "sample": f"{steps} oracle steps of a {crop}x{crop} crop of the catchment "
+                      f"(5 mm film from t={T_WARM:.0f} s), {el:.1f} s, single thread"}
+
+
+def run_reference(args):
+    ws, rank = _dist()
+    if rank != 0:
+        return None
+    from paper_2406_14933_gb300 import inputs
+    sc = inputs.carved_catchment()
+    import oracle
+    oracle.build()
+    crop = REF_CROP
+    r0, c0 = (sc.rows - crop) // 2, (sc.cols - crop) // 2
+    sl = (slice(r0, r0 + crop), slice(c0, c0 + crop))
+    cls = sc.cls[sl]
+    p = oracle.Problem(crop, crop, sc.l, sc.z[sl], sc.class_theta[cls], sc.class_alpha_s[cls],
+                       sc.class_alpha_p[cls], bc=(0, 0, 1, 0), g=sc.g, cfl=sc.cfl,
+                       dt_max=sc.dt_max, rain_t=sc.rain_t, rain_r=sc.rain_r)
+    h, v1, v2 = _film_state(sc)
+    m = p.mass(h[sl])
+    a, b = v1[sl].ravel().astype(np.float64), v2[sl].ravel().astype(np.float64)
+    t = T_WARM
+    for _ in range(args.warmup):
+        res = p.run(m, a, b, t, 1e9, max_steps=1)
+        m, a, b, t = res["m"], res["v1"], res["v2"], res["t"]
+    w0 = time.perf_counter()
+    for _ in range(args.steps):
+        res = p.run(m, a, b, t, 1e9, max_steps=1)
+        m, a, b, t = res["m"], res["v1"], res["v2"], res["t"]
+    el = time.perf_counter() - w0
+    value = crop * crop * args.steps / el
+    cfg = _workload_config(sc, args.steps)
+    cfg["reference_crop"] = f"{crop}x{crop} cells per step"
+    return {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": el * 1e3 / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic", "config": cfg,
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
+                             "sample": f"{args.steps} oracle steps of a {crop}x{crop} crop "
+                                       f"(5 mm film from t={T_WARM:.0f} s), single thread"},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=2000)
+    ap.add_argument("--warmup", type=int, default=20)
+    ap.add_argument("--impl", default="cuda", choices=["cuda", "reference"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--cpu-budget", type=float, default=15.0)
+    args = ap.parse_args()
+    args.warmup = max(args.warmup, 3)
+    out = run_reference(args) if args.impl == "reference" else run_cuda(args)
+    if out is not None:
+        print(json.dumps(out), flush=True)
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,189 @@
+/*
+ * asx.h -- C ABI of the GB300 (sm_103a) solver for the porosity-extended
+ * Saint-Venant model on a regular hexagonal raster (arxiv 2406.14933, "ASTERIX").
+ *
+ * The library advances the explicit finite-volume scheme of the paper, Sec. 2.2,
+ * Eq. fvm_2D_eq_frac.07, in the fractional form of Appendix A: upwind mass and
+ * momentum fluxes on every hexagon edge (Eqs. fvm_2D_eq.04-06, fvm_2D_eq_frac.01),
+ * the free-surface pressure term, rain at t^{n+1}, the closed-form implicit
+ * soil-friction / plant-drag update (Eq. miu-formula) and the CFL time step
+ * (Eqs. fvm_2D_eq_frac.12-13).  Every step runs on the GPU; the host only launches
+ * and reads results.
+ *
+ * Raster: `rows` x `cols` pointy-top hexagons, row-major, every row `cols` cells long,
+ * odd rows shifted east by half a centre spacing.  Cell (r, c) is element r*cols + c of
+ * every dense field passed in or out.  `edge_m` is the hexagon edge length (the paper's
+ * "radius"); cell area sigma = (3 sqrt3 / 2) edge_m^2.
+ *
+ * State: the prognostic mass m = theta*h lives in float32 as an unevaluated sum
+ * hi + lo (a compensated pair), the velocity (v1, v2) in float32.  The global ledger
+ * (rain in, outflow, clamped water, storage) is float64.
+ *
+ * Conventions for every call:
+ *   - Inputs are copied in; the caller keeps ownership and may free them on return.
+ *   - Output buffers are caller-allocated.  ASX_PTR_DEVICE pointers must be device
+ *     memory of `desc.device`, dense (no pitch).
+ *   - Work is ordered on `desc.cuda_stream` (NULL = the legacy default stream).  A
+ *     call returns once its results are valid for the caller: calls that fill host
+ *     memory or return host values synchronise with that stream.
+ *   - No exception crosses the ABI: every call returns an asx_status; asx_last_error
+ *     gives a one-line description of the last failure on that handle.
+ *   - One thread at a time per handle.
+ */
+#ifndef ASX_H
+#define ASX_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    ASX_OK = 0,
+    ASX_EINVAL = 1,    /* an argument is out of range (see each call) */
+    ASX_ENOMEM = 2,    /* device or host allocation failed */
+    ASX_ECUDA = 3,     /* a CUDA runtime call failed (asx_last_error has the text) */
+    ASX_ESTATE = 4,    /* the call needs fields / params that were not set */
+    ASX_ENUMERIC = 5,  /* the state became non-finite; the clock stops at that step */
+    ASX_ETIMEOUT = 6   /* a bounded wait inside a kernel ran out */
+} asx_status;
+
+enum { ASX_BC_WALL = 0, ASX_BC_FREE = 1 };
+enum { ASX_SIDE_W = 0, ASX_SIDE_E = 1, ASX_SIDE_S = 2, ASX_SIDE_N = 3 };
+enum { ASX_PTR_HOST = 0, ASX_PTR_DEVICE = 1 };
+#define ASX_MAX_CLASSES 16
+#define ASX_MAX_RAIN 64
+
+typedef struct asx_raster asx_raster;      /* opaque, owned by the library */
+
+/* Geometry and boundaries of one raster (Sec. 2.2 (a); boundary types of Sec. 3).
+ *   bc[side]            ASX_BC_WALL (mirror: the edge carries nothing) or ASX_BC_FREE
+ *                       (free discharge: a ghost copy of the inner cell, outflow only).
+ *   free_begin/free_end with bc = FREE, free discharge applies to the positions
+ *                       [begin, end) along that side (the column for S/N, the row for
+ *                       W/E) and the rest of the side is a wall; begin == end: all.
+ *   n_classes           0: porosity is a float per cell; 1..ASX_MAX_CLASSES: each cell
+ *                       holds a uint8 land-cover class and asx_params gives per-class
+ *                       porosity and coefficients.
+ *   max_samples         capacity of the outlet hydrograph (0 = no hydrograph).
+ * A boundary edge belongs to the S or N side when its missing neighbour's row is
+ * outside the raster, otherwise to W or E. */
+typedef struct {
+    int rows, cols;            /* >= 2 each; rows * cols < 2^31 */
+    double edge_m;             /* > 0 */
+    int bc[4];                 /* indexed by ASX_SIDE_* */
+    int free_begin[4], free_end[4];
+    int n_classes;
+    int max_samples;
+    void *cuda_stream;         /* cudaStream_t; NULL = default stream */
+    int device;                /* CUDA device ordinal */
+} asx_raster_desc;
+
+/* Physical and numerical parameters (Sec. 3 "Parameters"; Eq. eq_K_h_theta).
+ *   g                        gravity [m/s^2] (> 0)
+ *   cfl                      Courant number in (0, 1] (Eq. fvm_2D_eq_frac.12)
+ *   dt_max                   maximum time step [s] (> 0)
+ *   alpha_s, alpha_p         soil friction [-] and plant drag [1/m] (>= 0), used when
+ *                            n_classes == 0
+ *   class_theta/alpha_p/alpha_s  n_classes entries each when n_classes > 0
+ *                            (theta in (0, 1], coefficients >= 0); host pointers
+ *   n_rain, rain_t, rain_r   piecewise-linear rain rate r(t) [m/s] at increasing times
+ *                            [s], zero outside [rain_t[0], rain_t[n-1]]; host
+ *                            pointers; n_rain <= ASX_MAX_RAIN (0 = no rain)
+ *   sample_dt                hydrograph sample interval [s]; steps are cut at the
+ *                            sample times (0 = none)
+ * ASX_EINVAL on any value out of range. */
+typedef struct {
+    double g, cfl, dt_max;
+    double alpha_s, alpha_p;
+    const float *class_theta, *class_alpha_p, *class_alpha_s;
+    int n_rain;
+    const double *rain_t, *rain_r;
+    double sample_dt;
+} asx_params;
+
+/* Water budget since the last asx_set_fields, all in m^3 (float64):
+ *   rain_in   sum over steps of sigma * (applied rain depth) over all cells
+ *   outflow   water that left through free-discharge edges
+ *   storage   sum over cells of sigma * theta h now (computed on the device)
+ *   storage0  the same at asx_set_fields
+ *   clamped   water created by setting a negative mass to zero
+ *   defect_rel |storage0 + rain_in + clamped - outflow - storage| /
+ *              max(rain_in, storage0) (0 when both are 0)
+ *   steps     time steps taken */
+typedef struct {
+    double rain_in, outflow, storage, storage0, clamped, defect_rel;
+    long long steps;
+} asx_ledger;
+
+/* Create a raster on desc->device.  Allocates all device memory it will use.
+ * ASX_EINVAL: rows or cols < 2, edge_m <= 0, a bc value other than WALL/FREE,
+ * n_classes outside [0, ASX_MAX_CLASSES], max_samples < 0. */
+asx_status asx_create_raster(const asx_raster_desc *desc, asx_raster **out);
+
+/* Free the raster and all its device memory (NULL is accepted). */
+asx_status asx_destroy_raster(asx_raster *r);
+
+/* Set the parameters; may be called again between steps. */
+asx_status asx_set_params(asx_raster *r, const asx_params *p);
+
+/* Set the static fields and the initial state (the paper's "Data In", Sec. 3), reset
+ * the clock to t = 0 and the ledger.  z: bed elevation [m] (float32, finite);
+ * theta_or_null: porosity per cell in (0, 1] when n_classes == 0, else NULL;
+ * class_or_null: class per cell (< n_classes) when n_classes > 0, else NULL;
+ * h0: initial depth [m] (>= 0, finite); v1_0, v2_0: initial velocity [m/s] (finite;
+ * NULL = 0).  All dense rows x cols.  ptr_kind: ASX_PTR_HOST or ASX_PTR_DEVICE.
+ * Value checks (ASX_EINVAL) are made on host inputs; device inputs are trusted.
+ * Needs asx_set_params first (ASX_ESTATE). */
+asx_status asx_set_fields(asx_raster *r, const float *z, const float *theta_or_null,
+                          const uint8_t *class_or_null, const float *h0, const float *v1_0,
+                          const float *v2_0, int ptr_kind);
+
+/* Advance exactly n_steps time steps (n_steps >= 0) of Eq. fvm_2D_eq_frac.07, each
+ * with the CFL time step (cut at hydrograph sample times).  *t_out (may be NULL)
+ * receives the time reached.  ASX_ENUMERIC if the state became non-finite. */
+asx_status asx_step(asx_raster *r, int n_steps, double *t_out);
+
+/* Advance until t == t_end (the last step is cut to land on t_end).  t_end below the
+ * current time is a no-op.  *t_out (may be NULL) receives the time reached. */
+asx_status asx_run_until(asx_raster *r, double t_end, double *t_out);
+
+/* Water budget (see asx_ledger).  scenario must be 0 for a single raster. */
+asx_status asx_mass_ledger(asx_raster *r, int scenario, asx_ledger *out);
+
+/* Depth h = m / theta and velocity of every cell, dense rows x cols float32 (any
+ * pointer may be NULL to skip that field). */
+asx_status asx_get_fields(asx_raster *r, int scenario, float *h, float *v1, float *v2,
+                          int ptr_kind);
+
+/* The raw state: compensated mass pair (m_hi, m_lo), v1, v2, dense rows x cols
+ * float32 (for checkpoints; any pointer may be NULL). */
+asx_status asx_get_state(asx_raster *r, float *m_hi, float *m_lo, float *v1, float *v2,
+                         int ptr_kind);
+
+/* Restore a raw state written by asx_get_state together with the clock and ledger of
+ * asx_get_clock / asx_mass_ledger at that moment; continuing from it reproduces the
+ * uninterrupted run bit for bit.  Needs asx_set_fields first (static fields). */
+asx_status asx_set_state(asx_raster *r, const float *m_hi, const float *m_lo,
+                         const float *v1, const float *v2, int ptr_kind, double t,
+                         long long step, const asx_ledger *ledger, int n_samples,
+                         const double *samples_cum_outflow);
+
+/* Outlet hydrograph: q[k] = outflow volume between sample times k and k+1, divided
+ * by sample_dt [m^3/s], for the samples recorded so far (at most cap).  *n receives
+ * the number of samples recorded. */
+asx_status asx_get_hydrograph(asx_raster *r, int scenario, double *q, int cap, int *n);
+
+/* Current time, the time step the next step will take (0 when no step is pending),
+ * and the number of steps taken. */
+asx_status asx_get_clock(asx_raster *r, int scenario, double *t, double *dt, long long *step);
+
+/* One-line description of the last error on this handle ("" if none; a static string
+ * for r == NULL). */
+const char *asx_last_error(const asx_raster *r);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* ASX_H */

@@ -1,0 +1,192 @@
+"""ctypes binding of the C ABI in ``include/asx.h`` (argument marshalling only).
+
+Every function keeps its C name and raises ``AsxError`` on a non-zero status.  Device
+buffers are passed as integer addresses (e.g. ``torch.Tensor.data_ptr()``), host buffers
+as numpy arrays.  All computation happens in ``libasx.so``; if the library is missing
+the import fails: there is no fallback.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "_build", "libasx.so")
+
+ASX_OK, ASX_EINVAL, ASX_ENOMEM, ASX_ECUDA, ASX_ESTATE, ASX_ENUMERIC, ASX_ETIMEOUT = range(7)
+STATUS_NAMES = {0: "ASX_OK", 1: "ASX_EINVAL", 2: "ASX_ENOMEM", 3: "ASX_ECUDA", 4: "ASX_ESTATE",
+                5: "ASX_ENUMERIC", 6: "ASX_ETIMEOUT"}
+ASX_BC_WALL, ASX_BC_FREE = 0, 1
+ASX_SIDE_W, ASX_SIDE_E, ASX_SIDE_S, ASX_SIDE_N = 0, 1, 2, 3
+ASX_PTR_HOST, ASX_PTR_DEVICE = 0, 1
+ASX_MAX_CLASSES = 16
+ASX_MAX_RAIN = 64
+
+
+class AsxError(RuntimeError):
+    def __init__(self, status, msg):
+        super().__init__(f"{STATUS_NAMES.get(status, status)}: {msg}")
+        self.status = status
+
+
+class asx_raster_desc(C.Structure):
+    _fields_ = [("rows", C.c_int), ("cols", C.c_int), ("edge_m", C.c_double), ("bc", C.c_int * 4),
+                ("free_begin", C.c_int * 4), ("free_end", C.c_int * 4), ("n_classes", C.c_int),
+                ("max_samples", C.c_int), ("cuda_stream", C.c_void_p), ("device", C.c_int)]
+
+
+class asx_params(C.Structure):
+    _fields_ = [("g", C.c_double), ("cfl", C.c_double), ("dt_max", C.c_double),
+                ("alpha_s", C.c_double), ("alpha_p", C.c_double),
+                ("class_theta", C.POINTER(C.c_float)), ("class_alpha_p", C.POINTER(C.c_float)),
+                ("class_alpha_s", C.POINTER(C.c_float)), ("n_rain", C.c_int),
+                ("rain_t", C.POINTER(C.c_double)), ("rain_r", C.POINTER(C.c_double)),
+                ("sample_dt", C.c_double)]
+
+
+class asx_ledger(C.Structure):
+    _fields_ = [("rain_in", C.c_double), ("outflow", C.c_double), ("storage", C.c_double),
+                ("storage0", C.c_double), ("clamped", C.c_double), ("defect_rel", C.c_double),
+                ("steps", C.c_longlong)]
+
+    def as_dict(self):
+        return {k: getattr(self, k) for k, _ in self._fields_}
+
+
+_vp = C.c_void_p
+_RASTER = C.c_void_p
+
+# name: (restype, argtypes)
+_PROTOS = {
+    "asx_create_raster": (C.c_int, [C.POINTER(asx_raster_desc), C.POINTER(_RASTER)]),
+    "asx_destroy_raster": (C.c_int, [_RASTER]),
+    "asx_set_params": (C.c_int, [_RASTER, C.POINTER(asx_params)]),
+    "asx_set_fields": (C.c_int, [_RASTER, _vp, _vp, _vp, _vp, _vp, _vp, C.c_int]),
+    "asx_step": (C.c_int, [_RASTER, C.c_int, C.POINTER(C.c_double)]),
+    "asx_run_until": (C.c_int, [_RASTER, C.c_double, C.POINTER(C.c_double)]),
+    "asx_mass_ledger": (C.c_int, [_RASTER, C.c_int, C.POINTER(asx_ledger)]),
+    "asx_get_fields": (C.c_int, [_RASTER, C.c_int, _vp, _vp, _vp, C.c_int]),
+    "asx_get_state": (C.c_int, [_RASTER, _vp, _vp, _vp, _vp, C.c_int]),
+    "asx_set_state": (C.c_int, [_RASTER, _vp, _vp, _vp, _vp, C.c_int, C.c_double, C.c_longlong,
+                                C.POINTER(asx_ledger), C.c_int, _vp]),
+    "asx_get_hydrograph": (C.c_int, [_RASTER, C.c_int, _vp, C.c_int, C.POINTER(C.c_int)]),
+    "asx_get_clock": (C.c_int, [_RASTER, C.c_int, C.POINTER(C.c_double), C.POINTER(C.c_double),
+                                C.POINTER(C.c_longlong)]),
+    "asx_last_error": (C.c_char_p, [_RASTER]),
+}
+
+_lib = None
+
+
+def load(path: str = LIB_PATH):
+    """Load libasx.so (raises if it has not been built)."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(path):
+            raise ImportError(f"{path} is missing: build it with paper_2406_14933_gb300.build.build()")
+        lib = C.CDLL(path)
+        for name, (res, args) in _PROTOS.items():
+            f = getattr(lib, name)
+            f.restype = res
+            f.argtypes = args
+        _lib = lib
+    return _lib
+
+
+def exported_names():
+    return list(_PROTOS)
+
+
+def _check(st, r=None):
+    if st != ASX_OK:
+        msg = load().asx_last_error(r).decode() if r else ""
+        raise AsxError(st, msg)
+
+
+def _ptr(x):
+    """Address of a numpy array, an integer device address, a torch tensor, or None."""
+    if x is None:
+        return None
+    if isinstance(x, int):
+        return x
+    if isinstance(x, np.ndarray):
+        assert x.flags["C_CONTIGUOUS"]
+        return x.ctypes.data
+    if hasattr(x, "data_ptr"):
+        return x.data_ptr()
+    raise TypeError(type(x))
+
+
+# ----------------------------------------------------------------- C-named wrappers
+
+def asx_create_raster(desc: asx_raster_desc):
+    r = _RASTER()
+    _check(load().asx_create_raster(C.byref(desc), C.byref(r)))
+    return r
+
+
+def asx_destroy_raster(r):
+    _check(load().asx_destroy_raster(r))
+
+
+def asx_set_params(r, p: asx_params):
+    _check(load().asx_set_params(r, C.byref(p)), r)
+
+
+def asx_set_fields(r, z, theta, cls, h0, v1, v2, ptr_kind):
+    _check(load().asx_set_fields(r, _ptr(z), _ptr(theta), _ptr(cls), _ptr(h0), _ptr(v1), _ptr(v2),
+                                 ptr_kind), r)
+
+
+def asx_step(r, n_steps):
+    t = C.c_double()
+    _check(load().asx_step(r, int(n_steps), C.byref(t)), r)
+    return t.value
+
+
+def asx_run_until(r, t_end):
+    t = C.c_double()
+    _check(load().asx_run_until(r, float(t_end), C.byref(t)), r)
+    return t.value
+
+
+def asx_mass_ledger(r, scenario=0):
+    led = asx_ledger()
+    _check(load().asx_mass_ledger(r, int(scenario), C.byref(led)), r)
+    return led
+
+
+def asx_get_fields(r, scenario, h, v1, v2, ptr_kind):
+    _check(load().asx_get_fields(r, int(scenario), _ptr(h), _ptr(v1), _ptr(v2), ptr_kind), r)
+
+
+def asx_get_state(r, m_hi, m_lo, v1, v2, ptr_kind):
+    _check(load().asx_get_state(r, _ptr(m_hi), _ptr(m_lo), _ptr(v1), _ptr(v2), ptr_kind), r)
+
+
+def asx_set_state(r, m_hi, m_lo, v1, v2, ptr_kind, t, step, ledger, samples=None):
+    ns = 0 if samples is None else int(len(samples))
+    sp = None if samples is None else _ptr(np.ascontiguousarray(samples, dtype=np.float64))
+    keep = samples
+    _check(load().asx_set_state(r, _ptr(m_hi), _ptr(m_lo), _ptr(v1), _ptr(v2), ptr_kind, float(t),
+                                int(step), C.byref(ledger), ns, sp), r)
+    del keep
+
+
+def asx_get_hydrograph(r, scenario, cap):
+    q = np.zeros(max(int(cap), 1))
+    n = C.c_int()
+    _check(load().asx_get_hydrograph(r, int(scenario), q.ctypes.data, int(cap), C.byref(n)), r)
+    return q[:min(n.value, int(cap))].copy(), n.value
+
+
+def asx_get_clock(r, scenario=0):
+    t, dt, s = C.c_double(), C.c_double(), C.c_longlong()
+    _check(load().asx_get_clock(r, int(scenario), C.byref(t), C.byref(dt), C.byref(s)), r)
+    return t.value, dt.value, s.value
+
+
+def asx_last_error(r):
+    return load().asx_last_error(r).decode()

@@ -1,0 +1,97 @@
+// asx_internal.cuh -- data layout, device control block and kernel launchers shared by
+// the CUDA kernels (kernels.cu) and the C-ABI runtime (runtime.cu).  Not installed.
+#pragma once
+
+#include <cstdint>
+#include <cuda_runtime.h>
+
+#include "../../include/asx.h"
+
+namespace asx {
+
+constexpr int kPitchAlign = 32;          // row pitch of every field, in elements
+constexpr int kMaxRain = ASX_MAX_RAIN;
+constexpr int kMaxClasses = ASX_MAX_CLASSES;
+
+// Device-resident clock, per-step scalars, step reductions and ledger of one raster.
+// Written only by the single thread that finishes a step (the last CTA of the step
+// kernel) or by one-thread control kernels; read by every CTA at the start of a step.
+struct DevCtl {
+    // clock
+    double t;            // t^n
+    double dt;           // dt_n of the pending step (0 if none)
+    double t_next;       // t^{n+1} of the pending step
+    double t_end;        // run target
+    long long step;      // steps taken
+    long long step_limit;
+    // scalars of the pending step, identical for every CTA
+    float kappa;         // dt / sigma
+    float qr;            // rain depth added to every cell: fl32(dt * r(t^{n+1}))
+    float dtf;           // (float) dt
+    int active;          // 1 if a step is pending
+    int parity;          // state buffer holding t^n
+    int err;             // error bits (kErrNumeric, kErrTimeout)
+    float cmax_cur;      // c_max of the state at t^n
+    int pad0;
+    // reductions of the running step
+    unsigned int cmax_bits;
+    unsigned int done_ctas;
+    unsigned int scan_done;
+    unsigned int pad2;
+    double out_acc;      // sum of boundary mass increments (per unit area)
+    double clamp_acc;    // sum of clamped (negative) mass, per unit area
+    // ledger [m^3]
+    double rain_in, outflow, clamped, storage0, storage;
+    // hydrograph
+    double sample_dt;
+    int n_samples, max_samples;
+    double *samples;     // cumulative outflow at each sample time
+    // parameters of the time step and the rain
+    double g, cfl, dt_max, sigma, phi;
+    long long ncells;
+    int n_rain, pad1;
+    double rain_t[kMaxRain], rain_r[kMaxRain];
+};
+
+constexpr int kErrNumeric = 1;
+constexpr int kErrTimeout = 2;
+
+// Arguments of the step kernels (passed by value; fixed for a raster so that a
+// captured CUDA graph can replay them).
+struct StepArgs {
+    int rows, cols, pitch;
+    int nblocks;                       // CTAs of one step launch (last-CTA detection)
+    // state buffers [parity][field], each rows x pitch float32
+    float *mhi[2], *mlo[2], *v1[2], *v2[2];
+    const float *z;                    // rows x pitch
+    const float *theta;                // rows x pitch, or nullptr in class mode
+    const uint8_t *cls;                // rows x pitch, or nullptr
+    // per-class tables (class mode) or the global coefficients in entry 0
+    float cls_theta[kMaxClasses], cls_a[kMaxClasses], cls_b[kMaxClasses];
+    float alpha_s, alpha_p;            // per-cell-porosity mode
+    // geometry constants (float32)
+    float l;                           // edge length
+    float g;                           // gravity
+    float cpe[3][2];                   // -1/2 l g n for owned directions E, NE, NW
+    // boundaries
+    int bc[4], fb[4], fe[4];
+    DevCtl *ctl;
+};
+
+// ---- launchers (kernels.cu) ----
+cudaError_t launch_step_gather(const StepArgs &a, cudaStream_t s);
+int step_gather_blocks(int rows, int cols);
+cudaError_t launch_prepare(DevCtl *ctl, int mode, double t_end, long long n_steps, cudaStream_t s);
+cudaError_t launch_scan(const StepArgs &a, double *partials, int nparts, int set_storage0,
+                        cudaStream_t s);
+int scan_blocks(int rows, int cols);
+cudaError_t launch_init_state(const StepArgs &a, int parity, const float *h, const float *v1,
+                              const float *v2, cudaStream_t s);
+cudaError_t launch_extract_depth(const StepArgs &a, int parity, float *h_out, cudaStream_t s);
+
+// prepare modes
+constexpr int kPrepRecompute = 0;   // recompute the pending step from the current clock
+constexpr int kPrepSteps = 1;       // allow n more steps, no time target
+constexpr int kPrepUntil = 2;       // run to t_end, no step limit
+
+}  // namespace asx

@@ -323,14 +323,14 @@ def random_state(sc: Scenario, seed: int, wet_fraction=0.7, depth=0.05, speed=0.
 
 def tiny(rows, cols, seed, l=1.0, bc=(WALL, WALL, WALL, WALL), relief=0.2, theta_lo=0.6,
          rain_mm_h=0.0) -> Scenario:
-    """Small random raster for parity tests: random smooth-ish bed, random porosity in
-    [theta_lo, 1], random coefficients, random wet/dry state."""
+    """Small random raster for parity tests: random bed, random porosity per cell in
+    [theta_lo, 1], random (uniform) friction and drag coefficients, random wet/dry state."""
     rng = np.random.default_rng(seed)
     sh = (rows, cols)
     z = (relief * rng.uniform(size=sh)).astype(np.float32)
     theta = rng.uniform(theta_lo, 1.0, size=sh).astype(np.float32)
-    a_s = rng.uniform(0.0, 0.02, size=sh).astype(np.float32)
-    a_p = rng.uniform(0.0, 100.0, size=sh).astype(np.float32)
+    a_s = np.full(sh, rng.uniform(0.0, 0.02), dtype=np.float32)
+    a_p = np.full(sh, rng.uniform(0.0, 100.0), dtype=np.float32)
     sc = Scenario(f"tiny{rows}x{cols}", rows, cols, l, z, theta, a_s, a_p, _fill(sh, 0.0),
                   _fill(sh, 0.0), _fill(sh, 0.0), bc=tuple(bc))
     h, v1, v2 = random_state(sc, seed + 1)

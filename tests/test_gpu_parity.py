@@ -1,0 +1,215 @@
+"""Parity of the CUDA path (through the C ABI) with the FP64 oracle.
+
+Tolerances (float32 state against float64):
+  * one step, same dt: theta*h and the discharge theta*h*v agree to 2e-6 of the field's
+    maximum (each cell sums at most seven float32 terms of size <= CFL * theta*h, each
+    rounded once or twice);
+  * whole runs: depth and discharge relative L2 <= 1e-4, the stated target;
+  * mass budget: defect <= 1e-10 of the rain volume (compensated float32 mass).
+Velocity itself is compared through the discharge: in a dry cell the velocity is not
+defined by the water it carries.
+"""
+import math
+
+import numpy as np
+import pytest
+
+from paper_2406_14933_gb300 import inputs
+
+pytestmark = pytest.mark.gpu
+
+
+def _raster(asx, sc, **kw):
+    from paper_2406_14933_gb300.raster import Raster
+    return Raster(sc, **kw)
+
+
+def _oracle_problem(orc, sc):
+    return orc.from_scenario(sc)
+
+
+def _rel_l2(a, b):
+    a, b = np.asarray(a, np.float64).ravel(), np.asarray(b, np.float64).ravel()
+    nb = np.linalg.norm(b)
+    return np.linalg.norm(a - b) / (nb if nb > 0 else 1.0)
+
+
+SIZES = [(2, 2), (2, 3), (3, 5), (8, 8), (9, 31), (16, 16), (33, 70), (77, 130)]
+BCS = [(0, 0, 0, 0), (1, 1, 1, 1), (1, 0, 1, 0), (0, 1, 0, 1)]
+
+
+@pytest.mark.parametrize("rows,cols", SIZES)
+@pytest.mark.parametrize("bc", BCS)
+def test_one_step_matches_oracle(asx, orc, rows, cols, bc):
+    sc = inputs.tiny(rows, cols, seed=rows * 1000 + cols + 7 * sum(bc), bc=bc, rain_mm_h=60.0)
+    R = _raster(asx, sc)
+    p = _oracle_problem(orc, sc)
+    m0 = p.mass(sc.h0)
+    mg0, _, _ = R.mass64()
+    assert np.array_equal(mg0.ravel(), m0)          # theta*h of two float32 is exact in float64
+    t1 = R.step(1)
+    assert t1 > 0
+    mo, ao, bo = p.step(m0, sc.v1_0, sc.v2_0, t1, t1)
+    mg, vg1, vg2 = R.mass64()
+    mg = mg.ravel()
+    scale_m = max(np.abs(mo).max(), 1e-30)
+    assert np.abs(mg - mo).max() <= 2e-6 * scale_m
+    qo1, qo2 = mo * ao, mo * bo
+    qg1, qg2 = mg * vg1.ravel(), mg * vg2.ravel()
+    scale_q = max(np.abs(qo1).max(), np.abs(qo2).max(), 1e-30)
+    assert np.abs(qg1 - qo1).max() <= 2e-6 * scale_q
+    assert np.abs(qg2 - qo2).max() <= 2e-6 * scale_q
+    led = R.ledger()
+    assert led.defect_rel <= 1e-10
+    R.close()
+
+
+@pytest.mark.parametrize("rows,cols,bc", [(16, 16, (1, 1, 1, 1)), (33, 70, (1, 0, 1, 0)),
+                                          (77, 130, (0, 1, 0, 1))])
+def test_many_steps_with_dt_replay(asx, orc, rows, cols, bc):
+    """200 steps; the oracle replays the GPU's time levels.  Depth and discharge
+    relative L2 <= 1e-4, budget defect <= 1e-10."""
+    sc = inputs.tiny(rows, cols, seed=99 + rows, bc=bc, rain_mm_h=40.0)
+    R = _raster(asx, sc)
+    ts = [R.step(1) for _ in range(200)]
+    p = _oracle_problem(orc, sc)
+    res = p.run(p.mass(sc.h0), sc.v1_0, sc.v2_0, 0.0, ts[-1], t_replay=np.array(ts))
+    assert res["steps"] == 200
+    mg, vg1, vg2 = R.mass64()
+    ho, hg = p.depth(res["m"]), p.depth(mg.ravel())
+    assert _rel_l2(hg, ho) <= 1e-4
+    qo = np.concatenate([res["m"] * res["v1"], res["m"] * res["v2"]])
+    qg = np.concatenate([mg.ravel() * vg1.ravel(), mg.ravel() * vg2.ravel()])
+    assert _rel_l2(qg, qo) <= 1e-4
+    assert R.ledger().defect_rel <= 1e-10
+    R.close()
+
+
+def test_hillslope_full_run(asx, orc):
+    """The 64 x 64 vegetated hillslope (5 % slope, porosity 0.9, 50 mm/h for 600 s) run to
+    t_end on both sides with their own time steps."""
+    sc = inputs.hillslope()
+    R = _raster(asx, sc)
+    t = R.run_until(sc.t_end)
+    assert t == sc.t_end
+    p = _oracle_problem(orc, sc)
+    res = p.run(p.mass(sc.h0), sc.v1_0, sc.v2_0, 0.0, sc.t_end)
+    mg, vg1, vg2 = R.mass64()
+    assert _rel_l2(p.depth(mg.ravel()), p.depth(res["m"])) <= 1e-4
+    qo = np.concatenate([res["m"] * res["v1"], res["m"] * res["v2"]])
+    qg = np.concatenate([mg.ravel() * vg1.ravel(), mg.ravel() * vg2.ravel()])
+    assert _rel_l2(qg, qo) <= 1e-4
+    led = R.ledger()
+    assert led.defect_rel <= 1e-10
+    area = 64 * 64 * 1.5 * math.sqrt(3.0)
+    assert led.rain_in == pytest.approx(area * 50e-3 / 3600 * 600, rel=1e-6)
+    assert led.outflow == pytest.approx(res["ledger"].outflow, rel=1e-4)
+    R.close()
+
+
+def test_lake_at_rest_exact(asx):
+    """Dyadic bed, surface and porosity: the lake with dry islands stays exactly at rest."""
+    rows, cols = 40, 52
+    rng = np.random.default_rng(5)
+    sc = inputs.tiny(rows, cols, seed=3, bc=(1, 0, 1, 0))
+    z = np.round(rng.uniform(0, 1, (rows, cols)) * 4096) / 4096
+    sc.z = z.astype(np.float32)
+    sc.theta = rng.choice([0.5, 1.0], (rows, cols)).astype(np.float32)
+    sc.h0 = np.maximum(0.625 - sc.z, 0).astype(np.float32)
+    sc.v1_0[:] = 0
+    sc.v2_0[:] = 0
+    R = _raster(asx, sc)
+    R.step(500)
+    h, v1, v2 = R.fields()
+    assert np.array_equal(h, sc.h0)
+    assert not v1.any() and not v2.any()
+    R.close()
+
+
+def test_hydrograph_matches_oracle(asx, orc):
+    """A small carved catchment with one outlet, hydrograph every 10 s for 10 min."""
+    sc = inputs.carved_catchment(rows=96, cols=128, l=5.0, block=16, min_acc=3, seed=17)
+    sc.t_end = 600.0
+    R = _raster(asx, sc)
+    R.run_until(sc.t_end)
+    q = R.hydrograph()
+    p = _oracle_problem(orc, sc)
+    res = p.run(p.mass(sc.h0), sc.v1_0, sc.v2_0, 0.0, sc.t_end, sample_dt=sc.sample_dt,
+                sample_cap=1000)
+    cum = res["samples"]
+    qo = np.diff(np.concatenate([[0.0], cum])) / sc.sample_dt
+    assert len(q) == len(qo) == 60
+    assert qo.max() > 0
+    assert _rel_l2(q, qo) <= 1e-3
+    assert R.ledger().defect_rel <= 1e-10
+    R.close()
+
+
+def test_resume_is_bitwise(asx):
+    """Checkpoint (state, clock, ledger, hydrograph) and resume: identical to the
+    uninterrupted run."""
+    from paper_2406_14933_gb300 import asx as A
+    sc = inputs.tiny(40, 64, seed=8, bc=(1, 1, 0, 0), rain_mm_h=30.0)
+    sc.sample_dt = 5.0
+    sc.t_end = 200.0
+    R = _raster(asx, sc)
+    R.step(50)
+    mh, ml, v1, v2 = R.state()
+    t, _, step = R.clock()
+    led = R.ledger()
+    cum = np.cumsum(R.hydrograph()) * sc.sample_dt
+    R.step(70)
+    ref = R.state()
+    R2 = _raster(asx, sc)
+    A.asx_set_state(R2.handle, mh, ml, v1, v2, A.ASX_PTR_HOST, t, step, led, cum)
+    R2.step(70)
+    out = R2.state()
+    for a, b in zip(ref, out):
+        assert np.array_equal(a, b)
+    assert R2.clock() == R.clock()
+    R.close()
+    R2.close()
+
+
+def test_device_pointer_inputs_and_numeric_error(asx):
+    """Fields passed as device pointers; a NaN planted in a device input (device inputs
+    are not checked on the host) stops the clock with ASX_ENUMERIC."""
+    import torch
+    from paper_2406_14933_gb300 import asx as A
+    sc = inputs.tiny(24, 40, seed=4, bc=(1, 1, 1, 1))
+    R = _raster(asx, sc)
+    dev = {k: torch.from_numpy(np.ascontiguousarray(getattr(sc, k))).cuda()
+           for k in ("z", "theta", "h0", "v1_0", "v2_0")}
+    A.asx_set_fields(R.handle, dev["z"], dev["theta"], None, dev["h0"], dev["v1_0"], dev["v2_0"],
+                     A.ASX_PTR_DEVICE)
+    torch.cuda.synchronize()
+    R.step(3)
+    dev["v1_0"][5, 7] = float("nan")
+    A.asx_set_fields(R.handle, dev["z"], dev["theta"], None, dev["h0"], dev["v1_0"], dev["v2_0"],
+                     A.ASX_PTR_DEVICE)
+    with pytest.raises(A.AsxError) as e:
+        R.step(5)
+    assert e.value.status == A.ASX_ENUMERIC
+    R.close()
+
+
+def test_invalid_arguments(asx):
+    from paper_2406_14933_gb300 import asx as A
+    sc = inputs.tiny(8, 8, seed=1)
+    R = _raster(asx, sc)
+    with pytest.raises(A.AsxError) as e:
+        R.step(-1)
+    assert e.value.status == A.ASX_EINVAL
+    bad = sc.h0.copy()
+    bad[0, 0] = -1.0
+    with pytest.raises(A.AsxError) as e:
+        A.asx_set_fields(R.handle, sc.z, sc.theta, None, bad, sc.v1_0, sc.v2_0, A.ASX_PTR_HOST)
+    assert e.value.status == A.ASX_EINVAL
+    th = sc.theta.copy()
+    th[1, 1] = 0.0
+    with pytest.raises(A.AsxError) as e:
+        A.asx_set_fields(R.handle, sc.z, th, None, sc.h0, sc.v1_0, sc.v2_0, A.ASX_PTR_HOST)
+    assert e.value.status == A.ASX_EINVAL
+    with pytest.raises(A.AsxError):
+        R.set_params(cfl=1.5)
+    R.close()

@@ -290,7 +290,7 @@ __global__ void __launch_bounds__(kGX *kGY) step_gather_kernel(const StepArgs a)
         const Cell I = load_cell(a, mhi, v1, v2, k);
         float shi = I.m, slo = __ldg(mlo + k);
         float M1 = 0.0f, M2 = 0.0f;      // J_a + S_a
-        float outf = 0.0f;
+        double outd = 0.0;               // booked exactly as applied (each q is a float)
 #pragma unroll
         for (int d = 0; d < 6; d++) {
             int rr, cc, side;
@@ -325,13 +325,13 @@ __global__ void __launch_bounds__(kGX *kGY) step_gather_kernel(const StepArgs a)
                         acc_add(shi, slo, -q);
                         M1 -= F * I.v1;
                         M2 -= F * I.v2;
-                        outf += q;
+                        outd += (double)q;
                     }
                 }
                 // wall: mirror ghost, the edge carries nothing
             }
         }
-        outq = (double)outf;
+        outq = outd;
         // rain at t^{n+1}
         acc_add(shi, slo, qr);
         float hi, lo;

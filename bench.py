@@ -106,9 +106,9 @@ def _dist():
     return ws, rank
 
 
-def _workload_config(sc, k):
+def _workload_config(sc, k, t_warm=T_WARM):
     return {"workload": f"carved catchment {sc.rows}x{sc.cols} hex, edge {sc.l:g} m, "
-                        f"3 land-cover classes, double-peak storm, window from t={T_WARM:.0f} s",
+                        f"3 land-cover classes, double-peak storm, window from t={t_warm:.0f} s",
             "cells": sc.n, "rows": sc.rows, "cols": sc.cols, "steps_timed": k,
             "l2": "state 0.74 GB > 129 MB L2 (no flush needed)", "parallelism": "replicas"}
 
@@ -127,11 +127,12 @@ def run_cuda(args):
     from paper_2406_14933_gb300 import inputs
     from paper_2406_14933_gb300.raster import Raster
 
-    sc = inputs.carved_catchment()
+    sc = inputs.carved_catchment(rows=args.rows, cols=args.cols)
     stream = torch.cuda.current_stream()
     R = Raster(sc, device=local, stream=stream.cuda_stream)
-    R.run_until(T_WARM)
+    R.run_until(args.t_warm)
     R.step(args.warmup)
+    warm_steps = R.clock()[2]
     n = sc.n
 
     def barrier():
@@ -145,10 +146,12 @@ def run_cuda(args):
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     barrier()
     with ClockSampler(local) as clk:
+        torch.cuda.nvtx.range_push("timed")
         e0.record(stream)
         R.step(args.steps)
         e1.record(stream)
         torch.cuda.synchronize()
+        torch.cuda.nvtx.range_pop()
     ms = e0.elapsed_time(e1)
     barrier()
     # end to end through the C ABI from pinned host buffers: upload the state, K steps,
@@ -184,7 +187,9 @@ def run_cuda(args):
         "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f32",
         "data": "synthetic (seeded fBm catchment, carved channels, land-cover classes)",
-        "config": _workload_config(sc, args.steps),
+        "config": dict(_workload_config(sc, args.steps, args.t_warm), warm_steps=warm_steps,
+                       step_kernel=os.environ.get("ASX_STEP_KERNEL", "strip"),
+                       tile_rows=int(os.environ.get("ASX_TILE_ROWS", "16"))),
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                      "frac": achieved / peak, "traffic": traffic,
                      "peak_source": f"{peak_kind} copy bandwidth",
@@ -293,6 +298,10 @@ def main():
     ap.add_argument("--impl", default="cuda", choices=["cuda", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-budget", type=float, default=15.0)
+    ap.add_argument("--rows", type=int, default=4096)
+    ap.add_argument("--cols", type=int, default=4096)
+    ap.add_argument("--t-warm", type=float, default=T_WARM,
+                    help="simulated time before the timed window [s]")
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)
     out = run_reference(args) if args.impl == "reference" else run_cuda(args)

@@ -3,6 +3,7 @@
 #pragma once
 
 #include <cstdint>
+#include <cuda.h>
 #include <cuda_runtime.h>
 
 #include "../../include/asx.h"
@@ -10,6 +11,7 @@
 namespace asx {
 
 constexpr int kPitchAlign = 32;          // row pitch of every field, in elements
+constexpr int kStripW = 128;             // columns of a strip-kernel tile
 constexpr int kMaxRain = ASX_MAX_RAIN;
 constexpr int kMaxClasses = ASX_MAX_CLASSES;
 
@@ -61,13 +63,14 @@ constexpr int kErrTimeout = 2;
 struct StepArgs {
     int rows, cols, pitch;
     int nblocks;                       // CTAs of one step launch (last-CTA detection)
+    int tile_rows;                     // rows of a strip-kernel tile
     // state buffers [parity][field], each rows x pitch float32
     float *mhi[2], *mlo[2], *v1[2], *v2[2];
     const float *z;                    // rows x pitch
     const float *theta;                // rows x pitch, or nullptr in class mode
     const uint8_t *cls;                // rows x pitch, or nullptr
     // per-class tables (class mode) or the global coefficients in entry 0
-    float cls_theta[kMaxClasses], cls_a[kMaxClasses], cls_b[kMaxClasses];
+    float cls_theta[kMaxClasses], cls_rth[kMaxClasses], cls_a[kMaxClasses], cls_b[kMaxClasses];
     float alpha_s, alpha_p;            // per-cell-porosity mode
     // geometry constants (float32)
     float l;                           // edge length
@@ -78,7 +81,19 @@ struct StepArgs {
     DevCtl *ctl;
 };
 
-// ---- launchers (kernels.cu) ----
+// TMA descriptors of the fields, per state parity (strip kernel).  mhi/v1/v2/z/theta
+// boxes are (kStripW + 8) x 2 floats; mlo boxes kStripW x 2 floats; class boxes
+// (kStripW + 32) x 2 bytes.
+struct StripMaps {
+    CUtensorMap mhi[2], v1[2], v2[2], mlo[2];
+    CUtensorMap z, th;
+};
+
+// ---- launchers (kernels.cu, step_strip.cu) ----
+size_t step_strip_smem();
+int step_strip_blocks(int rows, int cols, int tile_rows);
+cudaError_t step_strip_configure();
+cudaError_t launch_step_strip(const StepArgs &a, const StripMaps &maps, cudaStream_t s);
 cudaError_t launch_step_gather(const StepArgs &a, cudaStream_t s);
 int step_gather_blocks(int rows, int cols);
 cudaError_t launch_prepare(DevCtl *ctl, int mode, double t_end, long long n_steps, cudaStream_t s);

@@ -22,250 +22,11 @@
 #include <cmath>
 #include <cstdio>
 
-#include "asx_internal.cuh"
+#include "device_common.cuh"
 
 namespace asx {
 
 namespace {
-
-constexpr float kS32 = 0.866025403784438647f;     // sqrt(3) / 2
-
-// ----------------------------------------------------------------- small helpers
-
-// Error-free transformation a + b = s + e (Knuth's two-sum).
-__device__ __forceinline__ void two_sum(float a, float b, float &s, float &e)
-{
-    s = __fadd_rn(a, b);
-    const float bb = __fsub_rn(s, a);
-    e = __fadd_rn(__fsub_rn(a, __fsub_rn(s, bb)), __fsub_rn(b, bb));
-}
-
-// Adds x to the compensated pair (hi, lo) (lo collects the rounding errors).
-__device__ __forceinline__ void acc_add(float &hi, float &lo, float x)
-{
-    float s, e;
-    two_sum(hi, x, s, e);
-    hi = s;
-    lo = __fadd_rn(lo, e);
-}
-
-// Wave speed c = |v| + sqrt(g h) (Eq. fvm_2D_eq_frac.13) from the float32 state.
-__device__ __forceinline__ float wave_speed(float v1, float v2, float h, float g)
-{
-    return __fadd_rn(__fsqrt_rn(__fmaf_rn(v1, v1, __fmul_rn(v2, v2))), __fsqrt_rn(__fmul_rn(g, h)));
-}
-
-// Piecewise-linear rain rate r(t) [m/s], zero outside the table (Appendix C).
-__device__ double rain_rate(const DevCtl *c, double t)
-{
-    const int n = c->n_rain;
-    if (n <= 0) return 0.0;
-    if (t < c->rain_t[0] || t > c->rain_t[n - 1]) return 0.0;
-    if (n == 1) return c->rain_r[0];
-    for (int k = 0; k + 1 < n; k++) {
-        const double t0 = c->rain_t[k], t1 = c->rain_t[k + 1];
-        if (t <= t1) {
-            if (t1 == t0) return c->rain_r[k + 1];
-            return c->rain_r[k] + (c->rain_r[k + 1] - c->rain_r[k]) * (t - t0) / (t1 - t0);
-        }
-    }
-    return c->rain_r[n - 1];
-}
-
-// dt_n = min(dt_max, CFL phi / c_max^n), cut at t_end and the next sample time
-// (Eqs. fvm_2D_eq_frac.12-13); fills the per-step scalars every CTA reads.
-__device__ void prepare_step(DevCtl *c)
-{
-    c->active = 0;
-    c->dt = 0.0;
-    if (c->err) return;
-    if (!(c->t < c->t_end) || c->step >= c->step_limit) return;
-    double dt = c->dt_max;
-    if (c->cmax_cur > 0.0f) {
-        const double tau = c->cfl * c->phi / (double)c->cmax_cur;
-        if (tau < dt) dt = tau;
-    }
-    double t_stop = c->t_end;
-    if (c->sample_dt > 0.0) {
-        const double ns = (double)(c->n_samples + 1) * c->sample_dt;
-        if (ns < t_stop) t_stop = ns;
-    }
-    double tn;
-    if (c->t + dt >= t_stop) {
-        dt = t_stop - c->t;
-        tn = t_stop;
-    } else {
-        tn = c->t + dt;
-    }
-    const double r = rain_rate(c, tn);
-    c->dt = dt;
-    c->t_next = tn;
-    c->kappa = (float)(dt / c->sigma);
-    c->qr = (float)(dt * r);
-    c->dtf = (float)dt;
-    c->active = 1;
-}
-
-// Books the finished step (run by one thread after every CTA of the step is done).
-__device__ void finish_step(DevCtl *c)
-{
-    volatile DevCtl *vc = c;
-    const unsigned bits = vc->cmax_bits;
-    const double outq = vc->out_acc;
-    const double clq = vc->clamp_acc;
-    const float cmax = __uint_as_float(bits);
-    c->rain_in += c->sigma * (double)c->ncells * (double)c->qr;
-    c->outflow += c->sigma * outq;
-    c->clamped += c->sigma * clq;
-    c->t = c->t_next;
-    c->step += 1;
-    c->parity ^= 1;
-    if (c->sample_dt > 0.0 && c->t == (double)(c->n_samples + 1) * c->sample_dt) {
-        if (c->n_samples < c->max_samples) c->samples[c->n_samples] = c->outflow;
-        c->n_samples += 1;
-    }
-    if (!(cmax <= FLT_MAX)) c->err |= kErrNumeric;   // NaN or Inf somewhere
-    c->cmax_cur = cmax;
-    c->cmax_bits = 0u;
-    c->out_acc = 0.0;
-    c->clamp_acc = 0.0;
-    c->done_ctas = 0u;
-    prepare_step(c);
-}
-
-// --------------------------------------------------------------- cell and edge terms
-
-struct Cell {
-    float m;    // theta*h (hi word)
-    float v1, v2;
-    float z;
-    float h;    // m / theta
-};
-
-__device__ __forceinline__ float cell_theta(const StepArgs &a, size_t k)
-{
-    return a.cls ? a.cls_theta[a.cls[k]] : a.theta[k];
-}
-
-__device__ __forceinline__ Cell load_cell(const StepArgs &a, const float *mhi, const float *v1,
-                                          const float *v2, size_t k)
-{
-    Cell q;
-    q.m = __ldg(mhi + k);
-    q.v1 = __ldg(v1 + k);
-    q.v2 = __ldg(v2 + k);
-    q.z = __ldg(a.z + k);
-    q.h = __fdiv_rn(q.m, a.cls ? a.cls_theta[__ldg(a.cls + k)] : __ldg(a.theta + k));
-    return q;
-}
-
-// Terms of the edge between A (lower index) and B, B lying in owned direction D of A
-// (0 = E, 1 = NE, 2 = NW): mass increment q = kappa * l * (theta h)_(A,B) * v_n, the
-// momentum flux F (v_a)_(A,B) and the pressure term P_a = -1/2 l g dw (theta h)^ n_a.
-// A receives -q and -F v + P, B receives +q and +F v + P.
-template <int D>
-__device__ __forceinline__ void edge_terms(const Cell &A, const Cell &B, float l, float kappa,
-                                           float c1, float c2, float &q, float &fa1, float &fa2,
-                                           float &p1, float &p2)
-{
-    const float s1 = __fadd_rn(A.v1, B.v1);          // 2 (v_1)_(A,B)
-    const float s2 = __fadd_rn(A.v2, B.v2);
-    float vn;                                        // (v_n)_(A,B), Eq. fvm_2D_eq.04
-    if (D == 0) vn = __fmul_rn(0.5f, s1);
-    else if (D == 1) vn = __fmul_rn(0.5f, __fmaf_rn(kS32, s2, __fmul_rn(0.5f, s1)));
-    else vn = __fmul_rn(0.5f, __fmaf_rn(kS32, s2, __fmul_rn(-0.5f, s1)));
-    const float mu = vn > 0.0f ? A.m : B.m;          // Eq. fvm_2D_eq.06 (F = 0 if v_n = 0)
-    const float F = __fmul_rn(__fmul_rn(l, mu), vn);
-    q = __fmul_rn(kappa, F);
-    const float hF = __fmul_rn(0.5f, F);
-    fa1 = __fmul_rn(hF, s1);
-    fa2 = __fmul_rn(hF, s2);
-    const float dw = __fadd_rn(__fsub_rn(B.z, A.z), __fsub_rn(B.h, A.h));   // (w_B - w_A) / g
-    const float hat = vn != 0.0f ? mu : (dw < 0.0f ? A.m : B.m);          // Eq. fvm_2D_eq.05
-    const float dh = __fmul_rn(dw, hat);
-    p1 = __fmul_rn(c1, dh);
-    p2 = __fmul_rn(c2, dh);
-}
-
-__device__ __forceinline__ bool side_is_free(const StepArgs &a, int side, int pos)
-{
-    if (a.bc[side] != ASX_BC_FREE) return false;
-    if (a.fb[side] == a.fe[side]) return true;
-    return pos >= a.fb[side] && pos < a.fe[side];
-}
-
-// Neighbour of (r, c) in direction d (0 E, 1 NE, 2 NW, 3 W, 4 SW, 5 SE); odd rows are
-// shifted east.  Returns false and the boundary side if it lies outside the raster.
-__device__ __forceinline__ bool neighbour(int rows, int cols, int r, int c, int d, int &rr, int &cc,
-                                          int &side)
-{
-    const int odd = r & 1;
-    rr = r;
-    cc = c;
-    switch (d) {
-    case 0: cc = c + 1; break;
-    case 1: rr = r + 1; cc = c + odd; break;
-    case 2: rr = r + 1; cc = c - 1 + odd; break;
-    case 3: cc = c - 1; break;
-    case 4: rr = r - 1; cc = c - 1 + odd; break;
-    default: rr = r - 1; cc = c + odd; break;
-    }
-    if (rr < 0) { side = ASX_SIDE_S; return false; }
-    if (rr >= rows) { side = ASX_SIDE_N; return false; }
-    if (cc < 0) { side = ASX_SIDE_W; return false; }
-    if (cc >= cols) { side = ASX_SIDE_E; return false; }
-    return true;
-}
-
-__constant__ float kN1[6] = {1.0f, 0.5f, -0.5f, -1.0f, -0.5f, 0.5f};
-__constant__ float kN2[6] = {0.0f, kS32, kS32, 0.0f, -kS32, -kS32};
-
-// Block reduction of (max c, sum outflow, sum clamp) and the last-CTA step finish.
-template <int NT>
-__device__ __forceinline__ void reduce_and_finish(const StepArgs &a, float c, double outq,
-                                                  double clq)
-{
-    __shared__ unsigned s_max[NT / 32];
-    __shared__ double s_out[NT / 32], s_cl[NT / 32];
-    __shared__ bool s_last;
-    const int tid = threadIdx.x + threadIdx.y * blockDim.x;
-    const int lane = tid & 31, wid = tid >> 5;
-    unsigned bits = __float_as_uint(__fadd_rn(c, 0.0f));   // -0 -> +0; NaN keeps high bits
-    bits = __reduce_max_sync(0xffffffffu, bits);
-    if (__any_sync(0xffffffffu, outq != 0.0 || clq != 0.0)) {
-#pragma unroll
-        for (int o = 16; o > 0; o >>= 1) {
-            outq += __shfl_down_sync(0xffffffffu, outq, o);
-            clq += __shfl_down_sync(0xffffffffu, clq, o);
-        }
-    }
-    if (lane == 0) {
-        s_max[wid] = bits;
-        s_out[wid] = outq;
-        s_cl[wid] = clq;
-    }
-    __syncthreads();
-    if (tid == 0) {
-        unsigned mb = 0u;
-        double so = 0.0, sc = 0.0;
-        for (int w = 0; w < NT / 32; w++) {
-            mb = max(mb, s_max[w]);
-            so += s_out[w];
-            sc += s_cl[w];
-        }
-        DevCtl *ctl = a.ctl;
-        atomicMax(&ctl->cmax_bits, mb);
-        if (so != 0.0) atomicAdd(&ctl->out_acc, so);
-        if (sc != 0.0) atomicAdd(&ctl->clamp_acc, sc);
-        __threadfence();
-        const unsigned prev = atomicAdd(&ctl->done_ctas, 1u);
-        s_last = (prev == (unsigned)a.nblocks - 1u);
-        if (s_last) {
-            __threadfence();
-            finish_step(ctl);
-        }
-    }
-}
 
 // ------------------------------------------------------------ step: gather variant
 
@@ -280,17 +41,17 @@ __global__ void __launch_bounds__(kGX *kGY) step_gather_kernel(const StepArgs a)
     if (!ctl->active) return;
     const int par = ctl->parity;
     const float kappa = ctl->kappa, qr = ctl->qr, dtf = ctl->dtf;
+    const float kl2 = kappa * (0.5f * a.l), l4 = 0.25f * a.l, l2 = 0.5f * a.l;
     const float *mhi = a.mhi[par], *mlo = a.mlo[par], *v1 = a.v1[par], *v2 = a.v2[par];
     const int c = blockIdx.x * kGX + threadIdx.x;
     const int r = blockIdx.y * kGY + threadIdx.y;
-    float cw = 0.0f;
-    double outq = 0.0, clq = 0.0;
+    unsigned cb = 0u;
+    FF outd, clq;
     if (r < a.rows && c < a.cols) {
         const size_t k = (size_t)r * a.pitch + c;
         const Cell I = load_cell(a, mhi, v1, v2, k);
         float shi = I.m, slo = __ldg(mlo + k);
         float M1 = 0.0f, M2 = 0.0f;      // J_a + S_a
-        double outd = 0.0;               // booked exactly as applied (each q is a float)
 #pragma unroll
         for (int d = 0; d < 6; d++) {
             int rr, cc, side;
@@ -298,12 +59,12 @@ __global__ void __launch_bounds__(kGX *kGY) step_gather_kernel(const StepArgs a)
                 const Cell J = load_cell(a, mhi, v1, v2, (size_t)rr * a.pitch + cc);
                 float q, f1, f2, p1, p2;
                 switch (d) {
-                case 0: edge_terms<0>(I, J, a.l, kappa, a.cpe[0][0], a.cpe[0][1], q, f1, f2, p1, p2); break;
-                case 1: edge_terms<1>(I, J, a.l, kappa, a.cpe[1][0], a.cpe[1][1], q, f1, f2, p1, p2); break;
-                case 2: edge_terms<2>(I, J, a.l, kappa, a.cpe[2][0], a.cpe[2][1], q, f1, f2, p1, p2); break;
-                case 3: edge_terms<0>(J, I, a.l, kappa, a.cpe[0][0], a.cpe[0][1], q, f1, f2, p1, p2); break;
-                case 4: edge_terms<1>(J, I, a.l, kappa, a.cpe[1][0], a.cpe[1][1], q, f1, f2, p1, p2); break;
-                default: edge_terms<2>(J, I, a.l, kappa, a.cpe[2][0], a.cpe[2][1], q, f1, f2, p1, p2); break;
+                case 0: edge_terms<0>(I, J, kl2, l4, a.cpe[0][0], a.cpe[0][1], q, f1, f2, p1, p2); break;
+                case 1: edge_terms<1>(I, J, kl2, l4, a.cpe[1][0], a.cpe[1][1], q, f1, f2, p1, p2); break;
+                case 2: edge_terms<2>(I, J, kl2, l4, a.cpe[2][0], a.cpe[2][1], q, f1, f2, p1, p2); break;
+                case 3: edge_terms<0>(J, I, kl2, l4, a.cpe[0][0], a.cpe[0][1], q, f1, f2, p1, p2); break;
+                case 4: edge_terms<1>(J, I, kl2, l4, a.cpe[1][0], a.cpe[1][1], q, f1, f2, p1, p2); break;
+                default: edge_terms<2>(J, I, kl2, l4, a.cpe[2][0], a.cpe[2][1], q, f1, f2, p1, p2); break;
                 }
                 if (d < 3) {              // I is the lower cell: it loses q
                     acc_add(shi, slo, -q);
@@ -316,63 +77,34 @@ __global__ void __launch_bounds__(kGX *kGY) step_gather_kernel(const StepArgs a)
                 }
             } else {
                 const int pos = (side == ASX_SIDE_S || side == ASX_SIDE_N) ? c : r;
-                if (side_is_free(a, side, pos)) {
-                    // free discharge: ghost copy of the cell, outflow only
-                    const float vn = __fmaf_rn(I.v1, kN1[d], __fmul_rn(I.v2, kN2[d]));
-                    if (vn > 0.0f) {
-                        const float F = __fmul_rn(__fmul_rn(a.l, I.m), vn);
-                        const float q = __fmul_rn(kappa, F);
-                        acc_add(shi, slo, -q);
-                        M1 -= F * I.v1;
-                        M2 -= F * I.v2;
-                        outd += (double)q;
-                    }
-                }
+                if (side_is_free(a, side, pos))
+                    free_edge(I, d, kl2, l2, shi, slo, M1, M2, outd);
                 // wall: mirror ghost, the edge carries nothing
             }
         }
-        outq = outd;
-        // rain at t^{n+1}
-        acc_add(shi, slo, qr);
-        float hi, lo;
-        two_sum(shi, slo, hi, lo);
-        if (hi < 0.0f || (hi == 0.0f && lo < 0.0f)) {
-            clq = -((double)hi + (double)lo);
-            hi = 0.0f;
-            lo = 0.0f;
-        }
-        // momentum: gamma = theta h v + dt / sigma (J + S)
-        const float g1 = __fmaf_rn(kappa, M1, I.m * I.v1);
-        const float g2 = __fmaf_rn(kappa, M2, I.m * I.v2);
-        // implicit friction: v = 2 gamma / (alpha + sqrt(alpha^2 + 4 beta |gamma|))
-        float th, ka, kb;
+        float th, ka, kb, rth;
         if (a.cls) {
             const int cl = a.cls[k];
             th = a.cls_theta[cl];
+            rth = a.cls_rth[cl];
             ka = a.cls_a[cl];
             kb = a.cls_b[cl];
         } else {
             th = a.theta[k];
+            rth = fast_rcp(th);
             ka = a.alpha_p * (1.0f - th);
             kb = th * a.alpha_s;
         }
-        const float hn = __fdiv_rn(hi, th);
-        const float beta = dtf * __fmaf_rn(ka, hn, kb);
-        const float ng = hypotf(g1, g2);
-        const float den = hi + __fsqrt_rn(__fmaf_rn(hi, hi, 4.0f * beta * ng));
-        float w1 = 0.0f, w2 = 0.0f;
-        if (den > 0.0f) {
-            w1 = __fdiv_rn(2.0f * g1, den);
-            w2 = __fdiv_rn(2.0f * g2, den);
-        }
+        const CellNew o = cell_update(shi, slo, M1, M2, I.m, I.v1, I.v2, rth, ka, kb, kappa, qr, dtf,
+                                      a.g, clq);
         const int np = par ^ 1;
-        a.mhi[np][k] = hi;
-        a.mlo[np][k] = lo;
-        a.v1[np][k] = w1;
-        a.v2[np][k] = w2;
-        cw = wave_speed(w1, w2, hn, a.g);
+        a.mhi[np][k] = o.hi;
+        a.mlo[np][k] = o.lo;
+        a.v1[np][k] = o.v1;
+        a.v2[np][k] = o.v2;
+        cb = o.cbits;
     }
-    reduce_and_finish<kGX * kGY>(a, cw, outq, clq);
+    reduce_and_finish<kGX * kGY>(a, cb, outd.value(), clq.value());
 }
 
 // --------------------------------------------------------------- control kernels
@@ -402,22 +134,22 @@ __global__ void __launch_bounds__(kScanThreads) scan_kernel(const StepArgs a, do
     const float *mhi = a.mhi[par], *mlo = a.mlo[par], *v1 = a.v1[par], *v2 = a.v2[par];
     const long long n = (long long)a.rows * a.cols;
     double s = 0.0;
-    float cm = 0.0f;
+    unsigned cmb = 0u;
     for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n;
          i += (long long)gridDim.x * blockDim.x) {
         const int r = (int)(i / a.cols), c = (int)(i - (long long)r * a.cols);
         const size_t k = (size_t)r * a.pitch + c;
         const float hi = mhi[k];
         s += (double)hi + (double)mlo[k];
-        const float h = __fdiv_rn(hi, cell_theta(a, k));
-        cm = fmaxf(cm, wave_speed(v1[k], v2[k], h, a.g));
+        const float h = __fmul_rn(hi, cell_rtheta(a, k));
+        cmb = max(cmb, speed_bits(wave_speed(v1[k], v2[k], h, a.g)));
     }
     __shared__ double ss[kScanThreads / 32];
     __shared__ unsigned sm[kScanThreads / 32];
     __shared__ bool last;
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) s += __shfl_down_sync(0xffffffffu, s, o);
-    unsigned bits = __reduce_max_sync(0xffffffffu, __float_as_uint(__fadd_rn(cm, 0.0f)));
+    unsigned bits = __reduce_max_sync(0xffffffffu, cmb);
     if ((threadIdx.x & 31) == 0) {
         ss[threadIdx.x >> 5] = s;
         sm[threadIdx.x >> 5] = bits;
@@ -437,14 +169,15 @@ __global__ void __launch_bounds__(kScanThreads) scan_kernel(const StepArgs a, do
         if (last) {
             __threadfence();
             volatile double *vp = parts;
-            double tot = 0.0, cmx = 0.0;
+            double tot = 0.0;
+            unsigned cmx = 0u;
             for (unsigned b = 0; b < gridDim.x; b++) {
                 tot += vp[2 * b];
-                cmx = fmax(cmx, vp[2 * b + 1]);
+                cmx = max(cmx, speed_bits((float)vp[2 * b + 1]));
             }
             ctl->storage = tot * ctl->sigma;
             if (set_storage0) ctl->storage0 = ctl->storage;
-            ctl->cmax_cur = (float)cmx;
+            ctl->cmax_cur = __uint_as_float(cmx);
             if (!(ctl->cmax_cur <= FLT_MAX)) ctl->err |= kErrNumeric;
             ctl->scan_done = 0u;
         }

@@ -18,6 +18,61 @@ using namespace asx;
 namespace {
 
 constexpr int kGraphSteps = 32;   // step launches captured in one graph
+constexpr int kTileRowsDefault = 16;
+
+enum StepVariant { kVariantStrip = 0, kVariantGather = 1 };
+
+// Step kernel variant: ASX_STEP_KERNEL=gather selects the one-thread-per-cell gather
+// kernel; the default is the TMA strip kernel.  ASX_TILE_ROWS sets the strip tile height.
+int variant_from_env()
+{
+    const char *v = std::getenv("ASX_STEP_KERNEL");
+    if (v && std::strcmp(v, "gather") == 0) return kVariantGather;
+    return kVariantStrip;
+}
+
+int tile_rows_from_env()
+{
+    const char *v = std::getenv("ASX_TILE_ROWS");
+    int t = v ? std::atoi(v) : kTileRowsDefault;
+    if (t < 2) t = 2;
+    if (t > 1024) t = 1024;
+    return t;
+}
+
+typedef CUresult (*EncodeTiledFn)(CUtensorMap *, CUtensorMapDataType, cuuint32_t, void *,
+                                  const cuuint64_t *, const cuuint64_t *, const cuuint32_t *,
+                                  const cuuint32_t *, CUtensorMapInterleave, CUtensorMapSwizzle,
+                                  CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+
+EncodeTiledFn encode_fn()
+{
+    static EncodeTiledFn fn = nullptr;
+    if (!fn) {
+        void *p = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) ==
+                cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            fn = reinterpret_cast<EncodeTiledFn>(p);
+    }
+    return fn;
+}
+
+// 2-D tensor map over a pitched rows x cols plane; out-of-range elements read as zero.
+bool make_map(CUtensorMap *m, void *base, bool u8, int rows, int cols, int pitch, int box_x, int box_y)
+{
+    EncodeTiledFn enc = encode_fn();
+    if (!enc) return false;
+    const size_t es = u8 ? 1 : 4;
+    cuuint64_t dims[2] = {(cuuint64_t)cols, (cuuint64_t)rows};
+    cuuint64_t strides[1] = {(cuuint64_t)pitch * es};
+    cuuint32_t box[2] = {(cuuint32_t)box_x, (cuuint32_t)box_y};
+    cuuint32_t estr[2] = {1, 1};
+    return enc(m, u8 ? CU_TENSOR_MAP_DATA_TYPE_UINT8 : CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2, base, dims,
+               strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
+               CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+}
 
 // Leading part of DevCtl that the host reads after a call (the clock and flags).
 constexpr size_t kCtlHead = offsetof(DevCtl, cmax_bits);
@@ -36,6 +91,8 @@ struct asx_raster {
     double *scan_parts = nullptr;
     int scan_n = 0;
     StepArgs args{};
+    int variant = kVariantStrip;
+    StripMaps maps{};
     DevCtl host_ctl{};                  // parameter image (device copy is authoritative)
     DevCtl *mirror = nullptr;           // pinned host copies of the control head [2]
     bool have_params = false, have_fields = false;
@@ -113,6 +170,12 @@ void drop_graph(asx_raster *r)
     }
 }
 
+cudaError_t launch_step(asx_raster *r, cudaStream_t s)
+{
+    if (r->variant == kVariantGather) return launch_step_gather(r->args, s);
+    return launch_step_strip(r->args, r->maps, s);
+}
+
 asx_status build_graph(asx_raster *r)
 {
     if (r->graph) return ASX_OK;
@@ -123,7 +186,7 @@ asx_status build_graph(asx_raster *r)
     ASX_CUDA(r, cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking));
     cudaError_t e = cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal);
     if (e == cudaSuccess) {
-        for (int i = 0; i < kGraphSteps && e == cudaSuccess; i++) e = launch_step_gather(r->args, cs);
+        for (int i = 0; i < kGraphSteps && e == cudaSuccess; i++) e = launch_step(r, cs);
         cudaError_t e2 = cudaStreamEndCapture(cs, &g);
         if (e == cudaSuccess) e = e2;
     }
@@ -231,7 +294,10 @@ asx_status asx_create_raster(const asx_raster_desc *desc, asx_raster **out)
     a.rows = r->rows;
     a.cols = r->cols;
     a.pitch = r->pitch;
-    a.nblocks = step_gather_blocks(r->rows, r->cols);
+    r->variant = variant_from_env();
+    a.tile_rows = tile_rows_from_env();
+    a.nblocks = r->variant == kVariantGather ? step_gather_blocks(r->rows, r->cols)
+                                            : step_strip_blocks(r->rows, r->cols, a.tile_rows);
     const size_t pe = r->plane / sizeof(float);
     for (int p = 0; p < 2; p++) {
         a.mhi[p] = r->buf + (size_t)(4 * p + 0) * pe;
@@ -248,6 +314,25 @@ asx_status asx_create_raster(const asx_raster_desc *desc, asx_raster **out)
         a.fe[s] = desc->free_end[s];
     }
     a.ctl = r->ctl;
+    if (r->variant == kVariantStrip) {
+        bool ok = true;
+        const int bf = kStripW + 8;
+        for (int p = 0; p < 2; p++) {
+            ok = ok && make_map(&r->maps.mhi[p], a.mhi[p], false, r->rows, r->cols, r->pitch, bf, 2);
+            ok = ok && make_map(&r->maps.v1[p], a.v1[p], false, r->rows, r->cols, r->pitch, bf, 2);
+            ok = ok && make_map(&r->maps.v2[p], a.v2[p], false, r->rows, r->cols, r->pitch, bf, 2);
+            ok = ok && make_map(&r->maps.mlo[p], a.mlo[p], false, r->rows, r->cols, r->pitch, kStripW, 2);
+        }
+        ok = ok && make_map(&r->maps.z, (void *)a.z, false, r->rows, r->cols, r->pitch, bf, 2);
+        if (desc->n_classes > 0)
+            ok = ok && make_map(&r->maps.th, (void *)a.cls, true, r->rows, r->cols, r->pitch, kStripW + 32, 2);
+        else
+            ok = ok && make_map(&r->maps.th, (void *)a.theta, false, r->rows, r->cols, r->pitch, bf, 2);
+        if (!ok || step_strip_configure() != cudaSuccess) {
+            asx_destroy_raster(r);
+            return ASX_ECUDA;
+        }
+    }
     DevCtl &c = r->host_ctl;
     std::memset(&c, 0, sizeof(DevCtl));
     c.t_end = std::numeric_limits<double>::infinity();
@@ -311,6 +396,7 @@ asx_status asx_set_params(asx_raster *r, const asx_params *p)
             if (!(th > 0) || !(th <= 1) || !(ap >= 0) || !(as >= 0) || !std::isfinite(ap) || !std::isfinite(as))
                 return fail(r, ASX_EINVAL, "class table value out of range");
             a.cls_theta[k] = th;
+            a.cls_rth[k] = (float)(1.0 / (double)th);
             a.cls_a[k] = ap * (1.0f - th);
             a.cls_b[k] = th * as;
         }
@@ -421,14 +507,14 @@ asx_status asx_step(asx_raster *r, int n_steps, double *t_out)
     if (st) return st;
     ASX_CUDA(r, launch_prepare(r->ctl, kPrepSteps, 0.0, n_steps, r->stream));
     if (n_steps < kGraphSteps) {
-        for (int i = 0; i < n_steps; i++) ASX_CUDA(r, launch_step_gather(r->args, r->stream));
+        for (int i = 0; i < n_steps; i++) ASX_CUDA(r, launch_step(r, r->stream));
     } else {
         st = build_graph(r);
         if (st) return st;
         const int full = n_steps / kGraphSteps;
         for (int i = 0; i < full; i++) ASX_CUDA(r, cudaGraphLaunch(r->graph, r->stream));
         for (int i = 0; i < n_steps - full * kGraphSteps; i++)
-            ASX_CUDA(r, launch_step_gather(r->args, r->stream));
+            ASX_CUDA(r, launch_step(r, r->stream));
     }
     DevCtl *h;
     st = read_head(r, &h);

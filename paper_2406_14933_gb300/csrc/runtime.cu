@@ -18,7 +18,7 @@ using namespace asx;
 namespace {
 
 constexpr int kGraphSteps = 32;   // step launches captured in one graph
-constexpr int kTileRowsDefault = 16;
+constexpr int kTileRowsDefault = 32;
 
 enum StepVariant { kVariantStrip = 0, kVariantGather = 1 };
 
@@ -296,8 +296,8 @@ asx_status asx_create_raster(const asx_raster_desc *desc, asx_raster **out)
     a.pitch = r->pitch;
     r->variant = variant_from_env();
     a.tile_rows = tile_rows_from_env();
-    a.nblocks = r->variant == kVariantGather ? step_gather_blocks(r->rows, r->cols)
-                                            : step_strip_blocks(r->rows, r->cols, a.tile_rows);
+    if (r->variant == kVariantGather) a.nblocks = step_gather_blocks(r->rows, r->cols);
+    else step_strip_layout(a);
     const size_t pe = r->plane / sizeof(float);
     for (int p = 0; p < 2; p++) {
         a.mhi[p] = r->buf + (size_t)(4 * p + 0) * pe;
@@ -325,7 +325,7 @@ asx_status asx_create_raster(const asx_raster_desc *desc, asx_raster **out)
         }
         ok = ok && make_map(&r->maps.z, (void *)a.z, false, r->rows, r->cols, r->pitch, bf, 2);
         if (desc->n_classes > 0)
-            ok = ok && make_map(&r->maps.th, (void *)a.cls, true, r->rows, r->cols, r->pitch, kStripW + 32, 2);
+            ok = ok && make_map(&r->maps.th, (void *)a.cls, true, r->rows, r->cols, r->pitch, kStripW + 16, 2);
         else
             ok = ok && make_map(&r->maps.th, (void *)a.theta, false, r->rows, r->cols, r->pitch, bf, 2);
         if (!ok || step_strip_configure() != cudaSuccess) {

@@ -1,20 +1,28 @@
-// step_strip.cu -- the main step kernel: TMA-fed row marching over 128-column strips.
+// step_strip.cu -- the main step kernel: one warp marches down a 128-column tile fed by
+// TMA, four cells per lane.
 //
 // Same arithmetic as the gather kernel (Sec. 2.2, Eq. fvm_2D_eq_frac.07 in the form of
 // Appendix A), organised for GB300:
-//   * a CTA owns a tile of kStripW = 128 columns x H rows; 64 threads, two adjacent
-//     cells each;
-//   * the fields of rows r0-1 .. r0+H (one halo row above and below, four halo columns
-//     left and right) stream into a shared-memory ring of 2-row chunks with TMA tensor
-//     loads (cp.async.bulk.tensor.2d) completing on mbarriers; one thread refills a chunk
-//     as soon as every thread has finished with it;
-//   * the CTA marches down the tile one row per iteration; each edge is evaluated once,
-//     by the thread that owns its lower cell (E, NE, NW edges), and the terms destined for
-//     a cell of another thread are passed through shared memory; the depth h = m / theta
-//     of each row is computed once and shared the same way;
-//   * contributions to the row below are held in registers until that row is finished.
-// The mass increment of an edge is bit-identical to the gather kernel's (same canonical
-// edge function), so the water budget closes the same way.
+//   * a CTA is one warp and owns kSW = 128 columns x H rows; lane L owns the four
+//     adjacent cells at columns c0 + 4L .. c0 + 4L + 3;
+//   * rows r0-1 .. r0+H of every field (one halo row above and below, halo columns left
+//     and right) stream into a shared-memory ring of 2-row chunks through TMA tensor
+//     loads (cp.async.bulk.tensor.2d) that complete on mbarriers; lane 0 refills a chunk
+//     once the warp has moved past it;
+//   * the warp walks the tile row by row; the edges between row r and r+1 and the east
+//     edges of row r are evaluated by the lane that owns their lower cell; a lane also
+//     evaluates the one horizontal and one diagonal edge it shares with each neighbouring
+//     lane (the same canonical edge, so the same bits), which replaces every exchange of
+//     edge terms; neighbour cells come from warp shuffles, halo cells from the ring;
+//   * contributions to row r+1 stay in registers until that row is finished; no block
+//     barrier is needed;
+//   * tiles are laid out so that each tile with its halo lies inside the raster, which
+//     leaves no boundary edge in the tile code; the remaining cells along the raster
+//     sides (the frame) are processed in the same launch by frame CTAs that gather each
+//     cell's six neighbours (the same per-cell code as the gather kernel).
+// Both cells of an edge accumulate the mass increment of the same canonical edge
+// function, so opposite increments are bit-identical and the water budget closes to
+// float64 rounding.
 #include <cuda.h>
 
 #include "device_common.cuh"
@@ -24,13 +32,17 @@ namespace asx {
 namespace {
 
 constexpr int kSW = kStripW;           // tile width in cells
-constexpr int kST = kSW / 2;           // threads per CTA (two cells each)
 constexpr int kRB = 2;                 // rows per ring chunk
 constexpr int kNC = 3;                 // chunks in the ring
 constexpr int kBXF = kSW + 8;          // float box width (from column c0 - 4)
-constexpr int kBXC = kSW + 32;         // uint8 box width (from column c0 - 16)
+constexpr int kBXC = kSW + 16;         // uint8 box width (from column c0 - 4)
 constexpr int kXO = 4;                 // ring x index of column c0 (float fields)
-constexpr int kXOC = 16;               // ring x index of column c0 (class field)
+constexpr int kXOC = 4;                // ring x index of column c0 (class field)
+// TMA tiled loads must start on a 16-byte boundary: every tile column c0 is 4 mod 128,
+// so float boxes start at c0 - 4 (a multiple of 128 elements), the low-mass box at c0
+// (16 bytes past a multiple of 512), and the uint8 class box at c0 - 4 (a multiple of
+// 128 bytes).
+static_assert(kXOC == kXO && (kBXC % 16) == 0 && ((kBXF * 4) % 16) == 0, "TMA box alignment");
 
 struct __align__(128) FBox { float v[kRB][kBXF]; float pad[(1152 - kRB * kBXF * 4) / 4]; };
 struct __align__(128) LBox { float v[kRB][kSW]; };
@@ -43,9 +55,6 @@ static_assert(kRB * kBXC <= (int)sizeof(FBox), "class box fits the theta slot");
 
 struct StripSmem {
     Chunk ring[kNC];
-    float hrow[2][kBXF];               // depth of the rows j and j+1 (ring x indexing)
-    float eEq[kST], eE1[kST], eE2[kST];    // east edge terms for the next thread's cell a
-    float eDq[kST], eD1[kST], eD2[kST];    // diagonal edge terms for a neighbour thread
     unsigned long long bar[kNC];
 };
 
@@ -100,7 +109,7 @@ __device__ __forceinline__ bool mbar_wait_bounded(unsigned long long *bar, unsig
     return false;
 }
 
-// ----------------------------------------------------------------- the kernel
+// ----------------------------------------------------------------- cell helpers
 
 struct Acc {
     float hi, lo, m1, m2;    // compensated mass, momentum sums J + S
@@ -113,6 +122,18 @@ __device__ __forceinline__ void acc_in(Acc &A, float q, float u1, float u2)
     A.m2 += u2;
 }
 
+// Edge (X lower, Y upper) in direction D; adds its terms to ax if ux and to ay if uy
+// (a side not used belongs to another lane or is not updated by this tile).
+template <int D>
+__device__ __forceinline__ void edge(const StepArgs &a, const Cell &X, const Cell &Y, float kl2,
+                                     Acc &ax, bool ux, Acc &ay, bool uy)
+{
+    float q, f1, f2, p1, p2;
+    edge_terms<D>(X, Y, kl2, 0.25f * a.l, a.cpe[D][0], a.cpe[D][1], q, f1, f2, p1, p2);
+    if (ux) acc_in(ax, -q, p1 - f1, p2 - f2);
+    if (uy) acc_in(ay, q, p1 + f1, p2 + f2);
+}
+
 // Free-discharge contribution of a boundary edge of cell X in direction d (walls: none).
 __device__ __forceinline__ void bnd(const StepArgs &a, const Cell &X, int d, int side, int pos,
                                     float kl2, Acc &A, FF &outd)
@@ -120,351 +141,393 @@ __device__ __forceinline__ void bnd(const StepArgs &a, const Cell &X, int d, int
     if (side_is_free(a, side, pos)) free_edge(X, d, kl2, 0.5f * a.l, A.hi, A.lo, A.m1, A.m2, outd);
 }
 
-// Applies an interior edge (A lower, B upper) computed in direction D: the lower cell's
-// accumulator gets -q, P - F v; the upper's (returned) terms are q, P + F v.
-template <int D>
-__device__ __forceinline__ void edge(const StepArgs &a, const Cell &A, const Cell &B, float kl2,
-                                     Acc *accA, float &q, float &u1, float &u2)
+__device__ __forceinline__ Cell shfl_cell_up(const Cell &c)
 {
-    float f1, f2, p1, p2;
-    edge_terms<D>(A, B, kl2, 0.25f * a.l, a.cpe[D][0], a.cpe[D][1], q, f1, f2, p1, p2);
-    if (accA) acc_in(*accA, -q, p1 - f1, p2 - f2);
-    u1 = p1 + f1;
-    u2 = p2 + f2;
+    Cell o;
+    o.m = __shfl_up_sync(0xffffffffu, c.m, 1);
+    o.v1 = __shfl_up_sync(0xffffffffu, c.v1, 1);
+    o.v2 = __shfl_up_sync(0xffffffffu, c.v2, 1);
+    o.z = __shfl_up_sync(0xffffffffu, c.z, 1);
+    o.h = __shfl_up_sync(0xffffffffu, c.h, 1);
+    return o;
 }
 
-__device__ __forceinline__ Cell ring_cell(const Chunk &ch, int rr, int x, const float *hrow)
+__device__ __forceinline__ Cell shfl_cell_down(const Cell &c)
 {
-    Cell c;
-    c.m = ch.mhi.v[rr][x];
-    c.v1 = ch.v1.v[rr][x];
-    c.v2 = ch.v2.v[rr][x];
-    c.z = ch.z.v[rr][x];
-    c.h = hrow[x];
-    return c;
+    Cell o;
+    o.m = __shfl_down_sync(0xffffffffu, c.m, 1);
+    o.v1 = __shfl_down_sync(0xffffffffu, c.v1, 1);
+    o.v2 = __shfl_down_sync(0xffffffffu, c.v2, 1);
+    o.z = __shfl_down_sync(0xffffffffu, c.z, 1);
+    o.h = __shfl_down_sync(0xffffffffu, c.h, 1);
+    return o;
 }
 
-// 1 / theta of the ring cell at float index x (same value as cell_rtheta).
-__device__ __forceinline__ float ring_rtheta(const StepArgs &a, const Chunk &ch, int rr, int x)
+__device__ __forceinline__ Cell pick(bool take_b, const Cell &a, const Cell &b)
 {
-    if (a.cls) {
-        const uint8_t *cl = reinterpret_cast<const uint8_t *>(&ch.th.v[0][0]);
-        return a.cls_rth[cl[rr * kBXC + (x - kXO + kXOC)]];
+    Cell o;
+    o.m = take_b ? b.m : a.m;
+    o.v1 = take_b ? b.v1 : a.v1;
+    o.v2 = take_b ? b.v2 : a.v2;
+    o.z = take_b ? b.z : a.z;
+    o.h = take_b ? b.h : a.h;
+    return o;
+}
+
+// Per-lane state of one row: four cells, their 1/theta and friction coefficients, the
+// accumulators of their edge terms, and the halo cells at both ends of the tile row.
+struct Row {
+    Cell X[4];
+    float rt[4], ka[4], kb[4];
+    Acc A[4];
+    Cell hw, he;       // cells at columns c0 - 1 and c0 + kSW
+};
+
+// ----------------------------------------------------------------- the tile
+
+struct Tile {
+    const StepArgs &a;
+    StripSmem &S;
+    const StripMaps &maps;
+    int par, np, lane, c0, r0, Hn, nchunks;
+    float kappa, kl2, qr, dtf;
+    unsigned cwb = 0u;
+    FF outd, clq;
+    bool timed_out = false;
+    int n_issued = 0;
+
+    int jown;          // first local row this tile writes
+    bool lane_own;     // this lane's four columns are written by this tile
+
+    __device__ __forceinline__ Tile(const StepArgs &a_, StripSmem &S_, const StripMaps &m_, int c0_,
+                                    int r0_, int own_c, int own_r)
+        : a(a_), S(S_), maps(m_)
+    {
+        const DevCtl *ctl = a.ctl;
+        par = ctl->parity;
+        np = par ^ 1;
+        kappa = ctl->kappa;
+        qr = ctl->qr;
+        dtf = ctl->dtf;
+        kl2 = kappa * (0.5f * a.l);
+        lane = threadIdx.x;
+        c0 = c0_;
+        r0 = r0_;
+        Hn = a.tile_rows;
+        jown = 1 + (own_r - r0);
+        lane_own = c0 + 4 * lane >= own_c;
+        nchunks = (Hn + 2 + kRB - 1) / kRB;
     }
-    return fast_rcp(ch.th.v[rr][x]);
-}
 
-// One tile.  IN = the tile and its halo lie inside the raster (no boundary edge, every
-// cell valid): the boundary branches compile away.
-template <bool IN>
-__device__ __forceinline__ void strip_tile(const StepArgs &a, const StripMaps &maps, StripSmem &S,
-                                           int strip, int rblk)
-{
-    const DevCtl *ctl = a.ctl;
-    const int par = ctl->parity, np = par ^ 1;
-    const float kappa = ctl->kappa, qr = ctl->qr, dtf = ctl->dtf;
-    const float kl2 = kappa * (0.5f * a.l);
-    const int t = threadIdx.x;
-    const int H = a.tile_rows;
-    const int c0 = strip * kSW, r0 = rblk * H;
-    const int Hn = min(H, a.rows - r0);          // owned rows inside the raster
-    const int nrows = Hn + 2;                     // local rows 0 .. Hn+1
-    const int nchunks = (nrows + kRB - 1) / kRB;
-    const CUtensorMap *mp_mhi = &maps.mhi[par], *mp_v1 = &maps.v1[par], *mp_v2 = &maps.v2[par];
-    const CUtensorMap *mp_mlo = &maps.mlo[par];
-    const unsigned chunk_bytes = (unsigned)(4 * kRB * kBXF * 4 + kRB * kSW * 4) +
-                                 (unsigned)(a.cls ? kRB * kBXC : kRB * kBXF * 4);
+    __device__ __forceinline__ int col(int e) const { return c0 + 4 * lane + e; }
 
-    auto issue = [&](int k) {
+    __device__ __forceinline__ void issue(int k)
+    {
+        // refuse a misaligned tensor copy (it would stop the context): flag and skip;
+        // the waits then run out and the step reports ASX_ETIMEOUT
+        if (((c0 - kXO) & 15) != 0 || (c0 & 3) != 0) {
+            atomicOr(&a.ctl->err, kErrTimeout);
+            return;
+        }
         Chunk &ch = S.ring[k % kNC];
         unsigned long long *bar = &S.bar[k % kNC];
         const int y = r0 - 1 + k * kRB;
-        mbar_expect_tx(bar, chunk_bytes);
-        tma_load_2d(&ch.mhi.v[0][0], mp_mhi, c0 - kXO, y, bar);
-        tma_load_2d(&ch.v1.v[0][0], mp_v1, c0 - kXO, y, bar);
-        tma_load_2d(&ch.v2.v[0][0], mp_v2, c0 - kXO, y, bar);
+        const unsigned bytes = (unsigned)(4 * kRB * kBXF * 4 + kRB * kSW * 4) +
+                               (unsigned)(a.cls ? kRB * kBXC : kRB * kBXF * 4);
+        mbar_expect_tx(bar, bytes);
+        tma_load_2d(&ch.mhi.v[0][0], &maps.mhi[par], c0 - kXO, y, bar);
+        tma_load_2d(&ch.v1.v[0][0], &maps.v1[par], c0 - kXO, y, bar);
+        tma_load_2d(&ch.v2.v[0][0], &maps.v2[par], c0 - kXO, y, bar);
         tma_load_2d(&ch.z.v[0][0], &maps.z, c0 - kXO, y, bar);
         if (a.cls) tma_load_2d(&ch.th.v[0][0], &maps.th, c0 - kXOC, y, bar);
         else tma_load_2d(&ch.th.v[0][0], &maps.th, c0 - kXO, y, bar);
-        tma_load_2d(&ch.mlo.v[0][0], mp_mlo, c0, y, bar);
-    };
-
-    int n_issued = 0;                  // chunks issued (thread 0)
-    if (t == 0) {
-        for (int k = 0; k < kNC; k++) mbar_init(&S.bar[k], 1);
-        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
-        for (int k = 0; k < kNC && k < nchunks; k++) issue(k);
-        n_issued = min(kNC, nchunks);
+        tma_load_2d(&ch.mlo.v[0][0], &maps.mlo[par], c0, y, bar);
     }
-    __syncthreads();
 
-    const int ca = c0 + 2 * t, cb = ca + 1;
-    const bool va = IN || ca < a.cols, vb = IN || cb < a.cols;
-    const bool hasE = IN || cb + 1 < a.cols;      // b's east neighbour (r, cb+1) exists
-    const bool hasW = IN || ca > 0;               // a's west neighbour (r, ca-1) exists
-    const int xa = kXO + 2 * t, xb = xa + 1;
+    // Halo cell of ring row rr at float index x.
+    __device__ __forceinline__ Cell ring_cell(const Chunk &ch, int rr, int x) const
+    {
+        Cell c;
+        c.m = ch.mhi.v[rr][x];
+        c.v1 = ch.v1.v[rr][x];
+        c.v2 = ch.v2.v[rr][x];
+        c.z = ch.z.v[rr][x];
+        float rt;
+        if (a.cls) rt = a.cls_rth[reinterpret_cast<const uint8_t *>(&ch.th.v[0][0])[rr * kBXC + x - kXO + kXOC]];
+        else rt = fast_rcp(ch.th.v[rr][x]);
+        c.h = __fmul_rn(c.m, rt);
+        return c;
+    }
 
-    Cell A0{}, B0{}, A1{}, B1{};     // row j (cur) and row j+1 (nxt) cells a, b
-    float rtA0 = 1.f, rtB0 = 1.f, rtA1 = 1.f, rtB1 = 1.f;       // 1 / theta
-    float kaA0 = 0.f, kaB0 = 0.f, kaA1 = 0.f, kaB1 = 0.f;       // alpha_p (1 - theta)
-    float kbA0 = 0.f, kbB0 = 0.f, kbA1 = 0.f, kbB1 = 0.f;       // theta alpha_s
-    Acc cA{}, cB{}, nA{}, nB{};      // accumulators of row j and row j+1
-    unsigned cwb = 0u;               // max wave speed as float bits (NaN sorts above +Inf)
-    FF outd, clq;                    // boundary outflow and clamped water of this thread
-    bool timed_out = false;
-
-    // Loads local row jr (global r0 - 1 + jr) into (A1, B1), computes its depth into
-    // hrow[jr & 1] (halo columns by the edge threads) and starts its accumulators.
-    auto load_row = [&](int jr) {
+    // Loads local row jr (global r0 - 1 + jr) into R.
+    __device__ __forceinline__ void load(int jr, Row &R)
+    {
         const int k = jr / kRB, rr = jr % kRB;
-        if (rr == 0 || jr == 0) {
+        if (rr == 0) {
+            __syncwarp();
+            if (k >= 1 && lane == 0 && k - 1 + kNC < nchunks) {
+                // the warp is past chunk k-1: refill its slot
+                asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+                issue(k - 1 + kNC);
+                n_issued = k + kNC;
+            }
             if (!mbar_wait_bounded(&S.bar[k % kNC], (unsigned)((k / kNC) & 1))) timed_out = true;
         }
         const Chunk &ch = S.ring[k % kNC];
-        const int rg = r0 - 1 + jr;
-        const bool in = rg >= 0 && rg < a.rows;
-        float *hr = S.hrow[jr & 1];
-        const float2 m2 = *reinterpret_cast<const float2 *>(&ch.mhi.v[rr][xa]);
-        const float2 u2 = *reinterpret_cast<const float2 *>(&ch.v1.v[rr][xa]);
-        const float2 w2 = *reinterpret_cast<const float2 *>(&ch.v2.v[rr][xa]);
-        const float2 z2 = *reinterpret_cast<const float2 *>(&ch.z.v[rr][xa]);
-        A1.m = m2.x; B1.m = m2.y;
-        A1.v1 = u2.x; B1.v1 = u2.y;
-        A1.v2 = w2.x; B1.v2 = w2.y;
-        A1.z = z2.x; B1.z = z2.y;
+        const int x = kXO + 4 * lane;
+        const float4 m4 = *reinterpret_cast<const float4 *>(&ch.mhi.v[rr][x]);
+        const float4 u4 = *reinterpret_cast<const float4 *>(&ch.v1.v[rr][x]);
+        const float4 w4 = *reinterpret_cast<const float4 *>(&ch.v2.v[rr][x]);
+        const float4 z4 = *reinterpret_cast<const float4 *>(&ch.z.v[rr][x]);
+        const float4 l4 = *reinterpret_cast<const float4 *>(&ch.mlo.v[rr][4 * lane]);
+        const float mm[4] = {m4.x, m4.y, m4.z, m4.w}, uu[4] = {u4.x, u4.y, u4.z, u4.w};
+        const float ww[4] = {w4.x, w4.y, w4.z, w4.w}, zz[4] = {z4.x, z4.y, z4.z, z4.w};
+        const float ll[4] = {l4.x, l4.y, l4.z, l4.w};
         if (a.cls) {
-            const uint8_t *cl = reinterpret_cast<const uint8_t *>(&ch.th.v[0][0]) + rr * kBXC + kXOC + 2 * t;
-            const int ia = cl[0], ib = cl[1];
-            rtA1 = a.cls_rth[ia]; kaA1 = a.cls_a[ia]; kbA1 = a.cls_b[ia];
-            rtB1 = a.cls_rth[ib]; kaB1 = a.cls_a[ib]; kbB1 = a.cls_b[ib];
+            const uchar4 c4 = *reinterpret_cast<const uchar4 *>(
+                reinterpret_cast<const uint8_t *>(&ch.th.v[0][0]) + rr * kBXC + kXOC + 4 * lane);
+            const int cc[4] = {c4.x, c4.y, c4.z, c4.w};
+#pragma unroll
+            for (int e = 0; e < 4; e++) {
+                R.rt[e] = a.cls_rth[cc[e]];
+                R.ka[e] = a.cls_a[cc[e]];
+                R.kb[e] = a.cls_b[cc[e]];
+            }
         } else {
-            const float2 th2 = *reinterpret_cast<const float2 *>(&ch.th.v[rr][xa]);
-            rtA1 = fast_rcp(th2.x); kaA1 = a.alpha_p * (1.0f - th2.x); kbA1 = th2.x * a.alpha_s;
-            rtB1 = fast_rcp(th2.y); kaB1 = a.alpha_p * (1.0f - th2.y); kbB1 = th2.y * a.alpha_s;
+            const float4 t4 = *reinterpret_cast<const float4 *>(&ch.th.v[rr][x]);
+            const float tt[4] = {t4.x, t4.y, t4.z, t4.w};
+#pragma unroll
+            for (int e = 0; e < 4; e++) {
+                R.rt[e] = fast_rcp(tt[e]);
+                R.ka[e] = a.alpha_p * (1.0f - tt[e]);
+                R.kb[e] = tt[e] * a.alpha_s;
+            }
         }
-        A1.h = (IN || (in && va)) ? __fmul_rn(A1.m, rtA1) : 0.0f;
-        B1.h = (IN || (in && vb)) ? __fmul_rn(B1.m, rtB1) : 0.0f;
-        *reinterpret_cast<float2 *>(&hr[xa]) = make_float2(A1.h, B1.h);
-        if (t == 0) {
-            const int x = kXO - 1;
-            hr[x] = (IN || (in && c0 > 0)) ? __fmul_rn(ch.mhi.v[rr][x], ring_rtheta(a, ch, rr, x)) : 0.0f;
+#pragma unroll
+        for (int e = 0; e < 4; e++) {
+            R.X[e].m = mm[e];
+            R.X[e].v1 = uu[e];
+            R.X[e].v2 = ww[e];
+            R.X[e].z = zz[e];
+            R.X[e].h = __fmul_rn(mm[e], R.rt[e]);
+            R.A[e] = Acc{mm[e], ll[e], 0.0f, 0.0f};
         }
-        if (t == kST - 1) {
-            const int x = kXO + kSW;
-            hr[x] = (IN || (in && c0 + kSW < a.cols)) ? __fmul_rn(ch.mhi.v[rr][x], ring_rtheta(a, ch, rr, x)) : 0.0f;
-        }
-        const float2 lo2 = *reinterpret_cast<const float2 *>(&ch.mlo.v[rr][2 * t]);
-        nA = Acc{A1.m, lo2.x, 0.0f, 0.0f};
-        nB = Acc{B1.m, lo2.y, 0.0f, 0.0f};
-    };
+        R.hw = ring_cell(ch, rr, kXO - 1);
+        R.he = ring_cell(ch, rr, kXO + kSW);
+    }
 
-    load_row(0);
-    for (int j = 0; j <= Hn; j++) {
-        // rotate: row j becomes current
-        A0 = A1; B0 = B1;
-        rtA0 = rtA1; rtB0 = rtB1; kaA0 = kaA1; kaB0 = kaB1; kbA0 = kbA1; kbB0 = kbB1;
-        cA = nA; cB = nB;
-        load_row(j + 1);
-        if (__syncthreads_or(timed_out)) break;                    // S1
-        // refill the chunk every thread has finished with (rows j-2, j-1)
-        if (t == 0 && j >= 2 && (j % kRB) == 0) {
-            const int kd = j / kRB - 1;
-            if (kd + kNC < nchunks) {
-                asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-                issue(kd + kNC);
-                n_issued = kd + kNC + 1;
-            }
-        }
-        const int r = r0 - 1 + j;
-        const bool in_r = IN || (r >= 0 && r < a.rows);
-        const bool in_n = IN || (r + 1 >= 0 && r + 1 < a.rows);
-        const bool own = j >= 1 && in_r;
-        const bool nown = j + 1 <= Hn && in_n;
-        const int odd = r & 1;
-        const int kc = j / kRB, rc = j % kRB, kn = (j + 1) / kRB, rn = (j + 1) % kRB;
-        const Chunk &chc = S.ring[kc % kNC];
-        const Chunk &chn = S.ring[kn % kNC];
-        const float *hc = S.hrow[j & 1], *hn = S.hrow[(j + 1) & 1];
-        float pq = 0.f, p1 = 0.f, p2 = 0.f;       // published diagonal terms
-        float q, u1, u2;
-
+    // Edge terms between row j (C, global row r) and row j+1 (N), and the east edges of
+    // row r.  own: row r is updated by this tile; nown: row r+1 is.  ODD: parity of r.
+    template <int ODD>
+    __device__ __forceinline__ void edges(Row &C, Row &N, bool own, bool nown)
+    {
+        // neighbour cells held by the lanes to the west / east, or the halo at tile ends
+        const Cell Wc = pick(lane == 0, shfl_cell_up(C.X[3]), C.hw);
+        const Cell Ec = pick(lane == 31, shfl_cell_down(C.X[0]), C.he);
         if (own) {
-            // ---- horizontal edges of row r
-            if (va) {
-                if (vb) {
-                    edge<0>(a, A0, B0, kl2, &cA, q, u1, u2);
-                    acc_in(cB, q, u1, u2);
-                } else {
-                    bnd(a, A0, 0, ASX_SIDE_E, r, kl2, cA, outd);
-                }
-            }
-            if (vb) {
-                if (hasE) {
-                    const Cell E = ring_cell(chc, rc, xb + 1, hc);
-                    edge<0>(a, B0, E, kl2, &cB, q, u1, u2);
-                    S.eEq[t] = q; S.eE1[t] = u1; S.eE2[t] = u2;
-                } else {
-                    bnd(a, B0, 0, ASX_SIDE_E, r, kl2, cB, outd);
-                }
-            }
-            if (va) {
-                if (!hasW) {
-                    bnd(a, A0, 3, ASX_SIDE_W, r, kl2, cA, outd);
-                } else if (t == 0) {
-                    const Cell Wc = ring_cell(chc, rc, xa - 1, hc);
-                    edge<0>(a, Wc, A0, kl2, nullptr, q, u1, u2);
-                    acc_in(cA, q, u1, u2);
-                }
-            }
+            // ---- east edges of row r (the west edge of c_0 is the west lane's, again)
+            edge<0>(a, Wc, C.X[0], kl2, C.A[0], false, C.A[0], true);
+#pragma unroll
+            for (int e = 0; e < 3; e++) edge<0>(a, C.X[e], C.X[e + 1], kl2, C.A[e], true, C.A[e + 1], true);
+            edge<0>(a, C.X[3], Ec, kl2, C.A[3], true, C.A[3], false);
         }
-        if (own || nown) {
-            if (!IN && !in_r) {
-                // row r is above the raster: the lower edges of row r+1 lie on the S side
-                if (nown) {
-                    if (va) { bnd(a, A1, 4, ASX_SIDE_S, ca, kl2, nA, outd); bnd(a, A1, 5, ASX_SIDE_S, ca, kl2, nA, outd); }
-                    if (vb) { bnd(a, B1, 4, ASX_SIDE_S, cb, kl2, nB, outd); bnd(a, B1, 5, ASX_SIDE_S, cb, kl2, nB, outd); }
-                }
-            } else if (!IN && !in_n) {
-                // row r+1 is beyond the raster: the upper edges of row r lie on the N side
-                if (own) {
-                    if (va) { bnd(a, A0, 1, ASX_SIDE_N, ca, kl2, cA, outd); bnd(a, A0, 2, ASX_SIDE_N, ca, kl2, cA, outd); }
-                    if (vb) { bnd(a, B0, 1, ASX_SIDE_N, cb, kl2, cB, outd); bnd(a, B0, 2, ASX_SIDE_N, cb, kl2, cB, outd); }
-                }
-            } else if (!odd) {
-                // even r: NE(c) = (r+1, c), NW(c) = (r+1, c-1)
-                Acc *oA = own ? &cA : nullptr, *oB = own ? &cB : nullptr;
-                if (va) {
-                    edge<1>(a, A0, A1, kl2, oA, q, u1, u2);             // a -> nxt a
-                    if (nown) acc_in(nA, q, u1, u2);
-                    if (hasW) {                                             // a -> (r+1, ca-1)
-                        const Cell Bn = ring_cell(chn, rn, xa - 1, hn);
-                        edge<2>(a, A0, Bn, kl2, oA, pq, p1, p2);
-                    } else if (own) {
-                        bnd(a, A0, 2, ASX_SIDE_W, r, kl2, cA, outd);
-                    }
-                }
-                if (vb) {
-                    edge<1>(a, B0, B1, kl2, oB, q, u1, u2);             // b -> nxt b
-                    if (nown) acc_in(nB, q, u1, u2);
-                    edge<2>(a, B0, A1, kl2, oB, q, u1, u2);             // b -> nxt a
-                    if (nown) acc_in(nA, q, u1, u2);
-                } else if (va && nown) {
-                    // nxt a's SE neighbour (r, cb) is beyond the east side
-                    bnd(a, A1, 5, ASX_SIDE_E, r + 1, kl2, nA, outd);
-                }
-                // nxt b's SE neighbour (r, cb+1): the next thread's a, or beyond the raster
-                if (vb && nown && t == kST - 1) {
-                    if (hasE) {
-                        const Cell Ec = ring_cell(chc, rc, xb + 1, hc);
-                        edge<2>(a, Ec, B1, kl2, nullptr, q, u1, u2);
-                        acc_in(nB, q, u1, u2);
-                    }
-                }
-                if (!IN && vb && nown && !hasE) bnd(a, B1, 5, ASX_SIDE_E, r + 1, kl2, nB, outd);
-            } else {
-                // odd r: NE(c) = (r+1, c+1), NW(c) = (r+1, c)
-                Acc *oA = own ? &cA : nullptr, *oB = own ? &cB : nullptr;
-                if (va) {
-                    edge<2>(a, A0, A1, kl2, oA, q, u1, u2);             // a -> nxt a
-                    if (nown) acc_in(nA, q, u1, u2);
-                    if (vb) {
-                        edge<1>(a, A0, B1, kl2, oA, q, u1, u2);         // a -> nxt b
-                        if (nown) acc_in(nB, q, u1, u2);
-                    } else if (own) {
-                        bnd(a, A0, 1, ASX_SIDE_E, r, kl2, cA, outd);
-                    }
-                }
-                if (vb) {
-                    edge<2>(a, B0, B1, kl2, oB, q, u1, u2);             // b -> nxt b
-                    if (nown) acc_in(nB, q, u1, u2);
-                    if (hasE) {                                             // b -> (r+1, cb+1)
-                        const Cell Bn = ring_cell(chn, rn, xb + 1, hn);
-                        edge<1>(a, B0, Bn, kl2, oB, pq, p1, p2);
-                    } else if (own) {
-                        bnd(a, B0, 1, ASX_SIDE_E, r, kl2, cB, outd);
-                    }
-                }
-                // nxt a's SW neighbour (r, ca-1): the previous thread's b, or beyond the raster
-                if (va && nown) {
-                    if (!hasW) {
-                        bnd(a, A1, 4, ASX_SIDE_W, r + 1, kl2, nA, outd);
-                    } else if (t == 0) {
-                        const Cell Wc = ring_cell(chc, rc, xa - 1, hc);
-                        edge<1>(a, Wc, A1, kl2, nullptr, q, u1, u2);
-                        acc_in(nA, q, u1, u2);
-                    }
-                }
+        if (ODD) {
+            // odd r: NE(c) = (r+1, c+1), NW(c) = (r+1, c)
+            const Cell On = pick(lane == 31, shfl_cell_down(N.X[0]), N.he);   // (r+1, c_3 + 1)
+#pragma unroll
+            for (int e = 0; e < 4; e++) {
+                edge<2>(a, C.X[e], N.X[e], kl2, C.A[e], own, N.A[e], nown);        // NW
+                if (e < 3) edge<1>(a, C.X[e], N.X[e + 1], kl2, C.A[e], own, N.A[e + 1], nown);
+                else edge<1>(a, C.X[3], On, kl2, C.A[3], own, C.A[3], false);
             }
-        }
-        S.eDq[t] = pq; S.eD1[t] = p1; S.eD2[t] = p2;
-        __syncthreads();                                           // S2
-        if (own && va && hasW && t > 0) acc_in(cA, S.eEq[t - 1], S.eE1[t - 1], S.eE2[t - 1]);
-        if (nown && in_r) {
-            if (!odd) {
-                if (vb && hasE && t < kST - 1) acc_in(nB, S.eDq[t + 1], S.eD1[t + 1], S.eD2[t + 1]);
-            } else {
-                if (va && hasW && t > 0) acc_in(nA, S.eDq[t - 1], S.eD1[t - 1], S.eD2[t - 1]);
+            // SW edge of (r+1, c_0): the NE edge of (r, c_0 - 1)
+            edge<1>(a, Wc, N.X[0], kl2, N.A[0], false, N.A[0], nown);
+        } else {
+            // even r: NE(c) = (r+1, c), NW(c) = (r+1, c-1)
+            const Cell On = pick(lane == 0, shfl_cell_up(N.X[3]), N.hw);      // (r+1, c_0 - 1)
+#pragma unroll
+            for (int e = 0; e < 4; e++) {
+                edge<1>(a, C.X[e], N.X[e], kl2, C.A[e], own, N.A[e], nown);        // NE
+                if (e >= 1) edge<2>(a, C.X[e], N.X[e - 1], kl2, C.A[e], own, N.A[e - 1], nown);
+                else edge<2>(a, C.X[0], On, kl2, C.A[0], own, C.A[0], false);
             }
-        }
-        if (own) {
-            // ---- finish the two cells of row r
-            const size_t k0 = (size_t)r * a.pitch + ca;
-            if (vb) {
-                const CellNew oa = cell_update(cA.hi, cA.lo, cA.m1, cA.m2, A0.m, A0.v1, A0.v2, rtA0, kaA0,
-                                               kbA0, kappa, qr, dtf, a.g, clq);
-                const CellNew ob = cell_update(cB.hi, cB.lo, cB.m1, cB.m2, B0.m, B0.v1, B0.v2, rtB0, kaB0,
-                                               kbB0, kappa, qr, dtf, a.g, clq);
-                *reinterpret_cast<float2 *>(a.mhi[np] + k0) = make_float2(oa.hi, ob.hi);
-                *reinterpret_cast<float2 *>(a.mlo[np] + k0) = make_float2(oa.lo, ob.lo);
-                *reinterpret_cast<float2 *>(a.v1[np] + k0) = make_float2(oa.v1, ob.v1);
-                *reinterpret_cast<float2 *>(a.v2[np] + k0) = make_float2(oa.v2, ob.v2);
-                cwb = max(cwb, max(oa.cbits, ob.cbits));
-            } else if (va) {
-                const CellNew oa = cell_update(cA.hi, cA.lo, cA.m1, cA.m2, A0.m, A0.v1, A0.v2, rtA0, kaA0,
-                                               kbA0, kappa, qr, dtf, a.g, clq);
-                a.mhi[np][k0] = oa.hi;
-                a.mlo[np][k0] = oa.lo;
-                a.v1[np][k0] = oa.v1;
-                a.v2[np][k0] = oa.v2;
-                cwb = max(cwb, oa.cbits);
-            }
+            // SE edge of (r+1, c_3): the NW edge of (r, c_3 + 1)
+            edge<2>(a, Ec, N.X[3], kl2, N.A[3], false, N.A[3], nown);
         }
     }
-    if (__syncthreads_or(timed_out)) {
-        // a tensor copy did not arrive in time: flag the error, wait (bounded) for the
-        // copies still in flight, and leave without finishing the step
-        if (t == 0) {
-            atomicOr(&a.ctl->err, kErrTimeout);
-            for (int k = max(0, n_issued - kNC); k < n_issued; k++)
-                mbar_wait_bounded(&S.bar[k % kNC], (unsigned)((k / kNC) & 1));
+
+    // Finishes the cells of row r and writes them to the other state buffer.
+    __device__ __forceinline__ void finish(int r, Row &C)
+    {
+        CellNew o[4];
+        FF cl;
+#pragma unroll
+        for (int e = 0; e < 4; e++) {
+            o[e] = cell_update(C.A[e].hi, C.A[e].lo, C.A[e].m1, C.A[e].m2, C.X[e].m, C.X[e].v1, C.X[e].v2,
+                               C.rt[e], C.ka[e], C.kb[e], kappa, qr, dtf, a.g, cl);
         }
-        return;
+        if (!lane_own) return;       // columns written by the neighbouring tile
+        if (cl.hi != 0.0f || cl.lo != 0.0f) {
+            clq.add(cl.hi);
+            clq.add(cl.lo);
+        }
+        const size_t k0 = (size_t)r * a.pitch + col(0);
+        *reinterpret_cast<float4 *>(a.mhi[np] + k0) = make_float4(o[0].hi, o[1].hi, o[2].hi, o[3].hi);
+        *reinterpret_cast<float4 *>(a.mlo[np] + k0) = make_float4(o[0].lo, o[1].lo, o[2].lo, o[3].lo);
+        *reinterpret_cast<float4 *>(a.v1[np] + k0) = make_float4(o[0].v1, o[1].v1, o[2].v1, o[3].v1);
+        *reinterpret_cast<float4 *>(a.v2[np] + k0) = make_float4(o[0].v2, o[1].v2, o[2].v2, o[3].v2);
+#pragma unroll
+        for (int e = 0; e < 4; e++) cwb = max(cwb, o[e].cbits);
     }
-    reduce_and_finish<kST>(a, cwb, outd.value(), clq.value());
+
+    // One row step: load row j+1, evaluate the edges of row j, finish row j.
+    template <int ODD>
+    __device__ __forceinline__ void step_row(int j, Row &C, Row &N)
+    {
+        load(j + 1, N);
+        if (j + 1 < jown) return;           // rows above the ones this tile writes
+        const bool own = j >= jown, nown = j + 1 <= Hn;
+        edges<ODD>(C, N, own, nown);
+        if (own) finish(r0 - 1 + j, C);
+    }
+
+    __device__ void run()
+    {
+        if (lane == 0) {
+            for (int k = 0; k < kNC; k++) mbar_init(&S.bar[k], 1);
+            asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+            for (int k = 0; k < kNC && k < nchunks; k++) issue(k);
+            n_issued = min(kNC, nchunks);
+        }
+        __syncwarp();
+        Row R0, R1;
+        load(0, R0);
+        // rows alternate parity: local row j is global row r0 - 1 + j
+        int j = 0;
+        if ((r0 & 1) == 0) {
+            for (; j + 1 <= Hn; j += 2) {
+                step_row<1>(j, R0, R1);
+                if (__any_sync(0xffffffffu, timed_out)) return;
+                step_row<0>(j + 1, R1, R0);
+                if (__any_sync(0xffffffffu, timed_out)) return;
+            }
+            if (j == Hn) step_row<1>(j, R0, R1);
+        } else {
+            for (; j + 1 <= Hn; j += 2) {
+                step_row<0>(j, R0, R1);
+                if (__any_sync(0xffffffffu, timed_out)) return;
+                step_row<1>(j + 1, R1, R0);
+                if (__any_sync(0xffffffffu, timed_out)) return;
+            }
+            if (j == Hn) step_row<0>(j, R0, R1);
+        }
+    }
+};
+
+// Frame CTA: kFrameCells consecutive cells of the frame, one per lane per round.
+__device__ __forceinline__ void frame_cells(const StepArgs &a, long long f0, unsigned &cwb, FF &outd,
+                                            FF &clq)
+{
+    const StepScalars sc = step_scalars(a);
+    const int ry1 = a.rye, cx1 = a.cxe;
+    const int wcols = a.cx0 + (a.cols - cx1);     // frame columns of the interior rows
+    for (int i = threadIdx.x; i < kFrameCells; i += 32) {
+        const long long f = f0 + i;
+        if (f >= a.frame_n) break;
+        int r, c;
+        if (f < a.frame_a) {
+            const int ra = (int)(f / a.cols);
+            r = ra < a.ry0 ? ra : ry1 + (ra - a.ry0);
+            c = (int)(f - (long long)ra * a.cols);
+        } else {
+            const long long g = f - a.frame_a;
+            const int rb = (int)(g / wcols), cb = (int)(g - (long long)rb * wcols);
+            r = a.ry0 + rb;
+            c = cb < a.cx0 ? cb : cx1 + (cb - a.cx0);
+        }
+        gather_cell(a, sc, r, c, cwb, outd, clq);
+    }
 }
 
-__global__ void __launch_bounds__(kST, 8) step_strip_kernel(const StepArgs a, const __grid_constant__ StripMaps maps)
+__global__ void __launch_bounds__(32) step_strip_kernel(const StepArgs a, const __grid_constant__ StripMaps maps)
 {
     extern __shared__ __align__(128) unsigned char smem_raw[];
     // TMA destinations need 128-byte alignment: align the dynamic block by hand
     StripSmem &S = *reinterpret_cast<StripSmem *>(
         smem_raw + ((128u - (smem_u32(smem_raw) & 127u)) & 127u));
     if (!a.ctl->active) return;
-    const int nstrips = (a.cols + kSW - 1) / kSW;
-    const int strip = blockIdx.x % nstrips, rblk = blockIdx.x / nstrips;
-    const int c0 = strip * kSW, r0 = rblk * a.tile_rows;
-    const bool interior = c0 > 0 && c0 + kSW < a.cols && r0 > 0 && r0 + a.tile_rows < a.rows;
-    if (interior) strip_tile<true>(a, maps, S, strip, rblk);
-    else strip_tile<false>(a, maps, S, strip, rblk);
+    unsigned cwb = 0u;
+    double outq = 0.0, clq = 0.0;
+    if ((int)blockIdx.x < a.ntiles) {
+        const int ns = a.nstrips + (a.cx_last >= 0 ? 1 : 0);
+        const int strip = blockIdx.x % ns, rblk = blockIdx.x / ns;
+        const int c0 = strip < a.nstrips ? a.cx0 + strip * kSW : a.cx_last;
+        const int own_c = strip < a.nstrips ? c0 : a.cx0 + a.nstrips * kSW;
+        const int r0 = rblk < a.nrb ? a.ry0 + rblk * a.tile_rows : a.r_last;
+        const int own_r = rblk < a.nrb ? r0 : a.ry0 + a.nrb * a.tile_rows;
+        Tile T(a, S, maps, c0, r0, own_c, own_r);
+        T.run();
+        if (__any_sync(0xffffffffu, T.timed_out)) {
+            // a tensor copy did not arrive in time: flag the error, wait (bounded) for
+            // the copies still in flight, and leave without finishing the step
+            if (threadIdx.x == 0) {
+                atomicOr(&a.ctl->err, kErrTimeout);
+                for (int k = max(0, T.n_issued - kNC); k < T.n_issued; k++)
+                    mbar_wait_bounded(&S.bar[k % kNC], (unsigned)((k / kNC) & 1));
+            }
+            return;
+        }
+        cwb = T.cwb;
+        outq = T.outd.value();
+        clq = T.clq.value();
+    } else {
+        FF o, cl;
+        frame_cells(a, (long long)(blockIdx.x - a.ntiles) * kFrameCells, cwb, o, cl);
+        outq = o.value();
+        clq = cl.value();
+    }
+    reduce_and_finish<32>(a, cwb, outq, clq);
 }
 
 }  // namespace
 
 size_t step_strip_smem() { return sizeof(StripSmem) + 128; }
 
-int step_strip_blocks(int rows, int cols, int tile_rows)
+void step_strip_layout(StepArgs &a)
 {
-    return ((cols + kSW - 1) / kSW) * ((rows + tile_rows - 1) / tile_rows);
+    const int H = a.tile_rows;
+    // tiles start at column 4 (TMA boxes start 4 columns to the left, on a 16-byte
+    // boundary) and row 1, and their halo must end inside the raster
+    a.cx0 = 4;
+    a.nstrips = a.cols - 1 - a.cx0 >= kSW ? (a.cols - 1 - a.cx0) / kSW : 0;
+    a.ry0 = 1;
+    a.nrb = a.rows - 2 >= H ? (a.rows - 2) / H : 0;
+    if (a.nstrips == 0 || a.nrb == 0) a.nstrips = a.nrb = 0;
+    const int cx1 = a.cx0 + a.nstrips * kSW, ry1 = a.ry0 + a.nrb * H;
+    a.cx_last = -1;
+    a.cxe = cx1;
+    a.r_last = -1;
+    a.rye = ry1;
+    if (a.nstrips > 0) {
+        // last strip flush with the east side: start 4 mod 16, halo column inside
+        const int cl = ((a.cols - 1 - kSW - 4) / 16) * 16 + 4;
+        if (cl + kSW > cx1 && cl >= a.cx0) {
+            a.cx_last = cl;
+            a.cxe = cl + kSW;
+        }
+        const int rl = a.rows - 1 - H;
+        if (rl + H > ry1 && rl >= a.ry0) {
+            a.r_last = rl;
+            a.rye = rl + H;
+        }
+    }
+    a.ntiles = (a.nstrips + (a.cx_last >= 0 ? 1 : 0)) * (a.nrb + (a.r_last >= 0 ? 1 : 0));
+    if (a.nstrips == 0) a.ntiles = 0;
+    const long long n = (long long)a.rows * a.cols;
+    const long long inner = (long long)(a.rye - a.ry0) * (a.cxe - a.cx0);
+    a.frame_n = a.ntiles ? n - inner : n;
+    a.frame_a = a.ntiles ? (long long)(a.rows - (a.rye - a.ry0)) * a.cols : n;
+    a.nblocks = a.ntiles + (int)((a.frame_n + kFrameCells - 1) / kFrameCells);
 }
 
 cudaError_t step_strip_configure()
@@ -475,7 +538,7 @@ cudaError_t step_strip_configure()
 
 cudaError_t launch_step_strip(const StepArgs &a, const StripMaps &maps, cudaStream_t s)
 {
-    step_strip_kernel<<<a.nblocks, kST, step_strip_smem(), s>>>(a, maps);
+    step_strip_kernel<<<a.nblocks, 32, step_strip_smem(), s>>>(a, maps);
     return cudaGetLastError();
 }
 

@@ -181,7 +181,7 @@ def run_cuda(args):
     value = ws * n * args.steps / (ms / 1e3)
     peak, peak_kind = _peaks()
     achieved = BYTES_PER_CELL * n / (ms_step / 1e3) / 1e9
-    traffic = _read_traffic()
+    traffic = _read_traffic(n) if os.environ.get("ASX_STEP_KERNEL", "strip") == "strip" else None
     out = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True,
@@ -193,7 +193,8 @@ def run_cuda(args):
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                      "frac": achieved / peak, "traffic": traffic,
                      "peak_source": f"{peak_kind} copy bandwidth",
-                     "note": "32 B algorithmic per cell-update / (step time incl. launch gap)"},
+                     "note": "32 B algorithmic per cell-update / (step time incl. launch gap); "
+                             "traffic: ncu DRAM bytes of a 2048x2048 window scaled by cells"},
         "e2e": {"value": ws * n * args.steps / e2e_s, "unit": UNIT,
                 "h2d_bytes_per_step": 16 * n / args.steps, "d2h_bytes_per_step": 16 * n / args.steps},
         "gpu_launches": args.steps + 1,
@@ -205,12 +206,32 @@ def run_cuda(args):
     return out
 
 
-def _read_traffic():
-    """DRAM bytes per step launch from a committed ncu summary, if one matches."""
-    path = os.path.join(ROOT, "profiles", "traffic_per_launch.json")
+TRAFFIC_SOURCES = ("paper_2406_14933_gb300/csrc/step_strip.cu",
+                   "paper_2406_14933_gb300/csrc/device_common.cuh")
+
+
+def _read_traffic(n_cells):
+    """DRAM bytes (read + write) of one step launch, from the committed ncu summary of a
+    smaller window of the same workload, scaled by cells; None when the kernel sources
+    have changed since those counters were taken."""
+    import hashlib
+    path = os.path.join(ROOT, "profiles", "step_strip_kernel__traffic.txt")
     try:
+        rec = {}
         with open(path) as f:
-            return float(json.load(f)["bytes_per_launch"])
+            for line in f:
+                if line.startswith("#") or not line.strip():
+                    continue
+                k, v = line.split()
+                rec[k] = v
+        h = hashlib.sha256()
+        for src in TRAFFIC_SOURCES:
+            with open(os.path.join(ROOT, src), "rb") as f:
+                h.update(f.read())
+        if h.hexdigest() != rec["kernel_sources_sha256"]:
+            return None
+        per_cell = (float(rec["dram_bytes_read"]) + float(rec["dram_bytes_write"])) / float(rec["cells"])
+        return per_cell * n_cells
     except Exception:
         return None
 

@@ -183,6 +183,27 @@ asx_status asx_get_clock(asx_raster *r, int scenario, double *t, double *dt, lon
  * for r == NULL). */
 const char *asx_last_error(const asx_raster *r);
 
+/* Allocation-free scan of a state the caller holds (the paper has no counterpart; this
+ * serves callers that may not allocate device memory, e.g. a runtime that owns every
+ * buffer and forbids allocation once started, or a library that only lends pointers).
+ * It writes to *storage_out the water volume sum_i sigma (m_hi + m_lo)_i [m^3] (float64,
+ * fixed-order sum) and to *cmax_out the largest wave speed |v| + sqrt(g h), h = m_hi /
+ * theta, of the state; both outputs are device pointers and are written asynchronously
+ * on cuda_stream.  All arrays are device memory of the current device, rows x cols with
+ * a row pitch of `pitch` elements (>= cols); theta in (0, 1].
+ * No memory is allocated: the scratch (per-CTA partials and a completion counter) is a
+ * fixed 64 KB device array held by the library for as long as it is loaded, one copy
+ * per device.  Limit: at most 67,108,864 cells (4096 CTAs of 16,384 cells); larger
+ * rasters return ASX_EINVAL.  The first call on a device looks up the array's device
+ * address (cudaGetSymbolAddress); make that first call before any stream capture.  All
+ * calls on a device share the scratch, so calls that overlap on the GPU (on different
+ * streams, or from several threads) race: order them on one stream.
+ * Returns ASX_EINVAL on bad sizes or null pointers, ASX_ECUDA on a CUDA error. */
+asx_status asx_state_scan_noalloc(int rows, int cols, int pitch, double edge_m, double g,
+                                  const float *m_hi, const float *m_lo, const float *v1,
+                                  const float *v2, const float *theta, double *storage_out,
+                                  float *cmax_out, void *cuda_stream);
+
 #ifdef __cplusplus
 }
 #endif

@@ -75,6 +75,8 @@ _PROTOS = {
     "asx_get_clock": (C.c_int, [_RASTER, C.c_int, C.POINTER(C.c_double), C.POINTER(C.c_double),
                                 C.POINTER(C.c_longlong)]),
     "asx_last_error": (C.c_char_p, [_RASTER]),
+    "asx_state_scan_noalloc": (C.c_int, [C.c_int, C.c_int, C.c_int, C.c_double, C.c_double, _vp, _vp,
+                                         _vp, _vp, _vp, _vp, _vp, _vp]),
 }
 
 _lib = None
@@ -190,3 +192,12 @@ def asx_get_clock(r, scenario=0):
 
 def asx_last_error(r):
     return load().asx_last_error(r).decode()
+
+
+def asx_state_scan_noalloc(rows, cols, pitch, edge_m, g, m_hi, m_lo, v1, v2, theta, storage_out,
+                           cmax_out, cuda_stream=None):
+    """Allocation-free storage / wave-speed scan of a caller-held device state (see asx.h);
+    every pointer is a device address, the outputs are written asynchronously."""
+    _check(load().asx_state_scan_noalloc(int(rows), int(cols), int(pitch), float(edge_m), float(g),
+                                         _ptr(m_hi), _ptr(m_lo), _ptr(v1), _ptr(v2), _ptr(theta),
+                                         _ptr(storage_out), _ptr(cmax_out), cuda_stream))

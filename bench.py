@@ -203,6 +203,8 @@ def run_cuda(args):
     }
     if not args.no_cpu_baseline:
         out["cpu_baseline"] = cpu_baseline(sc, budget_s=args.cpu_budget)
+    if args.ens_scenarios > 0:
+        out["ensemble"] = run_ensemble(args, stream)
     return out
 
 
@@ -271,6 +273,50 @@ def cpu_baseline(sc, budget_s=15.0, crop=REF_CROP):
                       f"(5 mm film from t={T_WARM:.0f} s), {el:.1f} s, single thread"}
 
 
+def run_ensemble(args, stream):
+    """Batched ensemble of uneven hillslope scenarios: one persistent launch against one
+    launch per scenario per step (the single-raster path run scenario by scenario)."""
+    import torch
+    from paper_2406_14933_gb300 import inputs
+    from paper_2406_14933_gb300.ensemble import Ensemble
+    from paper_2406_14933_gb300.raster import Raster
+    n = args.ens_scenarios
+    scs = [inputs.ensemble_member(s, t_end=args.ens_t_end) for s in range(n)]
+    cells = sum(sc.n for sc in scs)
+    E = Ensemble(scs, stream=stream.cuda_stream)
+    tuning = E.autotune(max_steps=20)
+    E.run()                                   # warm-up (graph capture)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    e0.record(stream)
+    E.run()
+    e1.record(stream)
+    torch.cuda.synchronize()
+    t_ens = e0.elapsed_time(e1) / 1e3
+    steps = sum(E.clock(i)[1] for i in range(n))
+    cell_steps = sum(E.clock(i)[1] * scs[i].n for i in range(n))
+    E.close()
+    # one launch per scenario per step: each scenario as a single raster, in turn
+    rasters = [Raster(sc, stream=stream.cuda_stream) for sc in scs]
+    torch.cuda.synchronize()
+    e0.record(stream)
+    for R, sc in zip(rasters, scs):
+        R.run_until(sc.t_end)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    t_one = e0.elapsed_time(e1) / 1e3
+    for R in rasters:
+        R.close()
+    return {"workload": f"{n} hillslope scenarios, sides 128-512 log-uniform, {cells} cells, "
+                        f"{args.ens_t_end:.0f} s simulated each",
+            "scenarios_per_s": n / t_ens, "cell_updates_per_s": cell_steps / t_ens,
+            "steps_total": steps, "seconds": t_ens,
+            "tuning": {"cluster": tuning.cluster, "threads": tuning.threads,
+                       "cells_per_thread": tuning.cells_per_thread},
+            "one_launch_per_scenario": {"scenarios_per_s": n / t_one, "seconds": t_one},
+            "speedup": t_one / t_ens}
+
+
 def run_reference(args):
     ws, rank = _dist()
     if rank != 0:
@@ -323,6 +369,10 @@ def main():
     ap.add_argument("--cols", type=int, default=4096)
     ap.add_argument("--t-warm", type=float, default=T_WARM,
                     help="simulated time before the timed window [s]")
+    ap.add_argument("--ens-scenarios", type=int, default=256,
+                    help="scenarios of the ensemble section (0 = skip it)")
+    ap.add_argument("--ens-t-end", type=float, default=200.0,
+                    help="simulated time of each ensemble scenario [s]")
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)
     out = run_reference(args) if args.impl == "reference" else run_cuda(args)

@@ -183,6 +183,69 @@ asx_status asx_get_clock(asx_raster *r, int scenario, double *t, double *dt, lon
  * for r == NULL). */
 const char *asx_last_error(const asx_raster *r);
 
+/* ---------------------------------------------------------------- ensembles
+ * A batch of independent rasters ("scenarios") of uneven sizes advanced together: each
+ * with its own CFL time step, clock, ledger and hydrograph, all in one persistent kernel
+ * launch (captured in a CUDA graph) in which a thread-block cluster takes a scenario at a
+ * time from a queue (longest first).  The per-scenario step is the single-raster step
+ * (Eq. fvm_2D_eq_frac.07), so a scenario's state matches a single raster run bit for bit
+ * (per-cell porosity; the gather cell code).  Ensembles serve sweeps over coefficients,
+ * slopes and storms such as the sensitivity and calibration studies of Secs. 4.3-4.4. */
+typedef struct asx_ensemble asx_ensemble;
+
+/* One scenario: geometry, boundaries and parameters as in asx_raster_desc / asx_params
+ * (per-cell porosity, scalar alpha_s / alpha_p), a rain table of at most 8 points (host
+ * pointers, copied), the end time t_end [s] the scenario runs to, the hydrograph interval
+ * sample_dt and capacity max_samples, and max_steps (0 = no limit). */
+typedef struct {
+    int rows, cols;
+    double edge_m;
+    int bc[4], free_begin[4], free_end[4];
+    double g, cfl, dt_max, alpha_s, alpha_p;
+    int n_rain;
+    const double *rain_t, *rain_r;
+    double t_end, sample_dt;
+    int max_samples;
+    long long max_steps;
+} asx_scenario_desc;
+
+/* Launch shape of the ensemble kernel: CTAs per cluster (1, 2, 4, 8) sharing one
+ * scenario, threads per CTA (128, 256, 512), cells each thread updates per round
+ * (1, 2, 4). */
+typedef struct {
+    int cluster, threads, cells_per_thread;
+} asx_ensemble_tuning;
+
+/* Create an ensemble of n scenarios on `device`, work ordered on cuda_stream.  Allocates
+ * all device memory.  ASX_EINVAL on any description out of range. */
+asx_status asx_create_ensemble(int n, const asx_scenario_desc *descs, void *cuda_stream, int device,
+                               asx_ensemble **out);
+asx_status asx_destroy_ensemble(asx_ensemble *e);
+
+/* Static fields and initial state of scenario s (dense rows x cols float32; v1, v2 may be
+ * NULL = 0); the state is kept so that every run starts from it. */
+asx_status asx_ensemble_set_fields(asx_ensemble *e, int s, const float *z, const float *theta,
+                                   const float *h0, const float *v1, const float *v2, int ptr_kind);
+
+/* Times every launch shape on the ensemble with each scenario cut to max_steps steps and
+ * keeps the fastest for asx_ensemble_run; *best_out (may be NULL) receives it. */
+asx_status asx_ensemble_autotune(asx_ensemble *e, int max_steps, asx_ensemble_tuning *best_out);
+
+/* Runs every scenario from its initial state to its t_end in one persistent launch
+ * (tuning NULL = the autotuned or default shape).  ASX_ENUMERIC if a scenario's state
+ * became non-finite (that scenario stops; the others finish). */
+asx_status asx_ensemble_run(asx_ensemble *e, const asx_ensemble_tuning *tuning);
+
+/* Per-scenario results of the last run (see asx_ledger, asx_get_fields, asx_get_state,
+ * asx_get_hydrograph). */
+asx_status asx_ensemble_ledger(asx_ensemble *e, int s, asx_ledger *out);
+asx_status asx_ensemble_get_fields(asx_ensemble *e, int s, float *h, float *v1, float *v2, int ptr_kind);
+asx_status asx_ensemble_get_state(asx_ensemble *e, int s, float *m_hi, float *m_lo, float *v1, float *v2,
+                                  int ptr_kind);
+asx_status asx_ensemble_get_hydrograph(asx_ensemble *e, int s, double *q, int cap, int *n);
+asx_status asx_ensemble_get_clock(asx_ensemble *e, int s, double *t, long long *steps);
+const char *asx_ensemble_last_error(const asx_ensemble *e);
+
 /* Allocation-free scan of a state the caller holds (the paper has no counterpart; this
  * serves callers that may not allocate device memory, e.g. a runtime that owns every
  * buffer and forbids allocation once started, or a library that only lends pointers).

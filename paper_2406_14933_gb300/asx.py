@@ -55,8 +55,25 @@ class asx_ledger(C.Structure):
         return {k: getattr(self, k) for k, _ in self._fields_}
 
 
+class asx_scenario_desc(C.Structure):
+    _fields_ = [("rows", C.c_int), ("cols", C.c_int), ("edge_m", C.c_double), ("bc", C.c_int * 4),
+                ("free_begin", C.c_int * 4), ("free_end", C.c_int * 4), ("g", C.c_double),
+                ("cfl", C.c_double), ("dt_max", C.c_double), ("alpha_s", C.c_double),
+                ("alpha_p", C.c_double), ("n_rain", C.c_int), ("rain_t", C.POINTER(C.c_double)),
+                ("rain_r", C.POINTER(C.c_double)), ("t_end", C.c_double), ("sample_dt", C.c_double),
+                ("max_samples", C.c_int), ("max_steps", C.c_longlong)]
+
+
+class asx_ensemble_tuning(C.Structure):
+    _fields_ = [("cluster", C.c_int), ("threads", C.c_int), ("cells_per_thread", C.c_int)]
+
+    def as_tuple(self):
+        return (self.cluster, self.threads, self.cells_per_thread)
+
+
 _vp = C.c_void_p
 _RASTER = C.c_void_p
+_ENS = C.c_void_p
 
 # name: (restype, argtypes)
 _PROTOS = {
@@ -77,6 +94,17 @@ _PROTOS = {
     "asx_last_error": (C.c_char_p, [_RASTER]),
     "asx_state_scan_noalloc": (C.c_int, [C.c_int, C.c_int, C.c_int, C.c_double, C.c_double, _vp, _vp,
                                          _vp, _vp, _vp, _vp, _vp, _vp]),
+    "asx_create_ensemble": (C.c_int, [C.c_int, C.POINTER(asx_scenario_desc), _vp, C.c_int, C.POINTER(_ENS)]),
+    "asx_destroy_ensemble": (C.c_int, [_ENS]),
+    "asx_ensemble_set_fields": (C.c_int, [_ENS, C.c_int, _vp, _vp, _vp, _vp, _vp, C.c_int]),
+    "asx_ensemble_autotune": (C.c_int, [_ENS, C.c_int, C.POINTER(asx_ensemble_tuning)]),
+    "asx_ensemble_run": (C.c_int, [_ENS, C.POINTER(asx_ensemble_tuning)]),
+    "asx_ensemble_ledger": (C.c_int, [_ENS, C.c_int, C.POINTER(asx_ledger)]),
+    "asx_ensemble_get_fields": (C.c_int, [_ENS, C.c_int, _vp, _vp, _vp, C.c_int]),
+    "asx_ensemble_get_state": (C.c_int, [_ENS, C.c_int, _vp, _vp, _vp, _vp, C.c_int]),
+    "asx_ensemble_get_hydrograph": (C.c_int, [_ENS, C.c_int, _vp, C.c_int, C.POINTER(C.c_int)]),
+    "asx_ensemble_get_clock": (C.c_int, [_ENS, C.c_int, C.POINTER(C.c_double), C.POINTER(C.c_longlong)]),
+    "asx_ensemble_last_error": (C.c_char_p, [_ENS]),
 }
 
 _lib = None
@@ -201,3 +229,68 @@ def asx_state_scan_noalloc(rows, cols, pitch, edge_m, g, m_hi, m_lo, v1, v2, the
     _check(load().asx_state_scan_noalloc(int(rows), int(cols), int(pitch), float(edge_m), float(g),
                                          _ptr(m_hi), _ptr(m_lo), _ptr(v1), _ptr(v2), _ptr(theta),
                                          _ptr(storage_out), _ptr(cmax_out), cuda_stream))
+
+
+# ----------------------------------------------------------------- ensembles
+
+def _echeck(st, e=None):
+    if st != ASX_OK:
+        msg = load().asx_ensemble_last_error(e).decode() if e else ""
+        raise AsxError(st, msg)
+
+
+def asx_create_ensemble(descs, cuda_stream=None, device=0):
+    arr = (asx_scenario_desc * len(descs))(*descs)
+    e = _ENS()
+    _echeck(load().asx_create_ensemble(len(descs), arr, cuda_stream, int(device), C.byref(e)))
+    return e
+
+
+def asx_destroy_ensemble(e):
+    _echeck(load().asx_destroy_ensemble(e))
+
+
+def asx_ensemble_set_fields(e, s, z, theta, h0, v1, v2, ptr_kind):
+    _echeck(load().asx_ensemble_set_fields(e, int(s), _ptr(z), _ptr(theta), _ptr(h0), _ptr(v1), _ptr(v2),
+                                           ptr_kind), e)
+
+
+def asx_ensemble_autotune(e, max_steps):
+    t = asx_ensemble_tuning()
+    _echeck(load().asx_ensemble_autotune(e, int(max_steps), C.byref(t)), e)
+    return t
+
+
+def asx_ensemble_run(e, tuning=None):
+    _echeck(load().asx_ensemble_run(e, C.byref(tuning) if tuning is not None else None), e)
+
+
+def asx_ensemble_ledger(e, s):
+    led = asx_ledger()
+    _echeck(load().asx_ensemble_ledger(e, int(s), C.byref(led)), e)
+    return led
+
+
+def asx_ensemble_get_fields(e, s, h, v1, v2, ptr_kind):
+    _echeck(load().asx_ensemble_get_fields(e, int(s), _ptr(h), _ptr(v1), _ptr(v2), ptr_kind), e)
+
+
+def asx_ensemble_get_state(e, s, m_hi, m_lo, v1, v2, ptr_kind):
+    _echeck(load().asx_ensemble_get_state(e, int(s), _ptr(m_hi), _ptr(m_lo), _ptr(v1), _ptr(v2), ptr_kind), e)
+
+
+def asx_ensemble_get_hydrograph(e, s, cap):
+    q = np.zeros(max(int(cap), 1))
+    n = C.c_int()
+    _echeck(load().asx_ensemble_get_hydrograph(e, int(s), q.ctypes.data, int(cap), C.byref(n)), e)
+    return q[:min(n.value, int(cap))].copy(), n.value
+
+
+def asx_ensemble_get_clock(e, s):
+    t, k = C.c_double(), C.c_longlong()
+    _echeck(load().asx_ensemble_get_clock(e, int(s), C.byref(t), C.byref(k)), e)
+    return t.value, k.value
+
+
+def asx_ensemble_last_error(e):
+    return load().asx_ensemble_last_error(e).decode()

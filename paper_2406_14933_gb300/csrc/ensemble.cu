@@ -1,0 +1,807 @@
+// ensemble.cu -- batched ensembles of uneven rasters in one persistent kernel, its
+// autotuner, and the asx_ensemble_* C ABI.
+//
+// Each scenario is an independent raster with its own time step, clock, ledger and
+// hydrograph (the same step as a single raster: Sec. 2.2, Eq. fvm_2D_eq_frac.07 in the form
+// of Appendix A, with the CFL step of Eqs. fvm_2D_eq_frac.12-13).  The sensitivity and
+// calibration sweeps of Secs. 4.3-4.4 are ensembles of this kind.
+//
+// Kernel: a persistent grid of thread-block clusters.  A cluster takes the next scenario
+// from an atomic queue (scenarios sorted longest first) and runs it to its end time: per
+// step, the cluster's CTAs split the raster's rows, each updates its band with the gather
+// cell code, reduces max wave speed / outflow / clamped water, and after one hardware
+// cluster barrier every CTA reads all partials through distributed shared memory and
+// derives the same next time step.  No grid-wide synchronisation and no spin wait.
+#include <cooperative_groups.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstring>
+#include <limits>
+#include <new>
+#include <string>
+#include <vector>
+
+#include "device_common.cuh"
+
+namespace cg = cooperative_groups;
+
+namespace asx {
+
+constexpr int kEnsMaxRain = 8;
+constexpr int kEnsMaxCluster = 8;
+
+// Device table entry of one scenario: inputs (args, clock parameters) and results.
+struct EnsScenario {
+    StepArgs a;                       // geometry, state pointers, coefficients (a.ctl unused)
+    double t_end, cfl, dt_max, sigma, phi, sample_dt;
+    int n_rain, max_samples;
+    double rain_t[kEnsMaxRain], rain_r[kEnsMaxRain];
+    double *samples;                  // cumulative outflow at sample times
+    // results
+    double t, rain_in, outflow, clamped, storage0, storage;
+    long long steps, max_steps;
+    int n_samples, err, parity, pad;
+};
+
+struct EnsPartial {
+    unsigned cbits;
+    unsigned pad;
+    double out, cl, sto;
+};
+
+namespace {
+
+__device__ double ens_rain(const EnsScenario &s, double t)
+{
+    const int n = s.n_rain;
+    if (n <= 0) return 0.0;
+    if (t < s.rain_t[0] || t > s.rain_t[n - 1]) return 0.0;
+    if (n == 1) return s.rain_r[0];
+    for (int k = 0; k + 1 < n; k++) {
+        const double t0 = s.rain_t[k], t1 = s.rain_t[k + 1];
+        if (t <= t1) {
+            if (t1 == t0) return s.rain_r[k + 1];
+            return s.rain_r[k] + (s.rain_r[k + 1] - s.rain_r[k]) * (t - t0) / (t1 - t0);
+        }
+    }
+    return s.rain_r[n - 1];
+}
+
+// Clock of the scenario a CTA is running (identical in every CTA of the cluster).
+struct EnsClock {
+    double t, dt, t_next, rain_in, outflow, clamped, storage0, storage;
+    long long steps;
+    float cmax, kappa, qr, dtf;
+    int n_samples, parity, active, err;
+};
+
+// Next time step, as prepare_step does for a single raster.
+__device__ void ens_prepare(const EnsScenario &s, EnsClock &k)
+{
+    k.active = 0;
+    if (k.err) return;
+    if (!(k.t < s.t_end) || k.steps >= s.max_steps) return;
+    double dt = s.dt_max;
+    if (k.cmax > 0.0f) {
+        const double tau = s.cfl * s.phi / (double)k.cmax;
+        if (tau < dt) dt = tau;
+    }
+    double t_stop = s.t_end;
+    if (s.sample_dt > 0.0) {
+        const double ns = (double)(k.n_samples + 1) * s.sample_dt;
+        if (ns < t_stop) t_stop = ns;
+    }
+    double tn;
+    if (k.t + dt >= t_stop) {
+        dt = t_stop - k.t;
+        tn = t_stop;
+    } else {
+        tn = k.t + dt;
+    }
+    if (!(dt > 0.0)) {           // a zero or non-finite step cannot advance the clock
+        k.err |= kErrNumeric;
+        return;
+    }
+    k.dt = dt;
+    k.t_next = tn;
+    k.kappa = (float)(dt / s.sigma);
+    k.qr = (float)(dt * ens_rain(s, tn));
+    k.dtf = (float)dt;
+    k.active = 1;
+}
+
+template <int NT>
+__device__ __forceinline__ void block_reduce(unsigned &cb, double &out, double &cl, double &sto)
+{
+    __shared__ unsigned rb[NT / 32];
+    __shared__ double ro[NT / 32], rc[NT / 32], rs[NT / 32];
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    cb = __reduce_max_sync(0xffffffffu, cb);
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        out += __shfl_down_sync(0xffffffffu, out, o);
+        cl += __shfl_down_sync(0xffffffffu, cl, o);
+        sto += __shfl_down_sync(0xffffffffu, sto, o);
+    }
+    __syncthreads();
+    if (lane == 0) {
+        rb[wid] = cb;
+        ro[wid] = out;
+        rc[wid] = cl;
+        rs[wid] = sto;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        for (int w = 1; w < NT / 32; w++) {
+            cb = max(cb, rb[w]);
+            out += ro[w];
+            cl += rc[w];
+            sto += rs[w];
+        }
+    }
+}
+
+// The persistent ensemble kernel.  NT threads per CTA, K cells per thread per round.
+template <int NT, int K>
+__global__ void __launch_bounds__(NT) ensemble_kernel(EnsScenario *scen, const int *order, int n_scen,
+                                                     unsigned *queue)
+{
+    cg::cluster_group cluster = cg::this_cluster();
+    const unsigned rank = cluster.block_rank(), csize = cluster.num_blocks();
+    __shared__ StepArgs sa;
+    __shared__ EnsClock clk;
+    __shared__ EnsPartial part[2];
+    __shared__ int s_idx;
+    const int tid = threadIdx.x;
+    for (;;) {
+        // ---- take the next scenario (the cluster's rank 0 pops, all ranks read it)
+        if (rank == 0 && tid == 0) {
+            const unsigned q = atomicAdd(queue, 1u);
+            s_idx = q < (unsigned)n_scen ? order[q] : -1;
+        }
+        cluster.sync();
+        const int si = *cluster.map_shared_rank(&s_idx, 0);
+        cluster.sync();              // every rank has read s_idx before rank 0 pops again
+        if (si < 0) return;
+        EnsScenario &S = scen[si];
+        if (tid == 0) {
+            sa = S.a;
+            clk.t = 0.0;
+            clk.steps = 0;
+            clk.rain_in = clk.outflow = clk.clamped = 0.0;
+            clk.n_samples = 0;
+            clk.parity = 0;
+            clk.err = 0;
+        }
+        __syncthreads();
+        const int rows = sa.rows, cols = sa.cols;
+        const int rb0 = (int)(((long long)rows * rank) / csize);
+        const int rb1 = (int)(((long long)rows * (rank + 1)) / csize);
+        const int band = (rb1 - rb0) * cols;
+        // ---- initial scan: c_max and storage of the initial state
+        {
+            unsigned cb = 0u;
+            double out = 0.0, cl = 0.0, sto = 0.0;
+            for (int i = tid; i < band; i += NT) {
+                const int r = rb0 + i / cols, c = i % cols;
+                const size_t k = (size_t)r * sa.pitch + c;
+                const float hi = sa.mhi[0][k];
+                sto += (double)hi + (double)sa.mlo[0][k];
+                const float h = __fmul_rn(hi, cell_rtheta(sa, k));
+                cb = max(cb, speed_bits(wave_speed(sa.v1[0][k], sa.v2[0][k], h, sa.g)));
+            }
+            block_reduce<NT>(cb, out, cl, sto);
+            if (tid == 0) part[0] = EnsPartial{cb, 0u, 0.0, 0.0, sto};
+            cluster.sync();
+            if (tid == 0) {
+                unsigned cm = 0u;
+                double st = 0.0;
+                for (unsigned q = 0; q < csize; q++) {
+                    const EnsPartial p = *cluster.map_shared_rank(&part[0], q);
+                    cm = max(cm, p.cbits);
+                    st += p.sto;
+                }
+                clk.cmax = __uint_as_float(cm);
+                if (!(clk.cmax <= FLT_MAX)) clk.err |= kErrNumeric;
+                clk.storage0 = st * S.sigma;
+                ens_prepare(S, clk);
+            }
+            cluster.sync();          // part[0] is read by every rank before it is reused
+        }
+        __syncthreads();
+        // ---- time loop
+        while (clk.active) {
+            const int par = clk.parity;
+            StepScalars sc;
+            sc.par = par;
+            sc.kappa = clk.kappa;
+            sc.qr = clk.qr;
+            sc.dtf = clk.dtf;
+            sc.kl2 = sc.kappa * (0.5f * sa.l);
+            sc.l4 = 0.25f * sa.l;
+            sc.l2 = 0.5f * sa.l;
+            unsigned cb = 0u;
+            FF outd, clq;
+            for (int i0 = tid; i0 < band; i0 += NT * K) {
+#pragma unroll
+                for (int u = 0; u < K; u++) {
+                    const int i = i0 + u * NT;
+                    if (i < band) gather_cell(sa, sc, rb0 + i / cols, i % cols, cb, outd, clq);
+                }
+            }
+            double out = outd.value(), cl = clq.value(), sto = 0.0;
+            block_reduce<NT>(cb, out, cl, sto);
+            if (tid == 0) {
+                __threadfence();
+                part[par] = EnsPartial{cb, 0u, out, cl, 0.0};
+            }
+            cluster.sync();          // the band is written and the partials are in place
+            if (tid == 0) {
+                unsigned cm = 0u;
+                double o = 0.0, c = 0.0;
+                for (unsigned q = 0; q < csize; q++) {
+                    const EnsPartial p = *cluster.map_shared_rank(&part[par], q);
+                    cm = max(cm, p.cbits);
+                    o += p.out;
+                    c += p.cl;
+                }
+                clk.rain_in += S.sigma * (double)((long long)rows * cols) * (double)clk.qr;
+                clk.outflow += S.sigma * o;
+                clk.clamped += S.sigma * c;
+                clk.t = clk.t_next;
+                clk.steps += 1;
+                clk.parity ^= 1;
+                if (S.sample_dt > 0.0 && clk.t == (double)(clk.n_samples + 1) * S.sample_dt) {
+                    if (rank == 0 && clk.n_samples < S.max_samples) S.samples[clk.n_samples] = clk.outflow;
+                    clk.n_samples += 1;
+                }
+                clk.cmax = __uint_as_float(cm);
+                if (!(clk.cmax <= FLT_MAX)) clk.err |= kErrNumeric;
+                ens_prepare(S, clk);
+            }
+            __syncthreads();
+        }
+        // ---- final storage and results
+        {
+            const int par = clk.parity;
+            unsigned cb = 0u;
+            double out = 0.0, cl = 0.0, sto = 0.0;
+            for (int i = tid; i < band; i += NT) {
+                const int r = rb0 + i / cols, c = i % cols;
+                const size_t k = (size_t)r * sa.pitch + c;
+                sto += (double)sa.mhi[par][k] + (double)sa.mlo[par][k];
+            }
+            block_reduce<NT>(cb, out, cl, sto);
+            if (tid == 0) part[0] = EnsPartial{0u, 0u, 0.0, 0.0, sto};
+            cluster.sync();
+            if (rank == 0 && tid == 0) {
+                double st = 0.0;
+                for (unsigned q = 0; q < csize; q++) st += cluster.map_shared_rank(&part[0], q)->sto;
+                S.t = clk.t;
+                S.steps = clk.steps;
+                S.rain_in = clk.rain_in;
+                S.outflow = clk.outflow;
+                S.clamped = clk.clamped;
+                S.storage0 = clk.storage0;
+                S.storage = st * S.sigma;
+                S.n_samples = clk.n_samples;
+                S.err = clk.err;
+                S.parity = clk.parity;
+            }
+            cluster.sync();
+        }
+    }
+}
+
+using EnsKernel = void (*)(EnsScenario *, const int *, int, unsigned *);
+
+template <int NT, int K>
+EnsKernel ens_kernel_ptr()
+{
+    return ensemble_kernel<NT, K>;
+}
+
+EnsKernel ens_kernel(int nt, int k)
+{
+    if (nt == 256) return k == 1 ? ens_kernel_ptr<256, 1>() : k == 2 ? ens_kernel_ptr<256, 2>() : ens_kernel_ptr<256, 4>();
+    if (nt == 512) return k == 1 ? ens_kernel_ptr<512, 1>() : k == 2 ? ens_kernel_ptr<512, 2>() : ens_kernel_ptr<512, 4>();
+    return k == 1 ? ens_kernel_ptr<128, 1>() : k == 2 ? ens_kernel_ptr<128, 2>() : ens_kernel_ptr<128, 4>();
+}
+
+}  // namespace
+}  // namespace asx
+
+using namespace asx;
+
+// ------------------------------------------------------------------ host side
+
+struct asx_ensemble {
+    int n = 0, device = 0;
+    cudaStream_t stream = nullptr;
+    std::vector<asx_scenario_desc> desc;
+    std::vector<EnsScenario> host;          // parameter image of the device table
+    std::vector<size_t> plane_off;          // float offset of each scenario's planes
+    std::vector<int> pitch;
+    float *buf = nullptr;
+    double *samples = nullptr;
+    EnsScenario *dev = nullptr;
+    int *order = nullptr;
+    unsigned *queue = nullptr;
+    asx_ensemble_tuning tuning{};
+    bool tuned = false, have_fields_all = false;
+    std::vector<char> have_fields;
+    cudaGraphExec_t graph = nullptr;
+    asx_ensemble_tuning graph_tuning{};
+    std::string err;
+};
+
+namespace {
+
+asx_status efail(asx_ensemble *e, asx_status st, const std::string &m)
+{
+    if (e) e->err = m;
+    return st;
+}
+
+#define ENS_CUDA(e, call)                                                                      \
+    do {                                                                                       \
+        cudaError_t x_ = (call);                                                               \
+        if (x_ != cudaSuccess)                                                                 \
+            return efail((e), ASX_ECUDA, std::string(#call) + ": " + cudaGetErrorString(x_));   \
+    } while (0)
+
+bool tuning_valid(const asx_ensemble_tuning &t)
+{
+    const bool c = t.cluster == 1 || t.cluster == 2 || t.cluster == 4 || t.cluster == 8;
+    const bool n = t.threads == 128 || t.threads == 256 || t.threads == 512;
+    const bool k = t.cells_per_thread == 1 || t.cells_per_thread == 2 || t.cells_per_thread == 4;
+    return c && n && k;
+}
+
+// Clusters of this shape that fit on the device at once.
+int resident_clusters(const asx_ensemble_tuning &t)
+{
+    EnsKernel f = ens_kernel(t.threads, t.cells_per_thread);
+    cudaLaunchConfig_t cfg{};
+    cudaLaunchAttribute at[1];
+    at[0].id = cudaLaunchAttributeClusterDimension;
+    at[0].val.clusterDim.x = t.cluster;
+    at[0].val.clusterDim.y = 1;
+    at[0].val.clusterDim.z = 1;
+    cfg.gridDim = dim3(t.cluster);
+    cfg.blockDim = dim3(t.threads);
+    cfg.attrs = at;
+    cfg.numAttrs = 1;
+    int nc = 0;
+    if (cudaOccupancyMaxActiveClusters(&nc, (const void *)f, &cfg) != cudaSuccess || nc < 1) nc = 1;
+    return nc;
+}
+
+cudaError_t launch_ensemble(asx_ensemble *e, const asx_ensemble_tuning &t, cudaStream_t s)
+{
+    EnsKernel f = ens_kernel(t.threads, t.cells_per_thread);
+    const int nc = std::min(resident_clusters(t), e->n);
+    cudaLaunchConfig_t cfg{};
+    cudaLaunchAttribute at[1];
+    at[0].id = cudaLaunchAttributeClusterDimension;
+    at[0].val.clusterDim.x = t.cluster;
+    at[0].val.clusterDim.y = 1;
+    at[0].val.clusterDim.z = 1;
+    cfg.gridDim = dim3(nc * t.cluster);
+    cfg.blockDim = dim3(t.threads);
+    cfg.stream = s;
+    cfg.attrs = at;
+    cfg.numAttrs = 1;
+    cudaError_t x = cudaMemsetAsync(e->queue, 0, sizeof(unsigned), s);
+    if (x != cudaSuccess) return x;
+    return cudaLaunchKernelEx(&cfg, f, e->dev, (const int *)e->order, e->n, e->queue);
+}
+
+// Restores every scenario's initial state and clock (the state lives in parity 0 and a
+// copy of it in the spare planes at the end of the buffer).
+cudaError_t reset_state(asx_ensemble *e, cudaStream_t s)
+{
+    for (int i = 0; i < e->n; i++) {
+        EnsScenario &h = e->host[i];
+        const size_t plane = (size_t)h.a.rows * e->pitch[i] * sizeof(float);
+        const float *init = e->buf + e->plane_off[i] + 10 * (size_t)h.a.rows * e->pitch[i];
+        for (int f = 0; f < 4; f++) {
+            float *dst = f == 0 ? h.a.mhi[0] : f == 1 ? h.a.mlo[0] : f == 2 ? h.a.v1[0] : h.a.v2[0];
+            cudaError_t x = cudaMemcpyAsync(dst, init + f * plane / sizeof(float), plane, cudaMemcpyDeviceToDevice, s);
+            if (x != cudaSuccess) return x;
+        }
+    }
+    return cudaSuccess;
+}
+
+}  // namespace
+
+extern "C" {
+
+asx_status asx_create_ensemble(int n, const asx_scenario_desc *descs, void *cuda_stream, int device,
+                               asx_ensemble **out)
+{
+    if (!out || n < 1 || !descs) return ASX_EINVAL;
+    *out = nullptr;
+    for (int i = 0; i < n; i++) {
+        const asx_scenario_desc &d = descs[i];
+        if (d.rows < 2 || d.cols < 2 || (long long)d.rows * d.cols >= (1LL << 31) || !(d.edge_m > 0)) return ASX_EINVAL;
+        for (int s = 0; s < 4; s++)
+            if (d.bc[s] != ASX_BC_WALL && d.bc[s] != ASX_BC_FREE) return ASX_EINVAL;
+        if (!(d.g > 0) || !(d.cfl > 0) || !(d.cfl <= 1) || !(d.dt_max > 0) || !(d.alpha_s >= 0) || !(d.alpha_p >= 0))
+            return ASX_EINVAL;
+        if (d.n_rain < 0 || d.n_rain > kEnsMaxRain || (d.n_rain > 0 && (!d.rain_t || !d.rain_r))) return ASX_EINVAL;
+        if (!(d.t_end >= 0) || !std::isfinite(d.t_end) || !(d.sample_dt >= 0) || d.max_samples < 0) return ASX_EINVAL;
+    }
+    asx_ensemble *e = new (std::nothrow) asx_ensemble();
+    if (!e) return ASX_ENOMEM;
+    e->n = n;
+    e->device = device;
+    e->stream = (cudaStream_t)cuda_stream;
+    e->desc.assign(descs, descs + n);
+    e->have_fields.assign(n, 0);
+    if (cudaSetDevice(device) != cudaSuccess) { delete e; return ASX_ECUDA; }
+    // planes per scenario: 8 state (2 parities x m_hi, m_lo, v1, v2), z, theta, 4 initial
+    size_t total = 0, total_samples = 0;
+    e->plane_off.resize(n);
+    e->pitch.resize(n);
+    for (int i = 0; i < n; i++) {
+        e->pitch[i] = (descs[i].cols + kPitchAlign - 1) / kPitchAlign * kPitchAlign;
+        e->plane_off[i] = total;
+        total += 14 * (size_t)descs[i].rows * e->pitch[i];
+        total_samples += (size_t)std::max(descs[i].max_samples, 1);
+    }
+    cudaError_t x = cudaMalloc(&e->buf, total * sizeof(float));
+    if (x == cudaSuccess) x = cudaMalloc(&e->samples, total_samples * sizeof(double));
+    if (x == cudaSuccess) x = cudaMalloc(&e->dev, n * sizeof(EnsScenario));
+    if (x == cudaSuccess) x = cudaMalloc(&e->order, n * sizeof(int));
+    if (x == cudaSuccess) x = cudaMalloc(&e->queue, sizeof(unsigned));
+    if (x == cudaSuccess) x = cudaMemsetAsync(e->buf, 0, total * sizeof(float), e->stream);
+    if (x != cudaSuccess) {
+        asx_destroy_ensemble(e);
+        return x == cudaErrorMemoryAllocation ? ASX_ENOMEM : ASX_ECUDA;
+    }
+    e->host.resize(n);
+    size_t soff = 0;
+    std::vector<int> ord(n);
+    for (int i = 0; i < n; i++) {
+        const asx_scenario_desc &d = descs[i];
+        EnsScenario &h = e->host[i];
+        std::memset(&h, 0, sizeof(h));
+        StepArgs &a = h.a;
+        const size_t pe = (size_t)d.rows * e->pitch[i];
+        float *b = e->buf + e->plane_off[i];
+        a.rows = d.rows;
+        a.cols = d.cols;
+        a.pitch = e->pitch[i];
+        for (int p = 0; p < 2; p++) {
+            a.mhi[p] = b + (4 * p + 0) * pe;
+            a.mlo[p] = b + (4 * p + 1) * pe;
+            a.v1[p] = b + (4 * p + 2) * pe;
+            a.v2[p] = b + (4 * p + 3) * pe;
+        }
+        a.z = b + 8 * pe;
+        a.theta = b + 9 * pe;
+        a.cls = nullptr;
+        a.alpha_s = (float)d.alpha_s;
+        a.alpha_p = (float)d.alpha_p;
+        a.l = (float)d.edge_m;
+        a.g = (float)d.g;
+        const double s3 = std::sqrt(3.0) / 2.0;
+        const double n1[3] = {1.0, 0.5, -0.5}, n2[3] = {0.0, s3, s3};
+        for (int k = 0; k < 3; k++) {
+            a.cpe[k][0] = (float)(-0.5 * d.edge_m * d.g * n1[k]);
+            a.cpe[k][1] = (float)(-0.5 * d.edge_m * d.g * n2[k]);
+        }
+        for (int s = 0; s < 4; s++) {
+            a.bc[s] = d.bc[s];
+            a.fb[s] = d.free_begin[s];
+            a.fe[s] = d.free_end[s];
+        }
+        h.t_end = d.t_end;
+        h.cfl = d.cfl;
+        h.dt_max = d.dt_max;
+        h.sigma = 1.5 * std::sqrt(3.0) * d.edge_m * d.edge_m;
+        h.phi = h.sigma / (6.0 * d.edge_m);
+        h.sample_dt = d.sample_dt;
+        h.n_rain = d.n_rain;
+        for (int k = 0; k < d.n_rain; k++) {
+            h.rain_t[k] = d.rain_t[k];
+            h.rain_r[k] = d.rain_r[k];
+        }
+        h.max_samples = d.max_samples;
+        h.samples = e->samples + soff;
+        soff += (size_t)std::max(d.max_samples, 1);
+        h.max_steps = d.max_steps > 0 ? d.max_steps : (1LL << 62);
+        ord[i] = i;
+    }
+    // longest first: cells x expected steps ~ cells x t_end / cell size
+    std::sort(ord.begin(), ord.end(), [&](int p, int q) {
+        const double wp = (double)descs[p].rows * descs[p].cols * descs[p].t_end / descs[p].edge_m;
+        const double wq = (double)descs[q].rows * descs[q].cols * descs[q].t_end / descs[q].edge_m;
+        return wp > wq;
+    });
+    x = cudaMemcpyAsync(e->order, ord.data(), n * sizeof(int), cudaMemcpyHostToDevice, e->stream);
+    if (x == cudaSuccess)
+        x = cudaMemcpyAsync(e->dev, e->host.data(), n * sizeof(EnsScenario), cudaMemcpyHostToDevice, e->stream);
+    if (x == cudaSuccess) x = cudaStreamSynchronize(e->stream);
+    if (x != cudaSuccess) {
+        asx_destroy_ensemble(e);
+        return ASX_ECUDA;
+    }
+    e->tuning = asx_ensemble_tuning{4, 256, 2};
+    *out = e;
+    return ASX_OK;
+}
+
+asx_status asx_destroy_ensemble(asx_ensemble *e)
+{
+    if (!e) return ASX_OK;
+    cudaSetDevice(e->device);
+    if (e->stream) cudaStreamSynchronize(e->stream);
+    if (e->graph) cudaGraphExecDestroy(e->graph);
+    cudaFree(e->buf);
+    cudaFree(e->samples);
+    cudaFree(e->dev);
+    cudaFree(e->order);
+    cudaFree(e->queue);
+    delete e;
+    return ASX_OK;
+}
+
+const char *asx_ensemble_last_error(const asx_ensemble *e)
+{
+    return e ? e->err.c_str() : "null ensemble handle";
+}
+
+asx_status asx_ensemble_set_fields(asx_ensemble *e, int s, const float *z, const float *theta,
+                                   const float *h0, const float *v1, const float *v2, int kind)
+{
+    if (!e) return ASX_EINVAL;
+    if (s < 0 || s >= e->n) return efail(e, ASX_EINVAL, "scenario out of range");
+    if (!z || !theta || !h0) return efail(e, ASX_EINVAL, "z, theta and h0 are required");
+    if (kind != ASX_PTR_HOST && kind != ASX_PTR_DEVICE) return efail(e, ASX_EINVAL, "bad ptr_kind");
+    const asx_scenario_desc &d = e->desc[s];
+    const size_t n = (size_t)d.rows * d.cols;
+    if (kind == ASX_PTR_HOST) {
+        for (size_t i = 0; i < n; i++) {
+            if (!std::isfinite(z[i]) || !(theta[i] > 0.0f) || !(theta[i] <= 1.0f) || !(h0[i] >= 0.0f) ||
+                !std::isfinite(h0[i]) || (v1 && !std::isfinite(v1[i])) || (v2 && !std::isfinite(v2[i])))
+                return efail(e, ASX_EINVAL, "field value out of range");
+        }
+    }
+    ENS_CUDA(e, cudaSetDevice(e->device));
+    const int pitch = e->pitch[s];
+    const cudaMemcpyKind mk = kind == ASX_PTR_HOST ? cudaMemcpyHostToDevice : cudaMemcpyDeviceToDevice;
+    auto put = [&](void *dst, const void *src) {
+        return cudaMemcpy2DAsync(dst, (size_t)pitch * 4, src, (size_t)d.cols * 4, (size_t)d.cols * 4, d.rows, mk,
+                                 e->stream);
+    };
+    EnsScenario &h = e->host[s];
+    StepArgs &a = h.a;
+    ENS_CUDA(e, put((void *)a.z, z));
+    ENS_CUDA(e, put((void *)a.theta, theta));
+    ENS_CUDA(e, put(a.mhi[1], h0));
+    if (v1) ENS_CUDA(e, put(a.v1[1], v1));
+    else ENS_CUDA(e, cudaMemsetAsync(a.v1[1], 0, (size_t)d.rows * pitch * 4, e->stream));
+    if (v2) ENS_CUDA(e, put(a.v2[1], v2));
+    else ENS_CUDA(e, cudaMemsetAsync(a.v2[1], 0, (size_t)d.rows * pitch * 4, e->stream));
+    ENS_CUDA(e, launch_init_state(a, 0, a.mhi[1], a.v1[1], a.v2[1], e->stream));
+    // keep a copy of the initial state for repeated runs
+    const size_t plane = (size_t)d.rows * pitch;
+    float *init = e->buf + e->plane_off[s] + 10 * plane;
+    ENS_CUDA(e, cudaMemcpyAsync(init, a.mhi[0], plane * 4, cudaMemcpyDeviceToDevice, e->stream));
+    ENS_CUDA(e, cudaMemcpyAsync(init + plane, a.mlo[0], plane * 4, cudaMemcpyDeviceToDevice, e->stream));
+    ENS_CUDA(e, cudaMemcpyAsync(init + 2 * plane, a.v1[0], plane * 4, cudaMemcpyDeviceToDevice, e->stream));
+    ENS_CUDA(e, cudaMemcpyAsync(init + 3 * plane, a.v2[0], plane * 4, cudaMemcpyDeviceToDevice, e->stream));
+    ENS_CUDA(e, cudaStreamSynchronize(e->stream));
+    e->have_fields[s] = 1;
+    e->have_fields_all = std::all_of(e->have_fields.begin(), e->have_fields.end(), [](char c) { return c != 0; });
+    return ASX_OK;
+}
+
+asx_status asx_ensemble_run(asx_ensemble *e, const asx_ensemble_tuning *tuning)
+{
+    if (!e) return ASX_EINVAL;
+    if (!e->have_fields_all) return efail(e, ASX_ESTATE, "asx_ensemble_set_fields missing for a scenario");
+    const asx_ensemble_tuning t = tuning ? *tuning : e->tuning;
+    if (!tuning_valid(t)) return efail(e, ASX_EINVAL, "tuning out of range");
+    ENS_CUDA(e, cudaSetDevice(e->device));
+    ENS_CUDA(e, reset_state(e, e->stream));
+    // one persistent launch, captured once per tuning in a CUDA graph and replayed
+    if (!e->graph || std::memcmp(&e->graph_tuning, &t, sizeof(t)) != 0) {
+        if (e->graph) {
+            cudaGraphExecDestroy(e->graph);
+            e->graph = nullptr;
+        }
+        cudaStream_t cs;
+        ENS_CUDA(e, cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking));
+        cudaGraph_t g = nullptr;
+        cudaError_t x = cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal);
+        if (x == cudaSuccess) {
+            x = launch_ensemble(e, t, cs);
+            cudaError_t x2 = cudaStreamEndCapture(cs, &g);
+            if (x == cudaSuccess) x = x2;
+        }
+        if (x == cudaSuccess) x = cudaGraphInstantiate(&e->graph, g, 0);
+        if (g) cudaGraphDestroy(g);
+        cudaStreamDestroy(cs);
+        if (x != cudaSuccess) {
+            e->graph = nullptr;
+            return efail(e, ASX_ECUDA, std::string("ensemble graph: ") + cudaGetErrorString(x));
+        }
+        e->graph_tuning = t;
+    }
+    ENS_CUDA(e, cudaGraphLaunch(e->graph, e->stream));
+    ENS_CUDA(e, cudaStreamSynchronize(e->stream));
+    // read back the results
+    std::vector<EnsScenario> res(e->n);
+    ENS_CUDA(e, cudaMemcpy(res.data(), e->dev, e->n * sizeof(EnsScenario), cudaMemcpyDeviceToHost));
+    bool bad = false;
+    for (int i = 0; i < e->n; i++) {
+        EnsScenario &h = e->host[i];
+        h.t = res[i].t;
+        h.steps = res[i].steps;
+        h.rain_in = res[i].rain_in;
+        h.outflow = res[i].outflow;
+        h.clamped = res[i].clamped;
+        h.storage0 = res[i].storage0;
+        h.storage = res[i].storage;
+        h.n_samples = res[i].n_samples;
+        h.err = res[i].err;
+        h.parity = res[i].parity;
+        if (h.err) bad = true;
+    }
+    if (bad) return efail(e, ASX_ENUMERIC, "a scenario's state became non-finite");
+    return ASX_OK;
+}
+
+asx_status asx_ensemble_autotune(asx_ensemble *e, int max_steps, asx_ensemble_tuning *best_out)
+{
+    if (!e || max_steps < 1) return ASX_EINVAL;
+    if (!e->have_fields_all) return efail(e, ASX_ESTATE, "asx_ensemble_set_fields missing for a scenario");
+    ENS_CUDA(e, cudaSetDevice(e->device));
+    // time every candidate on the whole ensemble with each scenario capped at max_steps
+    std::vector<long long> saved(e->n);
+    for (int i = 0; i < e->n; i++) {
+        saved[i] = e->host[i].max_steps;
+        e->host[i].max_steps = max_steps;
+    }
+    ENS_CUDA(e, cudaMemcpy(e->dev, e->host.data(), e->n * sizeof(EnsScenario), cudaMemcpyHostToDevice));
+    cudaEvent_t a, b;
+    ENS_CUDA(e, cudaEventCreate(&a));
+    ENS_CUDA(e, cudaEventCreate(&b));
+    float best_ms = std::numeric_limits<float>::infinity();
+    asx_ensemble_tuning best = e->tuning;
+    const int cl[4] = {1, 2, 4, 8}, nt[3] = {128, 256, 512}, kk[3] = {1, 2, 4};
+    asx_status st = ASX_OK;
+    for (int ci = 0; ci < 4 && st == ASX_OK; ci++)
+        for (int ti = 0; ti < 3 && st == ASX_OK; ti++)
+            for (int ki = 0; ki < 3 && st == ASX_OK; ki++) {
+                const asx_ensemble_tuning t{cl[ci], nt[ti], kk[ki]};
+                float ms = 0.0f;
+                cudaError_t x = reset_state(e, e->stream);
+                if (x == cudaSuccess) x = cudaEventRecord(a, e->stream);
+                if (x == cudaSuccess) x = launch_ensemble(e, t, e->stream);
+                if (x == cudaSuccess) x = cudaEventRecord(b, e->stream);
+                if (x == cudaSuccess) x = cudaEventSynchronize(b);
+                if (x == cudaSuccess) x = cudaEventElapsedTime(&ms, a, b);
+                if (x != cudaSuccess) {
+                    st = efail(e, ASX_ECUDA, std::string("autotune: ") + cudaGetErrorString(x));
+                    break;
+                }
+                if (ms < best_ms) {
+                    best_ms = ms;
+                    best = t;
+                }
+            }
+    cudaEventDestroy(a);
+    cudaEventDestroy(b);
+    for (int i = 0; i < e->n; i++) e->host[i].max_steps = saved[i];
+    ENS_CUDA(e, cudaMemcpy(e->dev, e->host.data(), e->n * sizeof(EnsScenario), cudaMemcpyHostToDevice));
+    if (st) return st;
+    e->tuning = best;
+    e->tuned = true;
+    if (best_out) *best_out = best;
+    return ASX_OK;
+}
+
+asx_status asx_ensemble_ledger(asx_ensemble *e, int s, asx_ledger *out)
+{
+    if (!e || !out) return ASX_EINVAL;
+    if (s < 0 || s >= e->n) return efail(e, ASX_EINVAL, "scenario out of range");
+    const EnsScenario &h = e->host[s];
+    out->rain_in = h.rain_in;
+    out->outflow = h.outflow;
+    out->storage = h.storage;
+    out->storage0 = h.storage0;
+    out->clamped = h.clamped;
+    out->steps = h.steps;
+    const double scale = std::fmax(h.rain_in, h.storage0);
+    const double d = std::fabs(h.storage0 + h.rain_in + h.clamped - h.outflow - h.storage);
+    out->defect_rel = scale > 0 ? d / scale : 0.0;
+    return ASX_OK;
+}
+
+asx_status asx_ensemble_get_fields(asx_ensemble *e, int s, float *h_out, float *v1, float *v2, int kind)
+{
+    if (!e) return ASX_EINVAL;
+    if (s < 0 || s >= e->n) return efail(e, ASX_EINVAL, "scenario out of range");
+    if (kind != ASX_PTR_HOST && kind != ASX_PTR_DEVICE) return efail(e, ASX_EINVAL, "bad ptr_kind");
+    ENS_CUDA(e, cudaSetDevice(e->device));
+    const asx_scenario_desc &d = e->desc[s];
+    const EnsScenario &h = e->host[s];
+    const int par = h.parity, np = par ^ 1;
+    const cudaMemcpyKind mk = kind == ASX_PTR_HOST ? cudaMemcpyDeviceToHost : cudaMemcpyDeviceToDevice;
+    const int pitch = e->pitch[s];
+    auto get = [&](void *dst, const void *src) {
+        return cudaMemcpy2DAsync(dst, (size_t)d.cols * 4, src, (size_t)pitch * 4, (size_t)d.cols * 4, d.rows, mk,
+                                 e->stream);
+    };
+    if (h_out) {
+        ENS_CUDA(e, launch_extract_depth(h.a, par, h.a.mhi[np], e->stream));
+        ENS_CUDA(e, get(h_out, h.a.mhi[np]));
+    }
+    if (v1) ENS_CUDA(e, get(v1, h.a.v1[par]));
+    if (v2) ENS_CUDA(e, get(v2, h.a.v2[par]));
+    ENS_CUDA(e, cudaStreamSynchronize(e->stream));
+    return ASX_OK;
+}
+
+asx_status asx_ensemble_get_state(asx_ensemble *e, int s, float *m_hi, float *m_lo, float *v1, float *v2,
+                                  int kind)
+{
+    if (!e) return ASX_EINVAL;
+    if (s < 0 || s >= e->n) return efail(e, ASX_EINVAL, "scenario out of range");
+    if (kind != ASX_PTR_HOST && kind != ASX_PTR_DEVICE) return efail(e, ASX_EINVAL, "bad ptr_kind");
+    ENS_CUDA(e, cudaSetDevice(e->device));
+    const asx_scenario_desc &d = e->desc[s];
+    const EnsScenario &h = e->host[s];
+    const int par = h.parity;
+    const cudaMemcpyKind mk = kind == ASX_PTR_HOST ? cudaMemcpyDeviceToHost : cudaMemcpyDeviceToDevice;
+    const int pitch = e->pitch[s];
+    auto get = [&](void *dst, const void *src) {
+        return cudaMemcpy2DAsync(dst, (size_t)d.cols * 4, src, (size_t)pitch * 4, (size_t)d.cols * 4, d.rows, mk,
+                                 e->stream);
+    };
+    if (m_hi) ENS_CUDA(e, get(m_hi, h.a.mhi[par]));
+    if (m_lo) ENS_CUDA(e, get(m_lo, h.a.mlo[par]));
+    if (v1) ENS_CUDA(e, get(v1, h.a.v1[par]));
+    if (v2) ENS_CUDA(e, get(v2, h.a.v2[par]));
+    ENS_CUDA(e, cudaStreamSynchronize(e->stream));
+    return ASX_OK;
+}
+
+asx_status asx_ensemble_get_hydrograph(asx_ensemble *e, int s, double *q, int cap, int *n)
+{
+    if (!e || !n || cap < 0 || (cap > 0 && !q)) return efail(e, ASX_EINVAL, "bad argument");
+    if (s < 0 || s >= e->n) return efail(e, ASX_EINVAL, "scenario out of range");
+    ENS_CUDA(e, cudaSetDevice(e->device));
+    const EnsScenario &h = e->host[s];
+    *n = h.n_samples;
+    const int m = std::min(h.n_samples, h.max_samples);
+    const int k = std::min(m, cap);
+    if (k > 0) {
+        std::vector<double> cum(k);
+        ENS_CUDA(e, cudaMemcpy(cum.data(), h.samples, k * sizeof(double), cudaMemcpyDeviceToHost));
+        double prev = 0.0;
+        const double sdt = h.sample_dt > 0 ? h.sample_dt : 1.0;
+        for (int i = 0; i < k; i++) {
+            q[i] = (cum[i] - prev) / sdt;
+            prev = cum[i];
+        }
+    }
+    return ASX_OK;
+}
+
+asx_status asx_ensemble_get_clock(asx_ensemble *e, int s, double *t, long long *steps)
+{
+    if (!e) return ASX_EINVAL;
+    if (s < 0 || s >= e->n) return efail(e, ASX_EINVAL, "scenario out of range");
+    if (t) *t = e->host[s].t;
+    if (steps) *steps = e->host[s].steps;
+    return ASX_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,97 @@
+"""The batched ensemble (one persistent launch, per-scenario clocks) against single
+rasters and the oracle."""
+import numpy as np
+import pytest
+
+from paper_2406_14933_gb300 import inputs
+
+pytestmark = pytest.mark.gpu
+
+SIZES = [40, 57, 90, 131, 200, 33]
+
+
+def _scenarios(t_end=120.0, sample_dt=10.0):
+    out = []
+    for i, n in enumerate(SIZES):
+        sc = inputs.ensemble_member(i, n_override=n, t_end=t_end)
+        sc.sample_dt = sample_dt
+        out.append(sc)
+    return out
+
+
+def _rel_l2(a, b):
+    a, b = np.asarray(a, np.float64).ravel(), np.asarray(b, np.float64).ravel()
+    nb = np.linalg.norm(b)
+    return np.linalg.norm(a - b) / (nb if nb > 0 else 1.0)
+
+
+def test_ensemble_matches_single_rasters_bitwise(asx, monkeypatch):
+    """Each scenario of the ensemble reaches the same state, bit for bit, as the same
+    raster run alone with the gather kernel (same per-cell code, same time steps)."""
+    from paper_2406_14933_gb300.ensemble import Ensemble
+    from paper_2406_14933_gb300.raster import Raster
+    monkeypatch.setenv("ASX_STEP_KERNEL", "gather")
+    scs = _scenarios()
+    E = Ensemble(scs)
+    E.run()
+    for i, sc in enumerate(scs):
+        R = Raster(sc)
+        t = R.run_until(sc.t_end)
+        te, ke = E.clock(i)
+        assert te == t == sc.t_end
+        assert ke == R.clock()[2]
+        for a, b in zip(E.state(i), R.state()):
+            assert np.array_equal(a, b)
+        le, lr = E.ledger(i), R.ledger()
+        assert le.rain_in == pytest.approx(lr.rain_in, rel=1e-12)
+        assert le.outflow == pytest.approx(lr.outflow, rel=1e-12, abs=1e-12)
+        assert le.storage == pytest.approx(lr.storage, rel=1e-12)
+        assert le.defect_rel <= 1e-10
+        qe, qr = E.hydrograph(i), R.hydrograph()
+        assert len(qe) == len(qr) == 12
+        assert np.allclose(qe, qr, rtol=1e-10, atol=1e-14)
+        R.close()
+    E.close()
+
+
+@pytest.mark.parametrize("tuning", [(1, 128, 1), (2, 256, 4), (8, 512, 2)])
+def test_ensemble_launch_shapes_agree(asx, tuning):
+    """Cluster size, threads and cells per thread change who computes a cell, not what:
+    the states are identical for every launch shape."""
+    from paper_2406_14933_gb300.ensemble import Ensemble
+    scs = _scenarios(t_end=60.0)
+    E = Ensemble(scs)
+    E.run((4, 256, 2))
+    ref = [E.state(i) for i in range(len(scs))]
+    E.run(tuning)
+    for i in range(len(scs)):
+        for a, b in zip(E.state(i), ref[i]):
+            assert np.array_equal(a, b)
+    E.close()
+
+
+def test_ensemble_autotune_and_oracle(asx, orc):
+    """The autotuner returns a valid launch shape; two scenarios match the FP64 oracle
+    (own time steps on both sides) to the stated tolerance and close their budgets."""
+    from paper_2406_14933_gb300.ensemble import Ensemble
+    scs = _scenarios(t_end=90.0)
+    E = Ensemble(scs)
+    t = E.autotune(max_steps=20)
+    assert t.cluster in (1, 2, 4, 8) and t.threads in (128, 256, 512) and t.cells_per_thread in (1, 2, 4)
+    E.run()
+    for i in (1, 4):
+        sc = scs[i]
+        p = orc.from_scenario(sc)
+        # the same sample times cut the steps on both sides
+        res = p.run(p.mass(sc.h0), sc.v1_0, sc.v2_0, 0.0, sc.t_end, sample_dt=sc.sample_dt,
+                    sample_cap=100)
+        mh, ml, v1, v2 = E.state(i)
+        mg = mh.astype(np.float64) + ml
+        assert _rel_l2(p.depth(mg.ravel()), p.depth(res["m"])) <= 1e-4
+        qo = np.concatenate([res["m"] * res["v1"], res["m"] * res["v2"]])
+        qg = np.concatenate([mg.ravel() * v1.ravel(), mg.ravel() * v2.ravel()])
+        assert _rel_l2(qg, qo) <= 1e-4
+        assert E.ledger(i).defect_rel <= 1e-10
+        qh = np.diff(np.concatenate([[0.0], res["samples"]])) / sc.sample_dt
+        assert _rel_l2(E.hydrograph(i), qh) <= 1e-4
+    E.close()

@@ -246,6 +246,51 @@ asx_status asx_ensemble_get_hydrograph(asx_ensemble *e, int s, double *q, int ca
 asx_status asx_ensemble_get_clock(asx_ensemble *e, int s, double *t, long long *steps);
 const char *asx_ensemble_last_error(const asx_ensemble *e);
 
+/* ---------------------------------------------------------------- the surrogate's GEMM
+ * D[M x N] = A[M x K] . B[N x K]^T on the tensor cores (tcgen05, BF16 inputs, FP32
+ * accumulation in tensor memory): the product the surrogate MLP is made of (not in the
+ * paper; the learned hydrograph surrogate is this library's addition).  A(m, k) =
+ * A[m*sam + k*sak] and B(n, k) = B[n*sbn + k*sbk] are BF16 device arrays read through
+ * these element strides; D is FP32, row stride ldd >= N.  Asynchronous on cuda_stream.
+ * ASX_EINVAL on non-positive sizes, null pointers or ldd < N. */
+asx_status asx_gemm_bf16(int M, int N, int K, const void *A, long long sam, long long sak, const void *B,
+                         long long sbn, long long sbk, float *D, long long ldd, void *cuda_stream);
+
+/* ---------------------------------------------------------------- the surrogate
+ * A learned stand-in for whole hillslope runs (not in the paper): an MLP mapping slope,
+ * vegetation cover, porosity, plant drag and a 32-sample hyetograph (ASX_MLP_IN inputs)
+ * to a 128-sample outlet hydrograph (ASX_MLP_OUT outputs), three hidden ReLU layers of
+ * ASX_MLP_HIDDEN units, trained on hydrographs the solver produces.  BF16 weights and
+ * activations, FP32 accumulation on the tensor cores (asx_gemm_bf16), FP32 master weights
+ * and Adam moments.  Parameters are packed as W1 (256 x 36, row = output unit), b1 (256),
+ * W2 (256 x 256), b2, W3 (256 x 256), b3, W4 (128 x 256), b4 (128): ASX_MLP_PARAMS
+ * floats.  x is batch x 36 and y, t are batch x 128, FP32 row-major.  Loss: mean squared
+ * error over batch x 128. */
+#define ASX_MLP_IN 36
+#define ASX_MLP_HIDDEN 256
+#define ASX_MLP_OUT 128
+#define ASX_MLP_PARAMS 173952
+typedef struct asx_mlp asx_mlp;
+
+/* Allocates parameters, Adam state and activations for batches up to max_batch
+ * (1 .. 4,194,304); parameters start at zero. */
+asx_status asx_mlp_create(int device, void *cuda_stream, int max_batch, asx_mlp **out);
+asx_status asx_mlp_destroy(asx_mlp *p);
+/* Sets / reads the packed FP32 parameters (setting also resets Adam). */
+asx_status asx_mlp_set_params(asx_mlp *p, const float *params, int ptr_kind);
+asx_status asx_mlp_get_params(asx_mlp *p, float *params, int ptr_kind);
+/* Inference on any batch (processed max_batch rows at a time). */
+asx_status asx_mlp_forward(asx_mlp *p, int batch, const float *x, float *y, int ptr_kind);
+/* Gradient of the loss with respect to the packed parameters, and the loss (batch <=
+ * max_batch); for gradient checks. */
+asx_status asx_mlp_gradients(asx_mlp *p, int batch, const float *x, const float *t, float *grad, float *loss,
+                             int ptr_kind);
+/* One Adam step (beta 0.9 / 0.999, eps 1e-8, decoupled-free L2 weight decay on the weight
+ * matrices); *loss (may be NULL) receives the batch loss before the step. */
+asx_status asx_mlp_train_step(asx_mlp *p, int batch, const float *x, const float *t, float lr,
+                              float weight_decay, float *loss, int ptr_kind);
+const char *asx_mlp_last_error(const asx_mlp *p);
+
 /* Allocation-free scan of a state the caller holds (the paper has no counterpart; this
  * serves callers that may not allocate device memory, e.g. a runtime that owns every
  * buffer and forbids allocation once started, or a library that only lends pointers).

@@ -105,7 +105,20 @@ _PROTOS = {
     "asx_ensemble_get_hydrograph": (C.c_int, [_ENS, C.c_int, _vp, C.c_int, C.POINTER(C.c_int)]),
     "asx_ensemble_get_clock": (C.c_int, [_ENS, C.c_int, C.POINTER(C.c_double), C.POINTER(C.c_longlong)]),
     "asx_ensemble_last_error": (C.c_char_p, [_ENS]),
+    "asx_gemm_bf16": (C.c_int, [C.c_int, C.c_int, C.c_int, _vp, C.c_longlong, C.c_longlong, _vp, C.c_longlong,
+                                C.c_longlong, _vp, C.c_longlong, _vp]),
+    "asx_mlp_create": (C.c_int, [C.c_int, _vp, C.c_int, C.POINTER(_vp)]),
+    "asx_mlp_destroy": (C.c_int, [_vp]),
+    "asx_mlp_set_params": (C.c_int, [_vp, _vp, C.c_int]),
+    "asx_mlp_get_params": (C.c_int, [_vp, _vp, C.c_int]),
+    "asx_mlp_forward": (C.c_int, [_vp, C.c_int, _vp, _vp, C.c_int]),
+    "asx_mlp_gradients": (C.c_int, [_vp, C.c_int, _vp, _vp, _vp, C.POINTER(C.c_float), C.c_int]),
+    "asx_mlp_train_step": (C.c_int, [_vp, C.c_int, _vp, _vp, C.c_float, C.c_float, C.POINTER(C.c_float),
+                                     C.c_int]),
+    "asx_mlp_last_error": (C.c_char_p, [_vp]),
 }
+
+ASX_MLP_IN, ASX_MLP_HIDDEN, ASX_MLP_OUT, ASX_MLP_PARAMS = 36, 256, 128, 173952
 
 _lib = None
 
@@ -294,3 +307,56 @@ def asx_ensemble_get_clock(e, s):
 
 def asx_ensemble_last_error(e):
     return load().asx_ensemble_last_error(e).decode()
+
+
+def asx_gemm_bf16(M, N, K, A, sam, sak, B, sbn, sbk, D, ldd, cuda_stream=None):
+    """Tensor-core GEMM D = A . B^T (BF16 in, FP32 out), device pointers (see asx.h)."""
+    _check(load().asx_gemm_bf16(int(M), int(N), int(K), _ptr(A), int(sam), int(sak), _ptr(B), int(sbn),
+                                int(sbk), _ptr(D), int(ldd), cuda_stream))
+
+
+# ----------------------------------------------------------------- the surrogate MLP
+
+def _mcheck(st, p=None):
+    if st != ASX_OK:
+        msg = load().asx_mlp_last_error(p).decode() if p else ""
+        raise AsxError(st, msg)
+
+
+def asx_mlp_create(device=0, cuda_stream=None, max_batch=65536):
+    p = _vp()
+    _mcheck(load().asx_mlp_create(int(device), cuda_stream, int(max_batch), C.byref(p)))
+    return p
+
+
+def asx_mlp_destroy(p):
+    _mcheck(load().asx_mlp_destroy(p))
+
+
+def asx_mlp_set_params(p, params, ptr_kind=ASX_PTR_HOST):
+    _mcheck(load().asx_mlp_set_params(p, _ptr(params), ptr_kind), p)
+
+
+def asx_mlp_get_params(p, params, ptr_kind=ASX_PTR_HOST):
+    _mcheck(load().asx_mlp_get_params(p, _ptr(params), ptr_kind), p)
+
+
+def asx_mlp_forward(p, batch, x, y, ptr_kind=ASX_PTR_HOST):
+    _mcheck(load().asx_mlp_forward(p, int(batch), _ptr(x), _ptr(y), ptr_kind), p)
+
+
+def asx_mlp_gradients(p, batch, x, t, grad, ptr_kind=ASX_PTR_HOST):
+    loss = C.c_float()
+    _mcheck(load().asx_mlp_gradients(p, int(batch), _ptr(x), _ptr(t), _ptr(grad), C.byref(loss), ptr_kind), p)
+    return loss.value
+
+
+def asx_mlp_train_step(p, batch, x, t, lr, weight_decay=0.0, ptr_kind=ASX_PTR_HOST, want_loss=True):
+    loss = C.c_float()
+    _mcheck(load().asx_mlp_train_step(p, int(batch), _ptr(x), _ptr(t), float(lr), float(weight_decay),
+                                      C.byref(loss) if want_loss else None, ptr_kind), p)
+    return loss.value if want_loss else None
+
+
+def asx_mlp_last_error(p):
+    return load().asx_mlp_last_error(p).decode()

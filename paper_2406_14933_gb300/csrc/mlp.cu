@@ -1,0 +1,723 @@
+// mlp.cu -- the learned surrogate: BF16 tensor-core GEMMs (tcgen05, accumulators in
+// TMEM), the fused layer epilogues, the loss, the bias gradients and Adam, and the
+// asx_mlp_* C ABI.
+//
+// The surrogate maps a scenario's slope, vegetation cover, porosity, plant drag and a
+// 32-sample hyetograph (36 inputs, padded to 64) to a 128-sample outlet hydrograph through
+// three hidden layers of 256 ReLU units: y = W4 r(W3 r(W2 r(W1 x + b1) + b2) + b3) + b4.
+// Weights and activations are BF16, every product accumulates in FP32 in tensor memory,
+// master weights and Adam moments are FP32.
+//
+// GEMM kernel: D[M x N] = A[M x K] . B[N x K]^T on one 128 x BN tile per CTA.  The four
+// warps stage 128 x 64 of A and BN x 64 of B in shared memory in the tensor core's
+// K-major core-matrix layout (8 rows x 16 bytes per core matrix), thread 0 issues the
+// tcgen05.mma instructions (kind::f16, BF16 inputs, FP32 accumulate) and commits them to
+// an mbarrier, and after the last chunk the warps read the accumulator out of TMEM with
+// tcgen05.ld (warp w owns lanes 32w..32w+31 = rows) and apply the epilogue.  Operands are
+// read through arbitrary strides, so the forward product, the input gradient and the
+// weight gradient are all this one kernel.
+#include <cuda_bf16.h>
+
+#include <cmath>
+#include <cstdint>
+#include <cstring>
+#include <new>
+#include <string>
+#include <vector>
+
+#include "asx_internal.cuh"
+
+namespace asx {
+namespace {
+
+constexpr int kTM = 128;       // tile rows (TMEM lanes)
+constexpr int kTK = 64;        // K chunk staged per round
+constexpr int kGemmThreads = 128;
+
+// ----------------------------------------------------------------- PTX wrappers
+
+__device__ __forceinline__ unsigned su32(const void *p) { return (unsigned)__cvta_generic_to_shared(p); }
+
+__device__ __forceinline__ void mbar_init1(unsigned long long *bar)
+{
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(su32(bar)) : "memory");
+}
+
+__device__ __forceinline__ bool mbar_try(unsigned long long *bar, unsigned parity)
+{
+    unsigned ok;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+        "selp.u32 %0, 1, 0, p;\n\t}"
+        : "=r"(ok)
+        : "r"(su32(bar)), "r"(parity)
+        : "memory");
+    return ok != 0;
+}
+
+__device__ __forceinline__ bool mbar_wait_bounded1(unsigned long long *bar, unsigned parity)
+{
+    for (unsigned it = 0; it < (1u << 26); it++) {
+        if (mbar_try(bar, parity)) return true;
+        if (it > 64) __nanosleep(32);
+    }
+    return false;
+}
+
+// Shared-memory matrix descriptor of a K-major, non-swizzled operand: core matrices of
+// 8 rows x 16 bytes; lbo = byte stride between core matrices along K, sbo = along M/N.
+__device__ __forceinline__ unsigned long long smem_desc(unsigned addr, unsigned lbo, unsigned sbo)
+{
+    unsigned long long d = 0;
+    d |= (unsigned long long)((addr >> 4) & 0x3FFFu);
+    d |= (unsigned long long)((lbo >> 4) & 0x3FFFu) << 16;
+    d |= (unsigned long long)((sbo >> 4) & 0x3FFFu) << 32;
+    d |= 1ull << 46;                       // descriptor version of this tensor-core generation
+    return d;                              // base offset 0, layout type 0 (no swizzle)
+}
+
+// Instruction descriptor: D FP32, A and B BF16, both K-major, M = 128, N = n.
+__host__ __device__ constexpr unsigned instr_desc(int n)
+{
+    return (1u << 4) | (1u << 7) | (1u << 10) | ((unsigned)(n >> 3) << 17) | ((unsigned)(kTM >> 4) << 24);
+}
+
+__device__ __forceinline__ void tc_mma(unsigned tmem_d, unsigned long long a, unsigned long long b, unsigned idesc,
+                                       unsigned accumulate)
+{
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "setp.ne.b32 p, %4, 0;\n\t"
+        "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}" ::"r"(tmem_d),
+        "l"(a), "l"(b), "r"(idesc), "r"(accumulate)
+        : "memory");
+}
+
+__device__ __forceinline__ void tc_commit(unsigned long long *bar)
+{
+    asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(su32(bar))
+                 : "memory");
+}
+
+__device__ __forceinline__ void tc_ld16(unsigned taddr, float *v)
+{
+    unsigned r[16];
+    asm volatile(
+        "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
+        : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
+          "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
+        : "r"(taddr));
+    asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+    for (int i = 0; i < 16; i++) v[i] = __uint_as_float(r[i]);
+}
+
+// ----------------------------------------------------------------- the GEMM
+
+struct GemmArgs {
+    int M, N, K;
+    const __nv_bfloat16 *A;
+    long long sam, sak;            // A(m, k) = A[m sam + k sak]
+    const __nv_bfloat16 *B;
+    long long sbn, sbk;            // B(n, k) = B[n sbn + k sbk]
+    // epilogue: v = D (+ bias[n]); relu: v = max(v, 0); mask: v *= (mask[m ldm + n] > 0)
+    const float *bias;
+    int relu;
+    const __nv_bfloat16 *mask;
+    long long ldm;
+    float *outf;                   // FP32 output (or nullptr)
+    __nv_bfloat16 *outb;           // BF16 output (or nullptr)
+    long long ldo;
+    int *err;
+};
+
+// Byte offset of element (r, k) of an R x 64 K-major chunk in core-matrix layout.
+__device__ __forceinline__ unsigned cm_off(int r, int k)
+{
+    return (unsigned)(((r >> 3) * (kTK / 8) + (k >> 3)) * 128 + (r & 7) * 16 + (k & 7) * 2);
+}
+
+template <int BN>
+constexpr int gemm_smem_bytes()
+{
+    return kTM * kTK * 2 + BN * kTK * 2 + 128;
+}
+
+template <int BN>
+__global__ void __launch_bounds__(kGemmThreads) gemm_tc_kernel(const GemmArgs g)
+{
+    extern __shared__ __align__(128) unsigned char gsm[];
+    unsigned char *base = gsm + ((128u - (su32(gsm) & 127u)) & 127u);
+    unsigned char *sA = base;                       // 128 x 64 BF16, core-matrix layout
+    unsigned char *sB = base + kTM * kTK * 2;       // BN x 64 BF16
+    __shared__ __align__(8) unsigned long long bar;
+    __shared__ unsigned tmem_base;
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    const int m0 = blockIdx.x * kTM, n0 = blockIdx.y * BN;
+    if (warp == 0) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(su32(&tmem_base)),
+                     "r"(BN)
+                     : "memory");
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+    }
+    if (tid == 0) {
+        mbar_init1(&bar);
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    __syncthreads();
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    const unsigned tmem = tmem_base;
+    const unsigned idesc = instr_desc(BN);
+    bool ok = true;
+    int phase = 0;
+    const int nchunks = (g.K + kTK - 1) / kTK;
+    for (int c = 0; c < nchunks; c++) {
+        const int k0 = c * kTK;
+        // ---- stage A (128 x 64) and B (BN x 64) chunks, zero outside the matrices
+        for (int i = tid; i < kTM * kTK; i += kGemmThreads) {
+            const int r = i / kTK, k = i % kTK;
+            const int m = m0 + r, kk = k0 + k;
+            __nv_bfloat16 v = __float2bfloat16(0.0f);
+            if (m < g.M && kk < g.K) v = g.A[(long long)m * g.sam + (long long)kk * g.sak];
+            *reinterpret_cast<__nv_bfloat16 *>(sA + cm_off(r, k)) = v;
+        }
+        for (int i = tid; i < BN * kTK; i += kGemmThreads) {
+            const int r = i / kTK, k = i % kTK;
+            const int n = n0 + r, kk = k0 + k;
+            __nv_bfloat16 v = __float2bfloat16(0.0f);
+            if (n < g.N && kk < g.K) v = g.B[(long long)n * g.sbn + (long long)kk * g.sbk];
+            *reinterpret_cast<__nv_bfloat16 *>(sB + cm_off(r, k)) = v;
+        }
+        // the tensor core reads shared memory through the async proxy
+        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+        __syncthreads();
+        if (tid == 0) {
+            asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+#pragma unroll
+            for (int s = 0; s < kTK / 16; s++) {
+                const unsigned long long da = smem_desc(su32(sA) + s * 256, 128, (kTK / 8) * 128);
+                const unsigned long long db = smem_desc(su32(sB) + s * 256, 128, (kTK / 8) * 128);
+                tc_mma(tmem, da, db, idesc, (c > 0 || s > 0) ? 1u : 0u);
+            }
+            tc_commit(&bar);
+        }
+        // wait for the MMAs before the chunk buffers are overwritten (and at the end)
+        if (!mbar_wait_bounded1(&bar, (unsigned)phase)) ok = false;
+        phase ^= 1;
+        asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+        __syncthreads();
+    }
+    if (!ok && tid == 0 && g.err) atomicOr(g.err, 1);
+    // ---- epilogue: warp w holds rows 32w..32w+31 of the tile, one row per lane
+    const int m = m0 + warp * 32 + lane;
+    for (int nc = 0; nc < BN; nc += 16) {
+        float v[16];
+        tc_ld16(tmem + ((unsigned)(warp * 32) << 16) + (unsigned)nc, v);
+        if (m < g.M) {
+#pragma unroll
+            for (int j = 0; j < 16; j++) {
+                const int n = n0 + nc + j;
+                if (n >= g.N) break;
+                float x = v[j];
+                if (g.bias) x += g.bias[n];
+                if (g.relu) x = fmaxf(x, 0.0f);
+                if (g.mask && !(__bfloat162float(g.mask[(long long)m * g.ldm + n]) > 0.0f)) x = 0.0f;
+                if (g.outf) g.outf[(long long)m * g.ldo + n] = x;
+                if (g.outb) g.outb[(long long)m * g.ldo + n] = __float2bfloat16(x);
+            }
+        }
+    }
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    __syncthreads();
+    if (warp == 0) {
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(BN) : "memory");
+    }
+}
+
+// ----------------------------------------------------------------- small kernels
+
+// db[n] = sum_m dZ[m][n] (FP32 from the BF16 gradient).
+__global__ void bias_grad_kernel(const __nv_bfloat16 *dz, int M, int N, float *db)
+{
+    const int n = blockIdx.x * blockDim.x + threadIdx.x;
+    if (n >= N) return;
+    float s = 0.0f;
+    for (int m = 0; m < M; m++) s += __bfloat162float(dz[(long long)m * N + n]);
+    db[n] = s;
+}
+
+// Mean-squared error over a batch and its gradient dY = 2 (Y - T) / (M N) as BF16.
+__global__ void mse_grad_kernel(const float *y, const float *t, int n_elem, float scale, __nv_bfloat16 *dy,
+                                float *loss_acc)
+{
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    float l = 0.0f;
+    if (i < n_elem) {
+        const float d = y[i] - t[i];
+        l = d * d;
+        dy[i] = __float2bfloat16(2.0f * d * scale);
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) l += __shfl_down_sync(0xffffffffu, l, o);
+    if ((threadIdx.x & 31) == 0 && l != 0.0f) atomicAdd(loss_acc, l * scale);
+}
+
+// Adam on FP32 master weights, refreshing the BF16 copy.
+__global__ void adam_kernel(float *w, const float *grad, float *mo, float *ve, __nv_bfloat16 *wb, int n, float lr,
+                            float b1, float b2, float eps, float c1, float c2, float wd)
+{
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    const float gi = grad[i] + wd * w[i];
+    const float m = b1 * mo[i] + (1.0f - b1) * gi;
+    const float v = b2 * ve[i] + (1.0f - b2) * gi * gi;
+    mo[i] = m;
+    ve[i] = v;
+    const float x = w[i] - lr * (m / c1) / (sqrtf(v / c2) + eps);
+    w[i] = x;
+    if (wb) wb[i] = __float2bfloat16(x);
+}
+
+__global__ void f32_to_bf16_kernel(const float *x, __nv_bfloat16 *y, long long n)
+{
+    const long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    if (i < n) y[i] = __float2bfloat16(x[i]);
+}
+
+// x (M x din FP32, row-major) -> (M x ldx BF16) with zero padding of the extra columns.
+__global__ void pad_input_kernel(const float *x, int M, int din, int ldx, __nv_bfloat16 *y)
+{
+    const long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    if (i >= (long long)M * ldx) return;
+    const int m = (int)(i / ldx), k = (int)(i % ldx);
+    y[i] = __float2bfloat16(k < din ? x[(long long)m * din + k] : 0.0f);
+}
+
+}  // namespace
+
+template <int BN>
+cudaError_t launch_gemm_bn(const GemmArgs &g, cudaStream_t s)
+{
+    static bool configured = false;
+    if (!configured) {
+        cudaError_t e = cudaFuncSetAttribute(gemm_tc_kernel<BN>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                             gemm_smem_bytes<BN>());
+        if (e != cudaSuccess) return e;
+        configured = true;
+    }
+    dim3 grid((g.M + kTM - 1) / kTM, (g.N + BN - 1) / BN);
+    gemm_tc_kernel<BN><<<grid, kGemmThreads, gemm_smem_bytes<BN>(), s>>>(g);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_gemm_tc(const GemmArgs &g, int bn, cudaStream_t s)
+{
+    if (bn == 256) return launch_gemm_bn<256>(g, s);
+    if (bn == 128) return launch_gemm_bn<128>(g, s);
+    return launch_gemm_bn<64>(g, s);
+}
+
+}  // namespace asx
+
+using namespace asx;
+
+// ------------------------------------------------------------------ C ABI
+
+extern "C" asx_status asx_gemm_bf16(int M, int N, int K, const void *A, long long sam, long long sak, const void *B,
+                                    long long sbn, long long sbk, float *D, long long ldd, void *cuda_stream)
+{
+    if (M < 1 || N < 1 || K < 1 || !A || !B || !D || ldd < N) return ASX_EINVAL;
+    GemmArgs g{};
+    g.M = M;
+    g.N = N;
+    g.K = K;
+    g.A = static_cast<const __nv_bfloat16 *>(A);
+    g.sam = sam;
+    g.sak = sak;
+    g.B = static_cast<const __nv_bfloat16 *>(B);
+    g.sbn = sbn;
+    g.sbk = sbk;
+    g.outf = D;
+    g.ldo = ldd;
+    const int bn = N >= 256 ? 256 : N > 64 ? 128 : 64;
+    return launch_gemm_tc(g, bn, static_cast<cudaStream_t>(cuda_stream)) == cudaSuccess ? ASX_OK : ASX_ECUDA;
+}
+
+// ------------------------------------------------------------------ the MLP
+
+namespace asx {
+namespace {
+
+constexpr int kIn = ASX_MLP_IN, kInPad = 64, kHid = ASX_MLP_HIDDEN, kOut = ASX_MLP_OUT;
+
+// Offsets (in floats) of the padded parameter layout: W1 is kept 256 x 64 with zero
+// columns 36..63 (their gradient is zero, so Adam keeps them zero).
+constexpr long long oW1 = 0, oB1 = oW1 + (long long)kHid * kInPad, oW2 = oB1 + kHid, oB2 = oW2 + (long long)kHid * kHid,
+                    oW3 = oB2 + kHid, oB3 = oW3 + (long long)kHid * kHid, oW4 = oB3 + kHid,
+                    oB4 = oW4 + (long long)kOut * kHid, kPadded = oB4 + kOut;
+
+}  // namespace
+}  // namespace asx
+
+struct asx_mlp {
+    int device = 0, max_batch = 0;
+    cudaStream_t stream = nullptr;
+    float *w = nullptr, *g = nullptr, *m = nullptr, *v = nullptr;   // FP32 master, grad, Adam moments
+    __nv_bfloat16 *wb = nullptr;                                    // BF16 copies of W1..W4 (padded layout)
+    __nv_bfloat16 *x0 = nullptr, *a1 = nullptr, *a2 = nullptr, *a3 = nullptr, *dy = nullptr, *dz = nullptr,
+                  *dz2 = nullptr;
+    float *y = nullptr, *xin = nullptr, *tin = nullptr, *loss = nullptr;
+    int *err = nullptr;
+    long long adam_t = 0;
+    std::string error;
+};
+
+namespace {
+
+using namespace asx;
+
+asx_status mfail(asx_mlp *p, asx_status st, const std::string &s)
+{
+    if (p) p->error = s;
+    return st;
+}
+
+#define MLP_CUDA(p, call)                                                                        \
+    do {                                                                                         \
+        cudaError_t x_ = (call);                                                                 \
+        if (x_ != cudaSuccess)                                                                   \
+            return mfail((p), ASX_ECUDA, std::string(#call) + ": " + cudaGetErrorString(x_));    \
+    } while (0)
+
+GemmArgs gemm(int M, int N, int K, const __nv_bfloat16 *A, long long sam, long long sak, const __nv_bfloat16 *B,
+              long long sbn, long long sbk, int *err)
+{
+    GemmArgs g{};
+    g.M = M;
+    g.N = N;
+    g.K = K;
+    g.A = A;
+    g.sam = sam;
+    g.sak = sak;
+    g.B = B;
+    g.sbn = sbn;
+    g.sbk = sbk;
+    g.err = err;
+    return g;
+}
+
+__nv_bfloat16 *wb_of(asx_mlp *p, int layer)
+{
+    static const long long off[4] = {oW1, oW2 - kHid, oW3 - 2 * kHid, oW4 - 3 * kHid};
+    return p->wb + off[layer];
+}
+
+// Forward pass of `batch` rows already in p->x0 (BF16, padded); fills a1..a3 and y.
+cudaError_t forward(asx_mlp *p, int B)
+{
+    GemmArgs g = gemm(B, kHid, kInPad, p->x0, kInPad, 1, wb_of(p, 0), kInPad, 1, p->err);
+    g.bias = p->w + oB1;
+    g.relu = 1;
+    g.outb = p->a1;
+    g.ldo = kHid;
+    cudaError_t e = launch_gemm_tc(g, 256, p->stream);
+    if (e != cudaSuccess) return e;
+    const __nv_bfloat16 *in[2] = {p->a1, p->a2};
+    __nv_bfloat16 *out[2] = {p->a2, p->a3};
+    const long long ob[2] = {oB2, oB3};
+    for (int l = 0; l < 2; l++) {
+        g = gemm(B, kHid, kHid, in[l], kHid, 1, wb_of(p, l + 1), kHid, 1, p->err);
+        g.bias = p->w + ob[l];
+        g.relu = 1;
+        g.outb = out[l];
+        g.ldo = kHid;
+        e = launch_gemm_tc(g, 256, p->stream);
+        if (e != cudaSuccess) return e;
+    }
+    g = gemm(B, kOut, kHid, p->a3, kHid, 1, wb_of(p, 3), kHid, 1, p->err);
+    g.bias = p->w + oB4;
+    g.outf = p->y;
+    g.ldo = kOut;
+    return launch_gemm_tc(g, 128, p->stream);
+}
+
+// Gradients of the mean-squared error of the last forward pass against targets p->tin
+// into p->g (padded layout); the loss into p->loss[0].
+cudaError_t backward(asx_mlp *p, int B)
+{
+    cudaError_t e = cudaMemsetAsync(p->loss, 0, sizeof(float), p->stream);
+    if (e != cudaSuccess) return e;
+    const int ne = B * kOut;
+    mse_grad_kernel<<<(ne + 255) / 256, 256, 0, p->stream>>>(p->y, p->tin, ne, 1.0f / (float)ne, p->dy, p->loss);
+    // layer 4
+    GemmArgs g = gemm(kOut, kHid, B, p->dy, 1, kOut, p->a3, 1, kHid, p->err);   // dW4 = dY^T A3
+    g.outf = p->g + oW4;
+    g.ldo = kHid;
+    if ((e = launch_gemm_tc(g, 256, p->stream)) != cudaSuccess) return e;
+    bias_grad_kernel<<<1, kOut, 0, p->stream>>>(p->dy, B, kOut, p->g + oB4);
+    g = gemm(B, kHid, kOut, p->dy, kOut, 1, wb_of(p, 3), 1, kHid, p->err);      // dZ3 = (dY W4) r'(z3)
+    g.mask = p->a3;
+    g.ldm = kHid;
+    g.outb = p->dz;
+    g.ldo = kHid;
+    if ((e = launch_gemm_tc(g, 256, p->stream)) != cudaSuccess) return e;
+    // layers 3 and 2
+    const __nv_bfloat16 *act_in[2] = {p->a2, p->a1};
+    const long long ow[2] = {oW3, oW2}, ob[2] = {oB3, oB2};
+    __nv_bfloat16 *cur = p->dz, *nxt = p->dz2;
+    for (int l = 0; l < 2; l++) {
+        g = gemm(kHid, kHid, B, cur, 1, kHid, act_in[l], 1, kHid, p->err);       // dW = dZ^T A_in
+        g.outf = p->g + ow[l];
+        g.ldo = kHid;
+        if ((e = launch_gemm_tc(g, 256, p->stream)) != cudaSuccess) return e;
+        bias_grad_kernel<<<1, kHid, 0, p->stream>>>(cur, B, kHid, p->g + ob[l]);
+        g = gemm(B, kHid, kHid, cur, kHid, 1, wb_of(p, 2 - l), 1, kHid, p->err);  // dZ_in = (dZ W) r'
+        g.mask = act_in[l];
+        g.ldm = kHid;
+        g.outb = nxt;
+        g.ldo = kHid;
+        if ((e = launch_gemm_tc(g, 256, p->stream)) != cudaSuccess) return e;
+        __nv_bfloat16 *t = cur;
+        cur = nxt;
+        nxt = t;
+    }
+    // layer 1
+    g = gemm(kHid, kInPad, B, cur, 1, kHid, p->x0, 1, kInPad, p->err);           // dW1 = dZ1^T X
+    g.outf = p->g + oW1;
+    g.ldo = kInPad;
+    if ((e = launch_gemm_tc(g, 64, p->stream)) != cudaSuccess) return e;
+    bias_grad_kernel<<<1, kHid, 0, p->stream>>>(cur, B, kHid, p->g + oB1);
+    return cudaGetLastError();
+}
+
+cudaError_t refresh_bf16(asx_mlp *p)
+{
+    const long long segs[4][2] = {{oW1, (long long)kHid * kInPad}, {oW2, (long long)kHid * kHid},
+                                  {oW3, (long long)kHid * kHid}, {oW4, (long long)kOut * kHid}};
+    for (int l = 0; l < 4; l++) {
+        const long long n = segs[l][1];
+        f32_to_bf16_kernel<<<(unsigned)((n + 255) / 256), 256, 0, p->stream>>>(p->w + segs[l][0], wb_of(p, l), n);
+    }
+    return cudaGetLastError();
+}
+
+// Packed (public) <-> padded (internal) parameter layouts on the host.
+void pack_to_padded(const float *src, std::vector<float> &dst)
+{
+    dst.assign((size_t)kPadded, 0.0f);
+    const float *s = src;
+    for (int o = 0; o < kHid; o++)
+        for (int i = 0; i < kIn; i++) dst[oW1 + (long long)o * kInPad + i] = *s++;
+    std::memcpy(&dst[oB1], s, sizeof(float) * (size_t)(kPadded - oB1));
+}
+
+void padded_to_pack(const std::vector<float> &src, float *dst)
+{
+    float *d = dst;
+    for (int o = 0; o < kHid; o++)
+        for (int i = 0; i < kIn; i++) *d++ = src[oW1 + (long long)o * kInPad + i];
+    std::memcpy(d, &src[oB1], sizeof(float) * (size_t)(kPadded - oB1));
+}
+
+asx_status stage_inputs(asx_mlp *p, int B, const float *x, const float *t, int kind)
+{
+    const cudaMemcpyKind mk = kind == ASX_PTR_HOST ? cudaMemcpyHostToDevice : cudaMemcpyDeviceToDevice;
+    MLP_CUDA(p, cudaMemcpyAsync(p->xin, x, sizeof(float) * (size_t)B * kIn, mk, p->stream));
+    if (t) MLP_CUDA(p, cudaMemcpyAsync(p->tin, t, sizeof(float) * (size_t)B * kOut, mk, p->stream));
+    const long long n = (long long)B * kInPad;
+    pad_input_kernel<<<(unsigned)((n + 255) / 256), 256, 0, p->stream>>>(p->xin, B, kIn, kInPad, p->x0);
+    MLP_CUDA(p, cudaGetLastError());
+    return ASX_OK;
+}
+
+asx_status check_err(asx_mlp *p)
+{
+    int h = 0;
+    MLP_CUDA(p, cudaMemcpyAsync(&h, p->err, sizeof(int), cudaMemcpyDeviceToHost, p->stream));
+    MLP_CUDA(p, cudaStreamSynchronize(p->stream));
+    if (h) return mfail(p, ASX_ETIMEOUT, "a tensor-core wait ran out");
+    return ASX_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+asx_status asx_mlp_create(int device, void *cuda_stream, int max_batch, asx_mlp **out)
+{
+    if (!out || max_batch < 1 || max_batch > (1 << 22)) return ASX_EINVAL;
+    *out = nullptr;
+    asx_mlp *p = new (std::nothrow) asx_mlp();
+    if (!p) return ASX_ENOMEM;
+    p->device = device;
+    p->max_batch = max_batch;
+    p->stream = (cudaStream_t)cuda_stream;
+    if (cudaSetDevice(device) != cudaSuccess) {
+        delete p;
+        return ASX_ECUDA;
+    }
+    const size_t B = (size_t)max_batch;
+    const size_t nwb = (size_t)kHid * kInPad + 2 * (size_t)kHid * kHid + (size_t)kOut * kHid;
+    cudaError_t e = cudaSuccess;
+    auto alloc = [&](void **ptr, size_t bytes) {
+        if (e == cudaSuccess) e = cudaMalloc(ptr, bytes);
+    };
+    alloc((void **)&p->w, sizeof(float) * kPadded);
+    alloc((void **)&p->g, sizeof(float) * kPadded);
+    alloc((void **)&p->m, sizeof(float) * kPadded);
+    alloc((void **)&p->v, sizeof(float) * kPadded);
+    alloc((void **)&p->wb, sizeof(__nv_bfloat16) * nwb);
+    alloc((void **)&p->x0, sizeof(__nv_bfloat16) * B * kInPad);
+    alloc((void **)&p->a1, sizeof(__nv_bfloat16) * B * kHid);
+    alloc((void **)&p->a2, sizeof(__nv_bfloat16) * B * kHid);
+    alloc((void **)&p->a3, sizeof(__nv_bfloat16) * B * kHid);
+    alloc((void **)&p->dy, sizeof(__nv_bfloat16) * B * kOut);
+    alloc((void **)&p->dz, sizeof(__nv_bfloat16) * B * kHid);
+    alloc((void **)&p->dz2, sizeof(__nv_bfloat16) * B * kHid);
+    alloc((void **)&p->y, sizeof(float) * B * kOut);
+    alloc((void **)&p->xin, sizeof(float) * B * kIn);
+    alloc((void **)&p->tin, sizeof(float) * B * kOut);
+    alloc((void **)&p->loss, sizeof(float));
+    alloc((void **)&p->err, sizeof(int));
+    if (e == cudaSuccess) e = cudaMemsetAsync(p->w, 0, sizeof(float) * kPadded, p->stream);
+    if (e == cudaSuccess) e = cudaMemsetAsync(p->m, 0, sizeof(float) * kPadded, p->stream);
+    if (e == cudaSuccess) e = cudaMemsetAsync(p->v, 0, sizeof(float) * kPadded, p->stream);
+    if (e == cudaSuccess) e = cudaMemsetAsync(p->err, 0, sizeof(int), p->stream);
+    if (e == cudaSuccess) e = refresh_bf16(p);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(p->stream);
+    if (e != cudaSuccess) {
+        asx_mlp_destroy(p);
+        return e == cudaErrorMemoryAllocation ? ASX_ENOMEM : ASX_ECUDA;
+    }
+    *out = p;
+    return ASX_OK;
+}
+
+asx_status asx_mlp_destroy(asx_mlp *p)
+{
+    if (!p) return ASX_OK;
+    cudaSetDevice(p->device);
+    if (p->stream) cudaStreamSynchronize(p->stream);
+    void *ptrs[] = {p->w, p->g, p->m, p->v, p->wb, p->x0, p->a1, p->a2, p->a3, p->dy, p->dz, p->dz2,
+                    p->y, p->xin, p->tin, p->loss, p->err};
+    for (void *q : ptrs) cudaFree(q);
+    delete p;
+    return ASX_OK;
+}
+
+const char *asx_mlp_last_error(const asx_mlp *p) { return p ? p->error.c_str() : "null surrogate handle"; }
+
+asx_status asx_mlp_set_params(asx_mlp *p, const float *params, int kind)
+{
+    if (!p || !params) return mfail(p, ASX_EINVAL, "null argument");
+    if (kind != ASX_PTR_HOST && kind != ASX_PTR_DEVICE) return mfail(p, ASX_EINVAL, "bad ptr_kind");
+    MLP_CUDA(p, cudaSetDevice(p->device));
+    std::vector<float> host(ASX_MLP_PARAMS);
+    if (kind == ASX_PTR_DEVICE) MLP_CUDA(p, cudaMemcpy(host.data(), params, sizeof(float) * ASX_MLP_PARAMS, cudaMemcpyDeviceToHost));
+    else std::memcpy(host.data(), params, sizeof(float) * ASX_MLP_PARAMS);
+    for (float f : host)
+        if (!std::isfinite(f)) return mfail(p, ASX_EINVAL, "non-finite parameter");
+    std::vector<float> pad;
+    pack_to_padded(host.data(), pad);
+    MLP_CUDA(p, cudaMemcpyAsync(p->w, pad.data(), sizeof(float) * kPadded, cudaMemcpyHostToDevice, p->stream));
+    MLP_CUDA(p, cudaMemsetAsync(p->m, 0, sizeof(float) * kPadded, p->stream));
+    MLP_CUDA(p, cudaMemsetAsync(p->v, 0, sizeof(float) * kPadded, p->stream));
+    MLP_CUDA(p, refresh_bf16(p));
+    MLP_CUDA(p, cudaStreamSynchronize(p->stream));
+    p->adam_t = 0;
+    return ASX_OK;
+}
+
+asx_status asx_mlp_get_params(asx_mlp *p, float *params, int kind)
+{
+    if (!p || !params) return mfail(p, ASX_EINVAL, "null argument");
+    if (kind != ASX_PTR_HOST && kind != ASX_PTR_DEVICE) return mfail(p, ASX_EINVAL, "bad ptr_kind");
+    MLP_CUDA(p, cudaSetDevice(p->device));
+    std::vector<float> pad(kPadded), host(ASX_MLP_PARAMS);
+    MLP_CUDA(p, cudaMemcpyAsync(pad.data(), p->w, sizeof(float) * kPadded, cudaMemcpyDeviceToHost, p->stream));
+    MLP_CUDA(p, cudaStreamSynchronize(p->stream));
+    padded_to_pack(pad, host.data());
+    if (kind == ASX_PTR_DEVICE) MLP_CUDA(p, cudaMemcpy(params, host.data(), sizeof(float) * ASX_MLP_PARAMS, cudaMemcpyHostToDevice));
+    else std::memcpy(params, host.data(), sizeof(float) * ASX_MLP_PARAMS);
+    return ASX_OK;
+}
+
+asx_status asx_mlp_forward(asx_mlp *p, int batch, const float *x, float *y, int kind)
+{
+    if (!p || !x || !y) return mfail(p, ASX_EINVAL, "null argument");
+    if (kind != ASX_PTR_HOST && kind != ASX_PTR_DEVICE) return mfail(p, ASX_EINVAL, "bad ptr_kind");
+    MLP_CUDA(p, cudaSetDevice(p->device));
+    const cudaMemcpyKind back = kind == ASX_PTR_HOST ? cudaMemcpyDeviceToHost : cudaMemcpyDeviceToDevice;
+    for (int b0 = 0; b0 < batch; b0 += p->max_batch) {
+        const int B = batch - b0 < p->max_batch ? batch - b0 : p->max_batch;
+        asx_status st = stage_inputs(p, B, x + (size_t)b0 * kIn, nullptr, kind);
+        if (st) return st;
+        MLP_CUDA(p, forward(p, B));
+        MLP_CUDA(p, cudaMemcpyAsync(y + (size_t)b0 * kOut, p->y, sizeof(float) * (size_t)B * kOut, back, p->stream));
+    }
+    if (kind == ASX_PTR_HOST) return check_err(p);
+    return ASX_OK;
+}
+
+asx_status asx_mlp_gradients(asx_mlp *p, int batch, const float *x, const float *t, float *grad, float *loss,
+                             int kind)
+{
+    if (!p || !x || !t || !grad) return mfail(p, ASX_EINVAL, "null argument");
+    if (batch < 1 || batch > p->max_batch) return mfail(p, ASX_EINVAL, "batch out of range");
+    if (kind != ASX_PTR_HOST && kind != ASX_PTR_DEVICE) return mfail(p, ASX_EINVAL, "bad ptr_kind");
+    MLP_CUDA(p, cudaSetDevice(p->device));
+    asx_status st = stage_inputs(p, batch, x, t, kind);
+    if (st) return st;
+    MLP_CUDA(p, forward(p, batch));
+    MLP_CUDA(p, backward(p, batch));
+    std::vector<float> pad(kPadded), host(ASX_MLP_PARAMS);
+    float l = 0.0f;
+    MLP_CUDA(p, cudaMemcpyAsync(pad.data(), p->g, sizeof(float) * kPadded, cudaMemcpyDeviceToHost, p->stream));
+    MLP_CUDA(p, cudaMemcpyAsync(&l, p->loss, sizeof(float), cudaMemcpyDeviceToHost, p->stream));
+    st = check_err(p);
+    if (st) return st;
+    padded_to_pack(pad, host.data());
+    if (kind == ASX_PTR_DEVICE) MLP_CUDA(p, cudaMemcpy(grad, host.data(), sizeof(float) * ASX_MLP_PARAMS, cudaMemcpyHostToDevice));
+    else std::memcpy(grad, host.data(), sizeof(float) * ASX_MLP_PARAMS);
+    if (loss) *loss = l;
+    return ASX_OK;
+}
+
+asx_status asx_mlp_train_step(asx_mlp *p, int batch, const float *x, const float *t, float lr, float weight_decay,
+                              float *loss, int kind)
+{
+    if (!p || !x || !t) return mfail(p, ASX_EINVAL, "null argument");
+    if (batch < 1 || batch > p->max_batch) return mfail(p, ASX_EINVAL, "batch out of range");
+    if (!(lr > 0.0f) || !(weight_decay >= 0.0f)) return mfail(p, ASX_EINVAL, "bad learning rate");
+    if (kind != ASX_PTR_HOST && kind != ASX_PTR_DEVICE) return mfail(p, ASX_EINVAL, "bad ptr_kind");
+    MLP_CUDA(p, cudaSetDevice(p->device));
+    asx_status st = stage_inputs(p, batch, x, t, kind);
+    if (st) return st;
+    MLP_CUDA(p, forward(p, batch));
+    MLP_CUDA(p, backward(p, batch));
+    p->adam_t += 1;
+    const float b1 = 0.9f, b2 = 0.999f;
+    const float c1 = 1.0f - (float)std::pow((double)b1, (double)p->adam_t);
+    const float c2 = 1.0f - (float)std::pow((double)b2, (double)p->adam_t);
+    // weights (with BF16 copies) and biases (FP32 only, no decay)
+    const long long segs[8][3] = {{oW1, (long long)kHid * kInPad, 0}, {oB1, kHid, -1}, {oW2, (long long)kHid * kHid, 1},
+                                  {oB2, kHid, -1}, {oW3, (long long)kHid * kHid, 2}, {oB3, kHid, -1},
+                                  {oW4, (long long)kOut * kHid, 3}, {oB4, kOut, -1}};
+    for (int s = 0; s < 8; s++) {
+        const long long o = segs[s][0], n = segs[s][1];
+        const int l = (int)segs[s][2];
+        adam_kernel<<<(unsigned)((n + 255) / 256), 256, 0, p->stream>>>(
+            p->w + o, p->g + o, p->m + o, p->v + o, l >= 0 ? wb_of(p, l) : nullptr, (int)n, lr, b1, b2, 1e-8f, c1, c2,
+            l >= 0 ? weight_decay : 0.0f);
+    }
+    MLP_CUDA(p, cudaGetLastError());
+    if (loss) {
+        MLP_CUDA(p, cudaMemcpyAsync(loss, p->loss, sizeof(float), cudaMemcpyDeviceToHost, p->stream));
+        return check_err(p);
+    }
+    return ASX_OK;
+}
+
+}  // extern "C"

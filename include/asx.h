@@ -291,6 +291,19 @@ asx_status asx_mlp_train_step(asx_mlp *p, int batch, const float *x, const float
                               float weight_decay, float *loss, int ptr_kind);
 const char *asx_mlp_last_error(const asx_mlp *p);
 
+/* The surrogate's check against the solver, with fallback: for k < n_check, with
+ * q = idx[k], computes e_k = ||y_q - ref_k||_2 / ||ref_k||_2 over the ASX_MLP_OUT samples
+ * of row q of y (batch x ASX_MLP_OUT, the surrogate's hydrographs) and row k of ref
+ * (n_check x ASX_MLP_OUT, the solver's hydrographs of the same queries, same units);
+ * where e_k > tol, or e_k is not a number, row q of y is overwritten with ref_k.
+ * rel_err[k] receives e_k (0 where both rows are zero, +inf where only ref_k is zero,
+ * NaN where idx[k] lies outside [0, batch) -- such a row is skipped), *n_replaced the
+ * number of rows replaced.  idx must not repeat.  All pointers are device memory;
+ * asynchronous on cuda_stream.  ASX_EINVAL on negative sizes, n_check > batch, tol < 0
+ * or null pointers. */
+asx_status asx_surrogate_check(int batch, int n_check, const int *idx, float *y, const float *ref, float tol,
+                               float *rel_err, int *n_replaced, void *cuda_stream);
+
 /* Allocation-free scan of a state the caller holds (the paper has no counterpart; this
  * serves callers that may not allocate device memory, e.g. a runtime that owns every
  * buffer and forbids allocation once started, or a library that only lends pointers).

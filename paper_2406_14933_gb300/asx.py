@@ -116,6 +116,7 @@ _PROTOS = {
     "asx_mlp_train_step": (C.c_int, [_vp, C.c_int, _vp, _vp, C.c_float, C.c_float, C.POINTER(C.c_float),
                                      C.c_int]),
     "asx_mlp_last_error": (C.c_char_p, [_vp]),
+    "asx_surrogate_check": (C.c_int, [C.c_int, C.c_int, _vp, _vp, _vp, C.c_float, _vp, _vp, _vp]),
 }
 
 ASX_MLP_IN, ASX_MLP_HIDDEN, ASX_MLP_OUT, ASX_MLP_PARAMS = 36, 256, 128, 173952
@@ -360,3 +361,9 @@ def asx_mlp_train_step(p, batch, x, t, lr, weight_decay=0.0, ptr_kind=ASX_PTR_HO
 
 def asx_mlp_last_error(p):
     return load().asx_mlp_last_error(p).decode()
+
+
+def asx_surrogate_check(batch, n_check, idx, y, ref, tol, rel_err, n_replaced, cuda_stream=None):
+    """All array arguments are device pointers (ints) or CUDA tensors."""
+    _check(load().asx_surrogate_check(int(batch), int(n_check), _ptr(idx), _ptr(y), _ptr(ref), float(tol),
+                                      _ptr(rel_err), _ptr(n_replaced), cuda_stream))

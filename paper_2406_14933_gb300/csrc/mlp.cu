@@ -295,6 +295,44 @@ __global__ void pad_input_kernel(const float *x, int M, int din, int ldx, __nv_b
     y[i] = __float2bfloat16(k < din ? x[(long long)m * din + k] : 0.0f);
 }
 
+
+// The surrogate's error check (one warp per checked query): e_k = ||y_q - ref_k|| /
+// ||ref_k|| over the hydrograph's samples, q = idx[k]; where e_k > tol (or is not a
+// number) the solver's hydrograph replaces the surrogate's in y.  An index outside
+// [0, batch) is skipped and reported as NaN.
+__global__ void hydro_check_kernel(int batch, int n_check, int len, const int *__restrict__ idx, float *y,
+                                   const float *__restrict__ ref, float tol, float *rel_err, int *n_replaced)
+{
+    const int k = (int)((blockIdx.x * blockDim.x + threadIdx.x) >> 5);
+    const int lane = threadIdx.x & 31;
+    if (k >= n_check) return;
+    const int q = idx[k];
+    if (q < 0 || q >= batch) {
+        if (lane == 0) rel_err[k] = __int_as_float(0x7fc00000);
+        return;
+    }
+    float *yq = y + (size_t)q * len;
+    const float *rk = ref + (size_t)k * len;
+    double dd = 0.0, rr = 0.0;
+    for (int j = lane; j < len; j += 32) {
+        const double d = (double)yq[j] - (double)rk[j];
+        dd += d * d;
+        rr += (double)rk[j] * (double)rk[j];
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        dd += __shfl_xor_sync(0xffffffffu, dd, o);
+        rr += __shfl_xor_sync(0xffffffffu, rr, o);
+    }
+    const float e = rr > 0.0 ? (float)sqrt(dd / rr) : (dd > 0.0 ? __int_as_float(0x7f800000) : 0.0f);
+    const bool replace = !(e <= tol);
+    if (replace)
+        for (int j = lane; j < len; j += 32) yq[j] = rk[j];
+    if (lane == 0) {
+        rel_err[k] = e;
+        if (replace) atomicAdd(n_replaced, 1);
+    }
+}
 }  // namespace
 
 template <int BN>
@@ -718,6 +756,20 @@ asx_status asx_mlp_train_step(asx_mlp *p, int batch, const float *x, const float
         return check_err(p);
     }
     return ASX_OK;
+}
+
+asx_status asx_surrogate_check(int batch, int n_check, const int *idx, float *y, const float *ref, float tol,
+                               float *rel_err, int *n_replaced, void *cuda_stream)
+{
+    if (batch < 0 || n_check < 0 || n_check > batch || !(tol >= 0.0f)) return ASX_EINVAL;
+    if (n_check > 0 && (!idx || !y || !ref || !rel_err || !n_replaced)) return ASX_EINVAL;
+    if (!n_replaced) return ASX_EINVAL;
+    cudaStream_t st = (cudaStream_t)cuda_stream;
+    if (cudaMemsetAsync(n_replaced, 0, sizeof(int), st) != cudaSuccess) return ASX_ECUDA;
+    if (n_check == 0) return ASX_OK;
+    const unsigned blocks = (unsigned)(((long long)n_check * 32 + 255) / 256);
+    asx::hydro_check_kernel<<<blocks, 256, 0, st>>>(batch, n_check, kOut, idx, y, ref, tol, rel_err, n_replaced);
+    return cudaGetLastError() == cudaSuccess ? ASX_OK : ASX_ECUDA;
 }
 
 }  // extern "C"

@@ -173,26 +173,36 @@ def fractal_basin(rows=1024, cols=1024, l=2.0, seed=1002, hurst=0.8, rms=10.0, t
                     rain_r=rr, t_end=t_end, meta=dict(seed=seed, cover=float(patch.mean())))
 
 
+def _member_draws(rng: np.random.Generator, n_lo: int, n_hi: int, n_override: int | None) -> dict:
+    u = rng.uniform()
+    n = int(round(n_lo * (n_hi / n_lo) ** u)) if n_override is None else int(n_override)
+    return dict(n=n, slope=rng.uniform(0.02, 0.30), cover=rng.uniform(0.0, 0.80),
+                theta=rng.uniform(0.70, 0.95), alpha_p=rng.uniform(20.0, 100.0),
+                rain_mm_h=rng.uniform(10.0, 150.0), rain_s=rng.uniform(20.0, 60.0) * 60.0)
+
+
+def member_params(s: int, base_seed=3000, n_lo=128, n_hi=512, n_override: int | None = None) -> dict:
+    """The scalar draws of ensemble member `s` (side n, slope, cover, porosity, drag, rain
+    rate and duration) without building its fields."""
+    return _member_draws(np.random.default_rng(base_seed + s), n_lo, n_hi, n_override)
+
+
 def ensemble_member(s: int, base_seed=3000, n_lo=128, n_hi=512, l=2.0, t_end=6400.0,
-                    n_override: int | None = None) -> Scenario:
+                    n_override: int | None = None, corr_cells: float = 8.0) -> Scenario:
     """Member `s` of the hillslope ensemble: square raster with side drawn log-uniform in
     [n_lo, n_hi], planar slope 2-30 % falling along x, vegetation cover 0-80 % from a
     thresholded Gaussian random field, porosity in [0.7, 0.95] and plant drag in
     [20, 100] 1/m drawn per member, block rain of 10-150 mm/h lasting 20-60 min, free
-    discharge downslope (east), walls elsewhere."""
+    discharge downslope (east), walls elsewhere.  The cover field's correlation length
+    is corr_cells cells."""
     rng = np.random.default_rng(base_seed + s)
-    u = rng.uniform()
-    n = int(round(n_lo * (n_hi / n_lo) ** u)) if n_override is None else int(n_override)
-    slope = rng.uniform(0.02, 0.30)
-    cover = rng.uniform(0.0, 0.80)
-    theta_v = rng.uniform(0.70, 0.95)
-    alpha_p = rng.uniform(20.0, 100.0)
-    rate = rng.uniform(10.0, 150.0)
-    dur = rng.uniform(20.0, 60.0) * 60.0
+    d = _member_draws(rng, n_lo, n_hi, n_override)
+    n, slope, cover, theta_v = d["n"], d["slope"], d["cover"], d["theta"]
+    alpha_p, rate, dur = d["alpha_p"], d["rain_mm_h"], d["rain_s"]
     x, _ = cell_centres(n, n, l)
     z = slope * (x.max() - x)
     if cover > 0:
-        f = grf(n, n, 8.0, rng)
+        f = grf(n, n, corr_cells, rng)
         veg = f >= np.quantile(f, 1.0 - cover)
     else:
         veg = np.zeros((n, n), dtype=bool)

@@ -205,11 +205,14 @@ def run_cuda(args):
         out["cpu_baseline"] = cpu_baseline(sc, budget_s=args.cpu_budget)
     if args.ens_scenarios > 0:
         out["ensemble"] = run_ensemble(args, stream)
+    if args.sur_train > 0:
+        out["surrogate"] = run_surrogate(args)
     return out
 
 
 TRAFFIC_SOURCES = ("paper_2406_14933_gb300/csrc/step_strip.cu",
-                   "paper_2406_14933_gb300/csrc/device_common.cuh")
+                   "paper_2406_14933_gb300/csrc/device_common.cuh",
+                   "paper_2406_14933_gb300/csrc/asx_internal.cuh")
 
 
 def _read_traffic(n_cells):
@@ -317,6 +320,52 @@ def run_ensemble(args, stream):
             "speedup": t_one / t_ens}
 
 
+MLP_FLOP_PER_QUERY = 2 * (36 * 256 + 256 * 256 + 256 * 256 + 256 * 128)   # algorithmic (unpadded)
+
+
+def run_surrogate(args):
+    """The learned surrogate: training runs from the ensemble solver, training on the GPU,
+    held-out error, the inference kernels on 65,536 queries (tensor roofline), and serving
+    with a 1 % solver check against the solver alone."""
+    import torch
+    from paper_2406_14933_gb300 import asx as A
+    from paper_2406_14933_gb300 import surrogate as S
+    _, peak_kind = _peaks()
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            bf16_peak = float(json.load(f)["bf16_tflops"])
+    except Exception:
+        bf16_peak = 1900.0
+    rep, model = S.pipeline(n=args.sur_n, l=args.sur_l, n_train=args.sur_train, n_held=args.sur_held,
+                            n_queries=args.sur_queries, epochs=args.sur_epochs,
+                            workers=min(8, os.cpu_count() or 1), chunk=4096)
+    # the forward kernels alone: 65,536 device-resident queries, CUDA events
+    Xq, _ = S.query_features(S.QUERY_SEED0, args.sur_queries, args.sur_n, args.sur_l)
+    X = torch.as_tensor(Xq, device="cuda")
+    Y = torch.empty((X.shape[0], S.N_HYDRO_OUT), dtype=torch.float32, device="cuda")
+    stream = torch.cuda.current_stream()
+    for _ in range(3):
+        A.asx_mlp_forward(model.handle, X.shape[0], X.data_ptr(), Y.data_ptr(), A.ASX_PTR_DEVICE)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    reps = 20
+    torch.cuda.synchronize()
+    e0.record(stream)
+    for _ in range(reps):
+        A.asx_mlp_forward(model.handle, X.shape[0], X.data_ptr(), Y.data_ptr(), A.ASX_PTR_DEVICE)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1) / reps
+    model.close()
+    tflops = MLP_FLOP_PER_QUERY * X.shape[0] / (ms / 1e3) / 1e12
+    rep["inference"] = {"queries": int(X.shape[0]), "ms": ms, "queries_per_s": X.shape[0] / (ms / 1e3),
+                        "roofline": {"bound": "tensor", "achieved": tflops, "peak": bf16_peak, "unit": "TFLOP/s",
+                                     "frac": tflops / bf16_peak, "traffic": None,
+                                     "peak_source": "measured bf16 (burst)" if peak_kind == "measured" else "fallback",
+                                     "note": f"{MLP_FLOP_PER_QUERY} algorithmic FLOP per query "
+                                             "(the kernel also multiplies layer 1's zero padding to K=64)"}}
+    return rep
+
+
 def run_reference(args):
     ws, rank = _dist()
     if rank != 0:
@@ -373,6 +422,13 @@ def main():
                     help="scenarios of the ensemble section (0 = skip it)")
     ap.add_argument("--ens-t-end", type=float, default=200.0,
                     help="simulated time of each ensemble scenario [s]")
+    ap.add_argument("--sur-train", type=int, default=16384,
+                    help="solver runs the surrogate trains on (0 = skip the surrogate section)")
+    ap.add_argument("--sur-held", type=int, default=1000)
+    ap.add_argument("--sur-queries", type=int, default=65536)
+    ap.add_argument("--sur-epochs", type=int, default=100)
+    ap.add_argument("--sur-n", type=int, default=64, help="surrogate members' raster side [cells]")
+    ap.add_argument("--sur-l", type=float, default=8.0, help="surrogate members' hexagon edge [m]")
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)
     out = run_reference(args) if args.impl == "reference" else run_cuda(args)

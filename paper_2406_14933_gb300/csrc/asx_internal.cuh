@@ -12,6 +12,10 @@ namespace asx {
 
 constexpr int kPitchAlign = 32;          // row pitch of every field, in elements
 constexpr int kStripW = 128;             // columns of a strip-kernel tile
+#ifndef ASX_STRIP_RB
+#define ASX_STRIP_RB 2
+#endif
+constexpr int kStripChunkRows = ASX_STRIP_RB;   // rows of every strip-kernel TMA box
 constexpr int kFrameCells = 256;         // frame cells per frame CTA of the strip kernel
 constexpr int kMaxRain = ASX_MAX_RAIN;
 constexpr int kMaxClasses = ASX_MAX_CLASSES;
@@ -94,15 +98,14 @@ struct StepArgs {
 };
 
 // TMA descriptors of the fields, per state parity (strip kernel).  mhi/v1/v2/z/theta
-// boxes are (kStripW + 8) x 2 floats; mlo boxes kStripW x 2 floats; class boxes
-// (kStripW + 16) x 2 bytes.
+// boxes are (kStripW + 8) x kStripChunkRows floats; mlo boxes kStripW x kStripChunkRows
+// floats; class boxes (kStripW + 16) x kStripChunkRows bytes.
 struct StripMaps {
     CUtensorMap mhi[2], v1[2], v2[2], mlo[2];
     CUtensorMap z, th;
 };
 
 // ---- launchers (kernels.cu, step_strip.cu) ----
-size_t step_strip_smem();
 void step_strip_layout(StepArgs &a);     // fills the interior / frame fields and nblocks
 cudaError_t step_strip_configure();
 cudaError_t launch_step_strip(const StepArgs &a, const StripMaps &maps, cudaStream_t s);

@@ -19,6 +19,7 @@
 #include <cuda_bf16.h>
 
 #include <cmath>
+#include <cstdlib>
 #include <cstdint>
 #include <cstring>
 #include <new>
@@ -399,11 +400,293 @@ constexpr long long oW1 = 0, oB1 = oW1 + (long long)kHid * kInPad, oW2 = oB1 + k
 }  // namespace
 }  // namespace asx
 
+namespace asx {
+namespace {
+
+// ----------------------------------------------------------------- the fused forward pass
+//
+// One CTA (four warps) carries a tile of 128 queries through all four layers: the input
+// tile (BF16, K padded to 64) and the activations (128 x 256 BF16) stay in shared memory
+// in the tensor core's core-matrix layout, every product accumulates in one 256-column
+// TMEM accumulator, and each layer's epilogue (bias, ReLU, BF16) writes the next layer's
+// operand straight back to shared memory.  The weights come from a copy kept in exactly
+// the shared-memory image (per layer, K/64 chunks of N x 64 core matrices), so a layer's
+// weights arrive with a few bulk copies (cp.async.bulk) on an mbarrier: W1 into the
+// activation buffer (dead until layer 1's epilogue), W2..W4 into a 128 KB weight buffer,
+// each as soon as the previous layer's MMAs have finished reading it.  CTAs are persistent
+// over the tiles.  Shared memory: 16 KB input + 64 KB activations + 128 KB weights.
+
+constexpr int kFusedThreads = 128;
+constexpr unsigned kWtBytes1 = (unsigned)kHid * kInPad * 2;   // W1: 32 KB
+constexpr unsigned kWtBytesH = (unsigned)kHid * kHid * 2;     // W2, W3: 128 KB each
+constexpr unsigned kWtBytes4 = (unsigned)kOut * kHid * 2;     // W4: 64 KB
+constexpr unsigned kWtOff1 = 0, kWtOff2 = kWtBytes1, kWtOff3 = kWtOff2 + kWtBytesH, kWtOff4 = kWtOff3 + kWtBytesH;
+constexpr unsigned kWtTotal = kWtOff4 + kWtBytes4;
+constexpr int kSmX = kTM * kInPad * 2;                        // 16 KB
+constexpr int kSmAct = kTM * kHid * 2;                        // 64 KB
+constexpr int kFusedSmem = kSmX + kSmAct + (int)kWtBytesH + 128;
+
+// Byte offset of element (r, k) of an R-row K-major operand stored as K/64 chunks of
+// R x 64 in core-matrix layout (chunk c at c * R * 128 bytes).
+__device__ __forceinline__ unsigned cm_off_k(int R, int r, int k)
+{
+    return (unsigned)((k >> 6) * R * 128) + cm_off(r, k & 63);
+}
+
+// The BF16 weights (row-major N x K, W1 | W2 | W3 | W4) into the image the fused kernel
+// copies to shared memory; 8 consecutive k of one row (16 bytes) per thread.
+__global__ void tile_weights_kernel(const __nv_bfloat16 *wb, unsigned char *wt)
+{
+    long long u = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    long long src = 0, dst = 0;
+#pragma unroll
+    for (int l = 0; l < 4; l++) {
+        const int N = l == 3 ? kOut : kHid, K = l == 0 ? kInPad : kHid;
+        const long long units = (long long)N * K / 8;
+        if (u < units) {
+            const int r = (int)(u / (K / 8)), k = (int)(u % (K / 8)) * 8;
+            const uint4 v = *reinterpret_cast<const uint4 *>(wb + src + (long long)r * K + k);
+            *reinterpret_cast<uint4 *>(wt + dst + cm_off_k(N, r, k)) = v;
+            return;
+        }
+        u -= units;
+        src += (long long)N * K;
+        dst += (long long)N * K * 2;
+    }
+}
+
+struct FusedArgs {
+    const float *x;                // batch x 36 FP32, rows 16-byte aligned
+    float *y;                      // batch x 128 FP32, 16-byte aligned
+    const unsigned char *wt;       // weight image, kWtTotal bytes
+    const float *b1, *b2, *b3, *b4;
+    int batch;
+    int *err;
+};
+
+__device__ __forceinline__ void mbar_expect(unsigned long long *bar, unsigned bytes)
+{
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(su32(bar)), "r"(bytes) : "memory");
+}
+
+// Global -> shared bulk copy of `bytes` (a multiple of 16, both addresses 16-byte aligned)
+// completing on `bar`, issued in pieces of 32 KB; one thread.
+__device__ __forceinline__ void load_image(unsigned char *dst, const unsigned char *src, unsigned bytes,
+                                           unsigned long long *bar)
+{
+    mbar_expect(bar, bytes);
+    for (unsigned o = 0; o < bytes; o += 32768u) {
+        const unsigned n = bytes - o < 32768u ? bytes - o : 32768u;
+        asm volatile(
+            "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+                su32(dst + o)),
+            "l"(src + o), "r"(n), "r"(su32(bar))
+            : "memory");
+    }
+}
+
+// D[128 x N] = A[128 x 16 ns] . B[N x 16 ns]^T, A and B in chunked core-matrix layout.
+__device__ __forceinline__ void layer_mma(unsigned tmem, const unsigned char *a, const unsigned char *b, int N,
+                                          int ns)
+{
+    const unsigned idesc = instr_desc(N);
+    for (int s = 0; s < ns; s++) {
+        const unsigned long long da = smem_desc(su32(a) + (unsigned)((s >> 2) * kTM * 128 + (s & 3) * 256), 128, 1024);
+        const unsigned long long db = smem_desc(su32(b) + (unsigned)((s >> 2) * N * 128 + (s & 3) * 256), 128, 1024);
+        tc_mma(tmem, da, db, idesc, s > 0 ? 1u : 0u);
+    }
+}
+
+// Hidden-layer epilogue of accumulator row r (this thread's TMEM lane): + bias, ReLU,
+// BF16 (round to nearest even), into the activation image.
+__device__ __forceinline__ void epi_hidden(unsigned trow, const float *__restrict__ bias, unsigned char *act, int r)
+{
+    for (int nc = 0; nc < kHid; nc += 16) {
+        float v[16];
+        tc_ld16(trow + (unsigned)nc, v);
+        unsigned w[8];
+#pragma unroll
+        for (int j = 0; j < 8; j++) {
+            const float a = fmaxf(v[2 * j] + __ldg(bias + nc + 2 * j), 0.0f);
+            const float b = fmaxf(v[2 * j + 1] + __ldg(bias + nc + 2 * j + 1), 0.0f);
+            const __nv_bfloat162 h = __floats2bfloat162_rn(a, b);
+            w[j] = *reinterpret_cast<const unsigned *>(&h);
+        }
+        *reinterpret_cast<uint4 *>(act + cm_off_k(kTM, r, nc)) = make_uint4(w[0], w[1], w[2], w[3]);
+        *reinterpret_cast<uint4 *>(act + cm_off_k(kTM, r, nc + 8)) = make_uint4(w[4], w[5], w[6], w[7]);
+    }
+}
+
+__global__ void __launch_bounds__(kFusedThreads, 1) mlp_fused_fwd_kernel(const FusedArgs f)
+{
+    extern __shared__ __align__(128) unsigned char fsm[];
+    unsigned char *base = fsm + ((128u - (su32(fsm) & 127u)) & 127u);
+    unsigned char *sX = base, *sAct = base + kSmX, *sW = base + kSmX + kSmAct;
+    __shared__ __align__(8) unsigned long long bar_a, bar_w, bar_m;   // W1 image, weight buffer, MMAs
+    __shared__ unsigned tmem_base;
+    const int tid = threadIdx.x, warp = tid >> 5;
+    const int ntiles = (f.batch + kTM - 1) / kTM;
+    if (warp == 0) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(su32(&tmem_base)),
+                     "r"(kHid)
+                     : "memory");
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+    }
+    if (tid == 0) {
+        mbar_init1(&bar_a);
+        mbar_init1(&bar_w);
+        mbar_init1(&bar_m);
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    __syncthreads();
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    const unsigned tmem = tmem_base;
+    const unsigned trow = tmem + ((unsigned)(warp * 32) << 16);
+    unsigned pa = 0, pw = 0, pm = 0;          // phases of the three barriers
+    int a_out = 0, w_out = 0, m_out = 0;      // completions issued but not yet waited for
+    bool ok = true;
+    if (tid == 0 && (int)blockIdx.x < ntiles) {
+        load_image(sAct, f.wt + kWtOff1, kWtBytes1, &bar_a);
+        load_image(sW, f.wt + kWtOff2, kWtBytesH, &bar_w);
+    }
+    if ((int)blockIdx.x < ntiles) a_out = w_out = 1;
+    const unsigned char *wnext[3] = {f.wt + kWtOff3, f.wt + kWtOff4, nullptr};
+    const unsigned wbytes[3] = {kWtBytesH, kWtBytes4, 0};
+    const float *bias[3] = {f.b1, f.b2, f.b3};
+    for (int t = blockIdx.x; t < ntiles && ok; t += gridDim.x) {
+        const int m0 = t * kTM;
+        // ---- input tile: thread r converts query row m0 + r to BF16, K padded to 64
+        {
+            const int m = m0 + tid;
+            float xv[40];
+            if (m < f.batch) {
+                const float4 *xr = reinterpret_cast<const float4 *>(f.x + (size_t)m * kIn);
+#pragma unroll
+                for (int q = 0; q < kIn / 4; q++) {
+                    const float4 v = xr[q];
+                    xv[4 * q] = v.x;
+                    xv[4 * q + 1] = v.y;
+                    xv[4 * q + 2] = v.z;
+                    xv[4 * q + 3] = v.w;
+                }
+            } else {
+#pragma unroll
+                for (int q = 0; q < kIn; q++) xv[q] = 0.0f;
+            }
+#pragma unroll
+            for (int q = kIn; q < 40; q++) xv[q] = 0.0f;
+#pragma unroll
+            for (int kg = 0; kg < kInPad / 8; kg++) {
+                unsigned w[4] = {0u, 0u, 0u, 0u};
+                if (kg < 5) {
+#pragma unroll
+                    for (int j = 0; j < 4; j++) {
+                        const __nv_bfloat162 h = __floats2bfloat162_rn(xv[8 * kg + 2 * j], xv[8 * kg + 2 * j + 1]);
+                        w[j] = *reinterpret_cast<const unsigned *>(&h);
+                    }
+                }
+                *reinterpret_cast<uint4 *>(sX + cm_off(tid, kg * 8)) = make_uint4(w[0], w[1], w[2], w[3]);
+            }
+        }
+        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+        __syncthreads();
+        // ---- layers 1..4
+        for (int l = 0; l < 4; l++) {
+            if (tid == 0) {
+                if (l == 0) {
+                    ok = ok && mbar_wait_bounded1(&bar_a, pa);
+                } else {
+                    ok = ok && mbar_wait_bounded1(&bar_w, pw);
+                }
+                if (ok) {
+                    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+                    if (l == 0) layer_mma(tmem, sX, sAct, kHid, kInPad / 16);
+                    else layer_mma(tmem, sAct, sW, l == 3 ? kOut : kHid, kHid / 16);
+                    tc_commit(&bar_m);
+                    m_out = 1;
+                }
+            }
+            if (l == 0) {
+                pa ^= 1u;
+                a_out = 0;
+            } else {
+                pw ^= 1u;
+                w_out = 0;
+            }
+            ok = !__syncthreads_or(!ok);
+            if (!ok) break;
+            ok = mbar_wait_bounded1(&bar_m, pm);
+            pm ^= 1u;
+            m_out = 0;
+            asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+            if (__syncthreads_or(!ok)) {
+                ok = false;
+                break;
+            }
+            // the MMAs are done with their operands: refill the freed buffers
+            if (l >= 1 && l <= 2) {
+                if (tid == 0) load_image(sW, wnext[l - 1], wbytes[l - 1], &bar_w);
+                w_out = 1;
+            }
+            if (l == 3 && t + (int)gridDim.x < ntiles) {
+                if (tid == 0) {
+                    load_image(sAct, f.wt + kWtOff1, kWtBytes1, &bar_a);
+                    load_image(sW, f.wt + kWtOff2, kWtBytesH, &bar_w);
+                }
+                a_out = w_out = 1;
+            }
+            if (l < 3) {
+                epi_hidden(trow, bias[l], sAct, tid);
+                asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+            } else {
+                const int m = m0 + tid;
+                for (int nc = 0; nc < kOut; nc += 16) {
+                    float v[16];
+                    tc_ld16(trow + (unsigned)nc, v);
+                    if (m < f.batch) {
+                        float4 *yr = reinterpret_cast<float4 *>(f.y + (size_t)m * kOut + nc);
+#pragma unroll
+                        for (int q = 0; q < 4; q++)
+                            yr[q] = make_float4(v[4 * q] + __ldg(f.b4 + nc + 4 * q), v[4 * q + 1] + __ldg(f.b4 + nc + 4 * q + 1),
+                                                v[4 * q + 2] + __ldg(f.b4 + nc + 4 * q + 2),
+                                                v[4 * q + 3] + __ldg(f.b4 + nc + 4 * q + 3));
+                    }
+                }
+            }
+            asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+            __syncthreads();
+        }
+    }
+    if (!ok) {
+        // a wait ran out: flag it, and let the copies and MMAs still in flight land
+        // (bounded) before the tensor memory is released
+        if (tid == 0) {
+            if (f.err) atomicOr(f.err, 1);
+            if (a_out) mbar_wait_bounded1(&bar_a, pa);
+            if (w_out) mbar_wait_bounded1(&bar_w, pw);
+            if (m_out) mbar_wait_bounded1(&bar_m, pm);
+        }
+        __syncthreads();
+    }
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    __syncthreads();
+    if (warp == 0) {
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(kHid) : "memory");
+    }
+}
+
+}  // namespace
+}  // namespace asx
+
 struct asx_mlp {
     int device = 0, max_batch = 0;
     cudaStream_t stream = nullptr;
     float *w = nullptr, *g = nullptr, *m = nullptr, *v = nullptr;   // FP32 master, grad, Adam moments
     __nv_bfloat16 *wb = nullptr;                                    // BF16 copies of W1..W4 (padded layout)
+    unsigned char *wt = nullptr;                                    // the same in the fused kernel's image
+    bool wt_dirty = true;                                           // wt lags behind wb
+    int n_sm = 0;
     __nv_bfloat16 *x0 = nullptr, *a1 = nullptr, *a2 = nullptr, *a3 = nullptr, *dy = nullptr, *dz = nullptr,
                   *dz2 = nullptr;
     float *y = nullptr, *xin = nullptr, *tin = nullptr, *loss = nullptr;
@@ -559,6 +842,32 @@ void padded_to_pack(const std::vector<float> &src, float *dst)
     std::memcpy(d, &src[oB1], sizeof(float) * (size_t)(kPadded - oB1));
 }
 
+// Forward pass of B queries x (device, 16-byte aligned) into y (device, 16-byte aligned)
+// by the fused kernel; refreshes the weight image first when the weights changed.
+cudaError_t fused_forward(asx_mlp *p, int B, const float *x, float *y)
+{
+    if (p->wt_dirty) {
+        const long long units = ((long long)kHid * kInPad + 2LL * kHid * kHid + (long long)kOut * kHid) / 8;
+        tile_weights_kernel<<<(unsigned)((units + 255) / 256), 256, 0, p->stream>>>(p->wb, p->wt);
+        cudaError_t e = cudaGetLastError();
+        if (e != cudaSuccess) return e;
+        p->wt_dirty = false;
+    }
+    FusedArgs f{x, y, p->wt, p->w + oB1, p->w + oB2, p->w + oB3, p->w + oB4, B, p->err};
+    const int ntiles = (B + kTM - 1) / kTM;
+    const int grid = ntiles < p->n_sm ? ntiles : p->n_sm;
+    mlp_fused_fwd_kernel<<<grid, kFusedThreads, kFusedSmem, p->stream>>>(f);
+    return cudaGetLastError();
+}
+
+bool fused_enabled()
+{
+    const char *e = std::getenv("ASX_MLP_FUSED");
+    return !(e && e[0] == '0');
+}
+
+bool aligned16(const void *q) { return ((uintptr_t)q & 15u) == 0; }
+
 asx_status stage_inputs(asx_mlp *p, int B, const float *x, const float *t, int kind)
 {
     const cudaMemcpyKind mk = kind == ASX_PTR_HOST ? cudaMemcpyHostToDevice : cudaMemcpyDeviceToDevice;
@@ -607,6 +916,7 @@ asx_status asx_mlp_create(int device, void *cuda_stream, int max_batch, asx_mlp 
     alloc((void **)&p->m, sizeof(float) * kPadded);
     alloc((void **)&p->v, sizeof(float) * kPadded);
     alloc((void **)&p->wb, sizeof(__nv_bfloat16) * nwb);
+    alloc((void **)&p->wt, kWtTotal);
     alloc((void **)&p->x0, sizeof(__nv_bfloat16) * B * kInPad);
     alloc((void **)&p->a1, sizeof(__nv_bfloat16) * B * kHid);
     alloc((void **)&p->a2, sizeof(__nv_bfloat16) * B * kHid);
@@ -624,6 +934,9 @@ asx_status asx_mlp_create(int device, void *cuda_stream, int max_batch, asx_mlp 
     if (e == cudaSuccess) e = cudaMemsetAsync(p->v, 0, sizeof(float) * kPadded, p->stream);
     if (e == cudaSuccess) e = cudaMemsetAsync(p->err, 0, sizeof(int), p->stream);
     if (e == cudaSuccess) e = refresh_bf16(p);
+    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&p->n_sm, cudaDevAttrMultiProcessorCount, device);
+    if (e == cudaSuccess)
+        e = cudaFuncSetAttribute(mlp_fused_fwd_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, kFusedSmem);
     if (e == cudaSuccess) e = cudaStreamSynchronize(p->stream);
     if (e != cudaSuccess) {
         asx_mlp_destroy(p);
@@ -638,7 +951,7 @@ asx_status asx_mlp_destroy(asx_mlp *p)
     if (!p) return ASX_OK;
     cudaSetDevice(p->device);
     if (p->stream) cudaStreamSynchronize(p->stream);
-    void *ptrs[] = {p->w, p->g, p->m, p->v, p->wb, p->x0, p->a1, p->a2, p->a3, p->dy, p->dz, p->dz2,
+    void *ptrs[] = {p->w, p->g, p->m, p->v, p->wb, p->wt, p->x0, p->a1, p->a2, p->a3, p->dy, p->dz, p->dz2,
                     p->y, p->xin, p->tin, p->loss, p->err};
     for (void *q : ptrs) cudaFree(q);
     delete p;
@@ -663,6 +976,7 @@ asx_status asx_mlp_set_params(asx_mlp *p, const float *params, int kind)
     MLP_CUDA(p, cudaMemsetAsync(p->m, 0, sizeof(float) * kPadded, p->stream));
     MLP_CUDA(p, cudaMemsetAsync(p->v, 0, sizeof(float) * kPadded, p->stream));
     MLP_CUDA(p, refresh_bf16(p));
+    p->wt_dirty = true;
     MLP_CUDA(p, cudaStreamSynchronize(p->stream));
     p->adam_t = 0;
     return ASX_OK;
@@ -688,6 +1002,22 @@ asx_status asx_mlp_forward(asx_mlp *p, int batch, const float *x, float *y, int 
     if (kind != ASX_PTR_HOST && kind != ASX_PTR_DEVICE) return mfail(p, ASX_EINVAL, "bad ptr_kind");
     MLP_CUDA(p, cudaSetDevice(p->device));
     const cudaMemcpyKind back = kind == ASX_PTR_HOST ? cudaMemcpyDeviceToHost : cudaMemcpyDeviceToDevice;
+    if (batch < 1) return batch == 0 ? ASX_OK : mfail(p, ASX_EINVAL, "negative batch");
+    if (fused_enabled()) {
+        if (kind == ASX_PTR_DEVICE && aligned16(x) && aligned16(y)) {
+            MLP_CUDA(p, fused_forward(p, batch, x, y));      // the whole batch in one launch
+            return ASX_OK;
+        }
+        const cudaMemcpyKind in = kind == ASX_PTR_HOST ? cudaMemcpyHostToDevice : cudaMemcpyDeviceToDevice;
+        for (int b0 = 0; b0 < batch; b0 += p->max_batch) {
+            const int B = batch - b0 < p->max_batch ? batch - b0 : p->max_batch;
+            MLP_CUDA(p, cudaMemcpyAsync(p->xin, x + (size_t)b0 * kIn, sizeof(float) * (size_t)B * kIn, in, p->stream));
+            MLP_CUDA(p, fused_forward(p, B, p->xin, p->y));
+            MLP_CUDA(p, cudaMemcpyAsync(y + (size_t)b0 * kOut, p->y, sizeof(float) * (size_t)B * kOut, back, p->stream));
+        }
+        if (kind == ASX_PTR_HOST) return check_err(p);
+        return ASX_OK;
+    }
     for (int b0 = 0; b0 < batch; b0 += p->max_batch) {
         const int B = batch - b0 < p->max_batch ? batch - b0 : p->max_batch;
         asx_status st = stage_inputs(p, B, x + (size_t)b0 * kIn, nullptr, kind);
@@ -751,6 +1081,7 @@ asx_status asx_mlp_train_step(asx_mlp *p, int batch, const float *x, const float
             l >= 0 ? weight_decay : 0.0f);
     }
     MLP_CUDA(p, cudaGetLastError());
+    p->wt_dirty = true;
     if (loss) {
         MLP_CUDA(p, cudaMemcpyAsync(loss, p->loss, sizeof(float), cudaMemcpyDeviceToHost, p->stream));
         return check_err(p);

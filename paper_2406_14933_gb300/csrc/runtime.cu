@@ -318,16 +318,16 @@ asx_status asx_create_raster(const asx_raster_desc *desc, asx_raster **out)
         bool ok = true;
         const int bf = kStripW + 8;
         for (int p = 0; p < 2; p++) {
-            ok = ok && make_map(&r->maps.mhi[p], a.mhi[p], false, r->rows, r->cols, r->pitch, bf, 2);
-            ok = ok && make_map(&r->maps.v1[p], a.v1[p], false, r->rows, r->cols, r->pitch, bf, 2);
-            ok = ok && make_map(&r->maps.v2[p], a.v2[p], false, r->rows, r->cols, r->pitch, bf, 2);
-            ok = ok && make_map(&r->maps.mlo[p], a.mlo[p], false, r->rows, r->cols, r->pitch, kStripW, 2);
+            ok = ok && make_map(&r->maps.mhi[p], a.mhi[p], false, r->rows, r->cols, r->pitch, bf, kStripChunkRows);
+            ok = ok && make_map(&r->maps.v1[p], a.v1[p], false, r->rows, r->cols, r->pitch, bf, kStripChunkRows);
+            ok = ok && make_map(&r->maps.v2[p], a.v2[p], false, r->rows, r->cols, r->pitch, bf, kStripChunkRows);
+            ok = ok && make_map(&r->maps.mlo[p], a.mlo[p], false, r->rows, r->cols, r->pitch, kStripW, kStripChunkRows);
         }
-        ok = ok && make_map(&r->maps.z, (void *)a.z, false, r->rows, r->cols, r->pitch, bf, 2);
+        ok = ok && make_map(&r->maps.z, (void *)a.z, false, r->rows, r->cols, r->pitch, bf, kStripChunkRows);
         if (desc->n_classes > 0)
-            ok = ok && make_map(&r->maps.th, (void *)a.cls, true, r->rows, r->cols, r->pitch, kStripW + 16, 2);
+            ok = ok && make_map(&r->maps.th, (void *)a.cls, true, r->rows, r->cols, r->pitch, kStripW + 16, kStripChunkRows);
         else
-            ok = ok && make_map(&r->maps.th, (void *)a.theta, false, r->rows, r->cols, r->pitch, bf, 2);
+            ok = ok && make_map(&r->maps.th, (void *)a.theta, false, r->rows, r->cols, r->pitch, bf, kStripChunkRows);
         if (!ok || step_strip_configure() != cudaSuccess) {
             asx_destroy_raster(r);
             return ASX_ECUDA;

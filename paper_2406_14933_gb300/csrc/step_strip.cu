@@ -8,7 +8,8 @@
 //   * rows r0-1 .. r0+H of every field (one halo row above and below, halo columns left
 //     and right) stream into a shared-memory ring of 2-row chunks through TMA tensor
 //     loads (cp.async.bulk.tensor.2d) that complete on mbarriers; lane 0 refills a chunk
-//     once the warp has moved past it;
+//     once every row of it is finished, so the halo cells at the tile ends are read from
+//     the ring when needed instead of being held in registers;
 //   * the warp walks the tile row by row; the edges between row r and r+1 and the east
 //     edges of row r are evaluated by the lane that owns their lower cell; a lane also
 //     evaluates the one horizontal and one diagonal edge it shares with each neighbouring
@@ -25,15 +26,23 @@
 // float64 rounding.
 #include <cuda.h>
 
+#include <type_traits>
+
 #include "device_common.cuh"
 
 namespace asx {
 
 namespace {
 
+#ifndef ASX_STRIP_NC
+#define ASX_STRIP_NC 2
+#endif
+#ifndef ASX_STRIP_MINB
+#define ASX_STRIP_MINB 16
+#endif
 constexpr int kSW = kStripW;           // tile width in cells
-constexpr int kRB = 2;                 // rows per ring chunk
-constexpr int kNC = 3;                 // chunks in the ring
+constexpr int kRB = kStripChunkRows;   // rows per ring chunk (= TMA box height)
+constexpr int kNC = ASX_STRIP_NC;      // chunks in the ring
 constexpr int kBXF = kSW + 8;          // float box width (from column c0 - 4)
 constexpr int kBXC = kSW + 16;         // uint8 box width (from column c0 - 4)
 constexpr int kXO = 4;                 // ring x index of column c0 (float fields)
@@ -44,17 +53,24 @@ constexpr int kXOC = 4;                // ring x index of column c0 (class field
 // 128 bytes).
 static_assert(kXOC == kXO && (kBXC % 16) == 0 && ((kBXF * 4) % 16) == 0, "TMA box alignment");
 
-struct __align__(128) FBox { float v[kRB][kBXF]; float pad[(1152 - kRB * kBXF * 4) / 4]; };
+constexpr int kFBoxBytes = (kRB * kBXF * 4 + 127) / 128 * 128;
+struct __align__(128) FBox { float v[kRB][kBXF]; float pad[(kFBoxBytes - kRB * kBXF * 4) / 4]; };
 struct __align__(128) LBox { float v[kRB][kSW]; };
+struct __align__(128) CBox { uint8_t v[kRB][kBXC]; };
+static_assert(sizeof(FBox) == kFBoxBytes && kFBoxBytes > kRB * kBXF * 4, "box padding");
+
+// One ring chunk: kRB rows of every field; the porosity slot holds theta (float) or, in
+// land-cover-class mode, the uint8 class ids.
+template <bool CLS>
 struct __align__(128) Chunk {
-    FBox mhi, v1, v2, z, th;           // th: theta (float) or, reinterpreted, class ids
+    FBox mhi, v1, v2, z;
+    typename std::conditional<CLS, CBox, FBox>::type th;
     LBox mlo;
 };
-static_assert(sizeof(FBox) == 1152, "box padding");
-static_assert(kRB * kBXC <= (int)sizeof(FBox), "class box fits the theta slot");
 
+template <bool CLS>
 struct StripSmem {
-    Chunk ring[kNC];
+    Chunk<CLS> ring[kNC];
     unsigned long long bar[kNC];
 };
 
@@ -174,20 +190,21 @@ __device__ __forceinline__ Cell pick(bool take_b, const Cell &a, const Cell &b)
     return o;
 }
 
-// Per-lane state of one row: four cells, their 1/theta and friction coefficients, the
-// accumulators of their edge terms, and the halo cells at both ends of the tile row.
+// Per-lane state of one row: four cells, their porosity (theta, or in class mode the
+// class id's bits) and the accumulators of their edge terms.  The halo cells at both ends
+// of the tile row are read from the ring when needed.
 struct Row {
     Cell X[4];
-    float rt[4], ka[4], kb[4];
+    float th[4];
     Acc A[4];
-    Cell hw, he;       // cells at columns c0 - 1 and c0 + kSW
 };
 
 // ----------------------------------------------------------------- the tile
 
+template <bool CLS>
 struct Tile {
     const StepArgs &a;
-    StripSmem &S;
+    StripSmem<CLS> &S;
     const StripMaps &maps;
     int par, np, lane, c0, r0, Hn, nchunks;
     float kappa, kl2, qr, dtf;
@@ -199,7 +216,7 @@ struct Tile {
     int jown;          // first local row this tile writes
     bool lane_own;     // this lane's four columns are written by this tile
 
-    __device__ __forceinline__ Tile(const StepArgs &a_, StripSmem &S_, const StripMaps &m_, int c0_,
+    __device__ __forceinline__ Tile(const StepArgs &a_, StripSmem<CLS> &S_, const StripMaps &m_, int c0_,
                                     int r0_, int own_c, int own_r)
         : a(a_), S(S_), maps(m_)
     {
@@ -229,23 +246,23 @@ struct Tile {
             atomicOr(&a.ctl->err, kErrTimeout);
             return;
         }
-        Chunk &ch = S.ring[k % kNC];
+        Chunk<CLS> &ch = S.ring[k % kNC];
         unsigned long long *bar = &S.bar[k % kNC];
         const int y = r0 - 1 + k * kRB;
         const unsigned bytes = (unsigned)(4 * kRB * kBXF * 4 + kRB * kSW * 4) +
-                               (unsigned)(a.cls ? kRB * kBXC : kRB * kBXF * 4);
+                               (unsigned)(CLS ? kRB * kBXC : kRB * kBXF * 4);
         mbar_expect_tx(bar, bytes);
         tma_load_2d(&ch.mhi.v[0][0], &maps.mhi[par], c0 - kXO, y, bar);
         tma_load_2d(&ch.v1.v[0][0], &maps.v1[par], c0 - kXO, y, bar);
         tma_load_2d(&ch.v2.v[0][0], &maps.v2[par], c0 - kXO, y, bar);
         tma_load_2d(&ch.z.v[0][0], &maps.z, c0 - kXO, y, bar);
-        if (a.cls) tma_load_2d(&ch.th.v[0][0], &maps.th, c0 - kXOC, y, bar);
+        if constexpr (CLS) tma_load_2d(&ch.th.v[0][0], &maps.th, c0 - kXOC, y, bar);
         else tma_load_2d(&ch.th.v[0][0], &maps.th, c0 - kXO, y, bar);
         tma_load_2d(&ch.mlo.v[0][0], &maps.mlo[par], c0, y, bar);
     }
 
     // Halo cell of ring row rr at float index x.
-    __device__ __forceinline__ Cell ring_cell(const Chunk &ch, int rr, int x) const
+    __device__ __forceinline__ Cell ring_cell(const Chunk<CLS> &ch, int rr, int x) const
     {
         Cell c;
         c.m = ch.mhi.v[rr][x];
@@ -253,27 +270,38 @@ struct Tile {
         c.v2 = ch.v2.v[rr][x];
         c.z = ch.z.v[rr][x];
         float rt;
-        if (a.cls) rt = a.cls_rth[reinterpret_cast<const uint8_t *>(&ch.th.v[0][0])[rr * kBXC + x - kXO + kXOC]];
+        if constexpr (CLS) rt = a.cls_rth[ch.th.v[rr][x - kXO + kXOC]];
         else rt = fast_rcp(ch.th.v[rr][x]);
         c.h = __fmul_rn(c.m, rt);
         return c;
+    }
+
+    // Halo cell of local row jr at ring x index x (the row's chunk is still resident).
+    __device__ __forceinline__ Cell halo(int jr, int x) const
+    {
+        return ring_cell(S.ring[(jr / kRB) % kNC], jr % kRB, x);
+    }
+
+    // Local row jr is done (its edges and the ones to the row below are in): once every
+    // row of its chunk is, refill the chunk's slot with the chunk kNC further on.
+    __device__ __forceinline__ void release(int jr)
+    {
+        if ((jr + 1) % kRB != 0) return;
+        const int k = jr / kRB;
+        __syncwarp();
+        if (lane == 0 && k + kNC < nchunks) {
+            asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+            issue(k + kNC);
+            n_issued = k + kNC + 1;
+        }
     }
 
     // Loads local row jr (global r0 - 1 + jr) into R.
     __device__ __forceinline__ void load(int jr, Row &R)
     {
         const int k = jr / kRB, rr = jr % kRB;
-        if (rr == 0) {
-            __syncwarp();
-            if (k >= 1 && lane == 0 && k - 1 + kNC < nchunks) {
-                // the warp is past chunk k-1: refill its slot
-                asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-                issue(k - 1 + kNC);
-                n_issued = k + kNC;
-            }
-            if (!mbar_wait_bounded(&S.bar[k % kNC], (unsigned)((k / kNC) & 1))) timed_out = true;
-        }
-        const Chunk &ch = S.ring[k % kNC];
+        if (rr == 0 && !mbar_wait_bounded(&S.bar[k % kNC], (unsigned)((k / kNC) & 1))) timed_out = true;
+        const Chunk<CLS> &ch = S.ring[k % kNC];
         const int x = kXO + 4 * lane;
         const float4 m4 = *reinterpret_cast<const float4 *>(&ch.mhi.v[rr][x]);
         const float4 u4 = *reinterpret_cast<const float4 *>(&ch.v1.v[rr][x]);
@@ -283,24 +311,21 @@ struct Tile {
         const float mm[4] = {m4.x, m4.y, m4.z, m4.w}, uu[4] = {u4.x, u4.y, u4.z, u4.w};
         const float ww[4] = {w4.x, w4.y, w4.z, w4.w}, zz[4] = {z4.x, z4.y, z4.z, z4.w};
         const float ll[4] = {l4.x, l4.y, l4.z, l4.w};
-        if (a.cls) {
-            const uchar4 c4 = *reinterpret_cast<const uchar4 *>(
-                reinterpret_cast<const uint8_t *>(&ch.th.v[0][0]) + rr * kBXC + kXOC + 4 * lane);
+        if constexpr (CLS) {
+            const uchar4 c4 = *reinterpret_cast<const uchar4 *>(&ch.th.v[rr][kXOC + 4 * lane]);
             const int cc[4] = {c4.x, c4.y, c4.z, c4.w};
 #pragma unroll
             for (int e = 0; e < 4; e++) {
-                R.rt[e] = a.cls_rth[cc[e]];
-                R.ka[e] = a.cls_a[cc[e]];
-                R.kb[e] = a.cls_b[cc[e]];
+                R.th[e] = __int_as_float(cc[e]);
+                R.X[e].h = __fmul_rn(mm[e], a.cls_rth[cc[e]]);
             }
         } else {
             const float4 t4 = *reinterpret_cast<const float4 *>(&ch.th.v[rr][x]);
             const float tt[4] = {t4.x, t4.y, t4.z, t4.w};
 #pragma unroll
             for (int e = 0; e < 4; e++) {
-                R.rt[e] = fast_rcp(tt[e]);
-                R.ka[e] = a.alpha_p * (1.0f - tt[e]);
-                R.kb[e] = tt[e] * a.alpha_s;
+                R.th[e] = tt[e];
+                R.X[e].h = __fmul_rn(mm[e], fast_rcp(tt[e]));
             }
         }
 #pragma unroll
@@ -309,21 +334,18 @@ struct Tile {
             R.X[e].v1 = uu[e];
             R.X[e].v2 = ww[e];
             R.X[e].z = zz[e];
-            R.X[e].h = __fmul_rn(mm[e], R.rt[e]);
             R.A[e] = Acc{mm[e], ll[e], 0.0f, 0.0f};
         }
-        R.hw = ring_cell(ch, rr, kXO - 1);
-        R.he = ring_cell(ch, rr, kXO + kSW);
     }
 
     // Edge terms between row j (C, global row r) and row j+1 (N), and the east edges of
     // row r.  own: row r is updated by this tile; nown: row r+1 is.  ODD: parity of r.
     template <int ODD>
-    __device__ __forceinline__ void edges(Row &C, Row &N, bool own, bool nown)
+    __device__ __forceinline__ void edges(int j, Row &C, Row &N, bool own, bool nown)
     {
         // neighbour cells held by the lanes to the west / east, or the halo at tile ends
-        const Cell Wc = pick(lane == 0, shfl_cell_up(C.X[3]), C.hw);
-        const Cell Ec = pick(lane == 31, shfl_cell_down(C.X[0]), C.he);
+        const Cell Wc = pick(lane == 0, shfl_cell_up(C.X[3]), halo(j, kXO - 1));
+        const Cell Ec = pick(lane == 31, shfl_cell_down(C.X[0]), halo(j, kXO + kSW));
         if (own) {
             // ---- east edges of row r (the west edge of c_0 is the west lane's, again)
             edge<0>(a, Wc, C.X[0], kl2, C.A[0], false, C.A[0], true);
@@ -333,7 +355,7 @@ struct Tile {
         }
         if (ODD) {
             // odd r: NE(c) = (r+1, c+1), NW(c) = (r+1, c)
-            const Cell On = pick(lane == 31, shfl_cell_down(N.X[0]), N.he);   // (r+1, c_3 + 1)
+            const Cell On = pick(lane == 31, shfl_cell_down(N.X[0]), halo(j + 1, kXO + kSW));   // (r+1, c_3 + 1)
 #pragma unroll
             for (int e = 0; e < 4; e++) {
                 edge<2>(a, C.X[e], N.X[e], kl2, C.A[e], own, N.A[e], nown);        // NW
@@ -344,7 +366,7 @@ struct Tile {
             edge<1>(a, Wc, N.X[0], kl2, N.A[0], false, N.A[0], nown);
         } else {
             // even r: NE(c) = (r+1, c), NW(c) = (r+1, c-1)
-            const Cell On = pick(lane == 0, shfl_cell_up(N.X[3]), N.hw);      // (r+1, c_0 - 1)
+            const Cell On = pick(lane == 0, shfl_cell_up(N.X[3]), halo(j + 1, kXO - 1));      // (r+1, c_0 - 1)
 #pragma unroll
             for (int e = 0; e < 4; e++) {
                 edge<1>(a, C.X[e], N.X[e], kl2, C.A[e], own, N.A[e], nown);        // NE
@@ -363,8 +385,20 @@ struct Tile {
         FF cl;
 #pragma unroll
         for (int e = 0; e < 4; e++) {
+            float rt, ka, kb;
+            if constexpr (CLS) {
+                const int k = __float_as_int(C.th[e]);
+                rt = a.cls_rth[k];
+                ka = a.cls_a[k];
+                kb = a.cls_b[k];
+            } else {
+                const float t = C.th[e];
+                rt = fast_rcp(t);
+                ka = a.alpha_p * (1.0f - t);
+                kb = t * a.alpha_s;
+            }
             o[e] = cell_update(C.A[e].hi, C.A[e].lo, C.A[e].m1, C.A[e].m2, C.X[e].m, C.X[e].v1, C.X[e].v2,
-                               C.rt[e], C.ka[e], C.kb[e], kappa, qr, dtf, a.g, cl);
+                               rt, ka, kb, kappa, qr, dtf, a.g, cl);
         }
         if (!lane_own) return;       // columns written by the neighbouring tile
         if (cl.hi != 0.0f || cl.lo != 0.0f) {
@@ -380,15 +414,18 @@ struct Tile {
         for (int e = 0; e < 4; e++) cwb = max(cwb, o[e].cbits);
     }
 
-    // One row step: load row j+1, evaluate the edges of row j, finish row j.
+    // One row step: load row j+1, evaluate the edges of row j, finish row j, free row j's
+    // ring space.
     template <int ODD>
     __device__ __forceinline__ void step_row(int j, Row &C, Row &N)
     {
         load(j + 1, N);
-        if (j + 1 < jown) return;           // rows above the ones this tile writes
-        const bool own = j >= jown, nown = j + 1 <= Hn;
-        edges<ODD>(C, N, own, nown);
-        if (own) finish(r0 - 1 + j, C);
+        if (j + 1 >= jown) {                // else: rows above the ones this tile writes
+            const bool own = j >= jown, nown = j + 1 <= Hn;
+            edges<ODD>(j, C, N, own, nown);
+            if (own) finish(r0 - 1 + j, C);
+        }
+        release(j);
     }
 
     __device__ void run()
@@ -449,11 +486,13 @@ __device__ __forceinline__ void frame_cells(const StepArgs &a, long long f0, uns
     }
 }
 
-__global__ void __launch_bounds__(32) step_strip_kernel(const StepArgs a, const __grid_constant__ StripMaps maps)
+// 128 registers and a 2 x 2-row ring (13.6 KB) let 15-16 one-warp CTAs share an SM
+template <bool CLS>
+__global__ void __launch_bounds__(32, ASX_STRIP_MINB) step_strip_kernel(const StepArgs a, const __grid_constant__ StripMaps maps)
 {
     extern __shared__ __align__(128) unsigned char smem_raw[];
     // TMA destinations need 128-byte alignment: align the dynamic block by hand
-    StripSmem &S = *reinterpret_cast<StripSmem *>(
+    StripSmem<CLS> &S = *reinterpret_cast<StripSmem<CLS> *>(
         smem_raw + ((128u - (smem_u32(smem_raw) & 127u)) & 127u));
     if (!a.ctl->active) return;
     unsigned cwb = 0u;
@@ -465,7 +504,7 @@ __global__ void __launch_bounds__(32) step_strip_kernel(const StepArgs a, const 
         const int own_c = strip < a.nstrips ? c0 : a.cx0 + a.nstrips * kSW;
         const int r0 = rblk < a.nrb ? a.ry0 + rblk * a.tile_rows : a.r_last;
         const int own_r = rblk < a.nrb ? r0 : a.ry0 + a.nrb * a.tile_rows;
-        Tile T(a, S, maps, c0, r0, own_c, own_r);
+        Tile<CLS> T(a, S, maps, c0, r0, own_c, own_r);
         T.run();
         if (__any_sync(0xffffffffu, T.timed_out)) {
             // a tensor copy did not arrive in time: flag the error, wait (bounded) for
@@ -491,7 +530,8 @@ __global__ void __launch_bounds__(32) step_strip_kernel(const StepArgs a, const 
 
 }  // namespace
 
-size_t step_strip_smem() { return sizeof(StripSmem) + 128; }
+template <bool CLS>
+size_t strip_smem() { return sizeof(StripSmem<CLS>) + 128; }
 
 void step_strip_layout(StepArgs &a)
 {
@@ -532,13 +572,18 @@ void step_strip_layout(StepArgs &a)
 
 cudaError_t step_strip_configure()
 {
-    return cudaFuncSetAttribute(step_strip_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                (int)step_strip_smem());
+    cudaError_t e = cudaFuncSetAttribute(step_strip_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)strip_smem<false>());
+    if (e != cudaSuccess) return e;
+    return cudaFuncSetAttribute(step_strip_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                (int)strip_smem<true>());
 }
 
 cudaError_t launch_step_strip(const StepArgs &a, const StripMaps &maps, cudaStream_t s)
 {
-    step_strip_kernel<<<a.nblocks, 32, step_strip_smem(), s>>>(a, maps);
+    // land-cover classes (uint8 ids and per-class tables) or per-cell theta
+    if (a.cls) step_strip_kernel<true><<<a.nblocks, 32, strip_smem<true>(), s>>>(a, maps);
+    else step_strip_kernel<false><<<a.nblocks, 32, strip_smem<false>(), s>>>(a, maps);
     return cudaGetLastError();
 }
 

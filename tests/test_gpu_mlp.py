@@ -77,3 +77,66 @@ def test_adam_training_reduces_loss(asx):
     final = float(np.mean((y - tt) ** 2))
     assert final < first / 10, (first, final)
     A.asx_mlp_destroy(p)
+
+
+@pytest.mark.parametrize("batch", [1, 127, 128, 129, 1000, 40000])
+def test_fused_forward_matches_layered(asx, batch, monkeypatch):
+    """The fused four-layer kernel against the layer-by-layer GEMMs: the same BF16
+    rounding points and the same FP32 accumulation order, device pointers (the whole
+    batch in one launch, beyond the handle's max_batch) and host pointers."""
+    import torch
+
+    from paper_2406_14933_gb300 import asx as A
+    rng = np.random.default_rng(batch)
+    theta = ref.init_params(rng).astype(np.float32)
+    theta[ref.N_PARAMS - 128:] = rng.standard_normal(128) * 0.1       # non-zero output bias
+    x = rng.standard_normal((batch, 36)).astype(np.float32)
+    p = A.asx_mlp_create(max_batch=1024)
+    A.asx_mlp_set_params(p, theta)
+    xd = torch.tensor(x, device="cuda")
+    yf = torch.empty((batch, 128), dtype=torch.float32, device="cuda")
+    A.asx_mlp_forward(p, batch, xd.data_ptr(), yf.data_ptr(), A.ASX_PTR_DEVICE)
+    yh = np.empty((batch, 128), np.float32)
+    A.asx_mlp_forward(p, batch, x, yh)                                   # host pointers
+    monkeypatch.setenv("ASX_MLP_FUSED", "0")
+    yl = np.empty((batch, 128), np.float32)
+    A.asx_mlp_forward(p, batch, x, yl)
+    monkeypatch.delenv("ASX_MLP_FUSED")
+    yf = yf.cpu().numpy()
+    scale = float(np.abs(yl).max())
+    assert np.abs(yf - yl).max() <= 1e-5 * scale
+    assert np.array_equal(yf, yh)
+    # misaligned device pointers take the staged path
+    xm = torch.empty(batch * 36 + 1, dtype=torch.float32, device="cuda")
+    xm[1:] = xd.reshape(-1)
+    ym = torch.empty(batch * 128 + 1, dtype=torch.float32, device="cuda")
+    A.asx_mlp_forward(p, batch, xm.data_ptr() + 4, ym.data_ptr() + 4, A.ASX_PTR_DEVICE)
+    assert np.array_equal(ym[1:].cpu().numpy().reshape(batch, 128), yf)
+    A.asx_mlp_destroy(p)
+
+
+def test_fused_forward_follows_training(asx):
+    """After Adam steps the fused kernel uses the updated weights (its weight image is
+    rebuilt), matching the layered pass."""
+    import os
+    from paper_2406_14933_gb300 import asx as A
+    rng = np.random.default_rng(3)
+    x = rng.uniform(-1, 1, (512, 36)).astype(np.float32)
+    t = rng.uniform(0, 1, (512, 128)).astype(np.float32)
+    p = A.asx_mlp_create(max_batch=512)
+    A.asx_mlp_set_params(p, ref.init_params(rng).astype(np.float32))
+    y0 = np.empty((512, 128), np.float32)
+    A.asx_mlp_forward(p, 512, x, y0)
+    for _ in range(5):
+        A.asx_mlp_train_step(p, 512, x, t, 1e-3)
+    y1 = np.empty((512, 128), np.float32)
+    A.asx_mlp_forward(p, 512, x, y1)
+    os.environ["ASX_MLP_FUSED"] = "0"
+    try:
+        yl = np.empty((512, 128), np.float32)
+        A.asx_mlp_forward(p, 512, x, yl)
+    finally:
+        del os.environ["ASX_MLP_FUSED"]
+    assert not np.array_equal(y0, y1)
+    assert np.abs(y1 - yl).max() <= 1e-5 * float(np.abs(yl).max())
+    A.asx_mlp_destroy(p)

@@ -339,42 +339,42 @@ struct Tile {
     }
 
     // Edge terms between row j (C, global row r) and row j+1 (N), and the east edges of
-    // row r.  own: row r is updated by this tile; nown: row r+1 is.  ODD: parity of r.
+    // row r; ODD: parity of r.  Both rows always accumulate: a row this tile does not
+    // update (a halo row, or a row above an overlapping last row block) is never
+    // finished, so its sums are simply dropped.
     template <int ODD>
-    __device__ __forceinline__ void edges(int j, Row &C, Row &N, bool own, bool nown)
+    __device__ __forceinline__ void edges(int j, Row &C, Row &N)
     {
         // neighbour cells held by the lanes to the west / east, or the halo at tile ends
         const Cell Wc = pick(lane == 0, shfl_cell_up(C.X[3]), halo(j, kXO - 1));
         const Cell Ec = pick(lane == 31, shfl_cell_down(C.X[0]), halo(j, kXO + kSW));
-        if (own) {
-            // ---- east edges of row r (the west edge of c_0 is the west lane's, again)
-            edge<0>(a, Wc, C.X[0], kl2, C.A[0], false, C.A[0], true);
+        // ---- east edges of row r (the west edge of c_0 is the west lane's, again)
+        edge<0>(a, Wc, C.X[0], kl2, C.A[0], false, C.A[0], true);
 #pragma unroll
-            for (int e = 0; e < 3; e++) edge<0>(a, C.X[e], C.X[e + 1], kl2, C.A[e], true, C.A[e + 1], true);
-            edge<0>(a, C.X[3], Ec, kl2, C.A[3], true, C.A[3], false);
-        }
+        for (int e = 0; e < 3; e++) edge<0>(a, C.X[e], C.X[e + 1], kl2, C.A[e], true, C.A[e + 1], true);
+        edge<0>(a, C.X[3], Ec, kl2, C.A[3], true, C.A[3], false);
         if (ODD) {
             // odd r: NE(c) = (r+1, c+1), NW(c) = (r+1, c)
             const Cell On = pick(lane == 31, shfl_cell_down(N.X[0]), halo(j + 1, kXO + kSW));   // (r+1, c_3 + 1)
 #pragma unroll
             for (int e = 0; e < 4; e++) {
-                edge<2>(a, C.X[e], N.X[e], kl2, C.A[e], own, N.A[e], nown);        // NW
-                if (e < 3) edge<1>(a, C.X[e], N.X[e + 1], kl2, C.A[e], own, N.A[e + 1], nown);
-                else edge<1>(a, C.X[3], On, kl2, C.A[3], own, C.A[3], false);
+                edge<2>(a, C.X[e], N.X[e], kl2, C.A[e], true, N.A[e], true);        // NW
+                if (e < 3) edge<1>(a, C.X[e], N.X[e + 1], kl2, C.A[e], true, N.A[e + 1], true);
+                else edge<1>(a, C.X[3], On, kl2, C.A[3], true, C.A[3], false);
             }
             // SW edge of (r+1, c_0): the NE edge of (r, c_0 - 1)
-            edge<1>(a, Wc, N.X[0], kl2, N.A[0], false, N.A[0], nown);
+            edge<1>(a, Wc, N.X[0], kl2, N.A[0], false, N.A[0], true);
         } else {
             // even r: NE(c) = (r+1, c), NW(c) = (r+1, c-1)
             const Cell On = pick(lane == 0, shfl_cell_up(N.X[3]), halo(j + 1, kXO - 1));      // (r+1, c_0 - 1)
 #pragma unroll
             for (int e = 0; e < 4; e++) {
-                edge<1>(a, C.X[e], N.X[e], kl2, C.A[e], own, N.A[e], nown);        // NE
-                if (e >= 1) edge<2>(a, C.X[e], N.X[e - 1], kl2, C.A[e], own, N.A[e - 1], nown);
-                else edge<2>(a, C.X[0], On, kl2, C.A[0], own, C.A[0], false);
+                edge<1>(a, C.X[e], N.X[e], kl2, C.A[e], true, N.A[e], true);        // NE
+                if (e >= 1) edge<2>(a, C.X[e], N.X[e - 1], kl2, C.A[e], true, N.A[e - 1], true);
+                else edge<2>(a, C.X[0], On, kl2, C.A[0], true, C.A[0], false);
             }
             // SE edge of (r+1, c_3): the NW edge of (r, c_3 + 1)
-            edge<2>(a, Ec, N.X[3], kl2, N.A[3], false, N.A[3], nown);
+            edge<2>(a, Ec, N.X[3], kl2, N.A[3], false, N.A[3], true);
         }
     }
 
@@ -421,9 +421,8 @@ struct Tile {
     {
         load(j + 1, N);
         if (j + 1 >= jown) {                // else: rows above the ones this tile writes
-            const bool own = j >= jown, nown = j + 1 <= Hn;
-            edges<ODD>(j, C, N, own, nown);
-            if (own) finish(r0 - 1 + j, C);
+            edges<ODD>(j, C, N);
+            if (j >= jown) finish(r0 - 1 + j, C);
         }
         release(j);
     }
@@ -439,24 +438,13 @@ struct Tile {
         __syncwarp();
         Row R0, R1;
         load(0, R0);
-        // rows alternate parity: local row j is global row r0 - 1 + j
-        int j = 0;
-        if ((r0 & 1) == 0) {
-            for (; j + 1 <= Hn; j += 2) {
-                step_row<1>(j, R0, R1);
-                if (__any_sync(0xffffffffu, timed_out)) return;
-                step_row<0>(j + 1, R1, R0);
-                if (__any_sync(0xffffffffu, timed_out)) return;
-            }
-            if (j == Hn) step_row<1>(j, R0, R1);
-        } else {
-            for (; j + 1 <= Hn; j += 2) {
-                step_row<0>(j, R0, R1);
-                if (__any_sync(0xffffffffu, timed_out)) return;
-                step_row<1>(j + 1, R1, R0);
-                if (__any_sync(0xffffffffu, timed_out)) return;
-            }
-            if (j == Hn) step_row<0>(j, R0, R1);
+        // local row j is global row r0 - 1 + j; every tile starts on an odd row r0, so
+        // even j are even rows and one loop with two row bodies covers every tile
+        for (int j = 0; j <= Hn; j += 2) {
+            step_row<0>(j, R0, R1);
+            if (__any_sync(0xffffffffu, timed_out) || j + 1 > Hn) return;
+            step_row<1>(j + 1, R1, R0);
+            if (__any_sync(0xffffffffu, timed_out)) return;
         }
     }
 };
@@ -504,6 +492,12 @@ __global__ void __launch_bounds__(32, ASX_STRIP_MINB) step_strip_kernel(const St
         const int own_c = strip < a.nstrips ? c0 : a.cx0 + a.nstrips * kSW;
         const int r0 = rblk < a.nrb ? a.ry0 + rblk * a.tile_rows : a.r_last;
         const int own_r = rblk < a.nrb ? r0 : a.ry0 + a.nrb * a.tile_rows;
+        if ((r0 & 1) == 0) {
+            // the layout puts every tile on an odd first row; anything else is refused
+            // before a copy is issued
+            if (threadIdx.x == 0) atomicOr(&a.ctl->err, kErrTimeout);
+            return;
+        }
         Tile<CLS> T(a, S, maps, c0, r0, own_c, own_r);
         T.run();
         if (__any_sync(0xffffffffu, T.timed_out)) {
@@ -535,6 +529,9 @@ size_t strip_smem() { return sizeof(StripSmem<CLS>) + 128; }
 
 void step_strip_layout(StepArgs &a)
 {
+    // tiles hold an even number of rows and start on odd rows (row 1, 1 + H, ...), so
+    // that every tile's first local row has the same parity
+    a.tile_rows += a.tile_rows & 1;
     const int H = a.tile_rows;
     // tiles start at column 4 (TMA boxes start 4 columns to the left, on a 16-byte
     // boundary) and row 1, and their halo must end inside the raster
@@ -555,7 +552,8 @@ void step_strip_layout(StepArgs &a)
             a.cx_last = cl;
             a.cxe = cl + kSW;
         }
-        const int rl = a.rows - 1 - H;
+        int rl = a.rows - 1 - H;
+        rl -= 1 - (rl & 1);                // odd first row (the frame takes a row left over)
         if (rl + H > ry1 && rl >= a.ry0) {
             a.r_last = rl;
             a.rye = rl + H;

@@ -203,10 +203,12 @@ __device__ __forceinline__ Cell load_cell(const StepArgs &a, const float *mhi, c
 //   momentum flux    fa = l (theta h)_(A,B) (v_n)_(A,B) (v_a)_(A,B)
 //   pressure term    p  = -1/2 l g (w_B - w_A) (theta h)^_(A,B) n_a     (Eq. fvm_2D_eq.05)
 // (Eq. fvm_2D_eq_frac.01).  A receives -q, p - fa; B receives +q, p + fa.
+// The terms of edge (A, B) that do not depend on the direction's normal components:
+// q and fa as above and dh = (w_B - w_A)/g (theta h)^_(A,B), so that p = c dh with
+// c = -1/2 l g n_a (c1, c2 per direction).
 template <int D>
-__device__ __forceinline__ void edge_terms(const Cell &A, const Cell &B, float kl2, float l4,
-                                           float c1, float c2, float &q, float &fa1, float &fa2,
-                                           float &p1, float &p2)
+__device__ __forceinline__ void edge_core(const Cell &A, const Cell &B, float kl2, float l4, float &q, float &fa1,
+                                          float &fa2, float &dh)
 {
     const float s1 = __fadd_rn(A.v1, B.v1);          // 2 (v_1)_(A,B)
     const float s2 = __fadd_rn(A.v2, B.v2);
@@ -222,7 +224,16 @@ __device__ __forceinline__ void edge_terms(const Cell &A, const Cell &B, float k
     fa2 = __fmul_rn(gl, s2);
     const float dw = __fadd_rn(__fsub_rn(B.z, A.z), __fsub_rn(B.h, A.h));   // (w_B - w_A) / g
     const float hat = vn2 != 0.0f ? mu : (dw < 0.0f ? A.m : B.m);
-    const float dh = __fmul_rn(dw, hat);
+    dh = __fmul_rn(dw, hat);
+}
+
+template <int D>
+__device__ __forceinline__ void edge_terms(const Cell &A, const Cell &B, float kl2, float l4,
+                                           float c1, float c2, float &q, float &fa1, float &fa2,
+                                           float &p1, float &p2)
+{
+    float dh;
+    edge_core<D>(A, B, kl2, l4, q, fa1, fa2, dh);
     p1 = __fmul_rn(c1, dh);
     p2 = __fmul_rn(c2, dh);
 }

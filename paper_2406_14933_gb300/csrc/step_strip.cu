@@ -8,13 +8,14 @@
 //   * rows r0-1 .. r0+H of every field (one halo row above and below, halo columns left
 //     and right) stream into a shared-memory ring of 2-row chunks through TMA tensor
 //     loads (cp.async.bulk.tensor.2d) that complete on mbarriers; lane 0 refills a chunk
-//     once every row of it is finished, so the halo cells at the tile ends are read from
-//     the ring when needed instead of being held in registers;
+//     once every row of it is finished;
 //   * the warp walks the tile row by row; the edges between row r and r+1 and the east
 //     edges of row r are evaluated by the lane that owns their lower cell; a lane also
 //     evaluates the one horizontal and one diagonal edge it shares with each neighbouring
 //     lane (the same canonical edge, so the same bits), which replaces every exchange of
-//     edge terms; neighbour cells come from warp shuffles, halo cells from the ring;
+//     edge terms; every lane reads the cells beside its four (in its own row and the
+//     next, including the halo columns at the tile ends) from the ring: the same values,
+//     hence the same bits, as the neighbouring lane's own cells;
 //   * contributions to row r+1 stay in registers until that row is finished; no block
 //     barrier is needed;
 //   * tiles are laid out so that each tile with its halo lies inside the raster, which
@@ -131,23 +132,26 @@ struct Acc {
     float hi, lo, m1, m2;    // compensated mass, momentum sums J + S
 };
 
-__device__ __forceinline__ void acc_in(Acc &A, float q, float u1, float u2)
-{
-    acc_add(A.hi, A.lo, q);
-    A.m1 += u1;
-    A.m2 += u2;
-}
-
 // Edge (X lower, Y upper) in direction D; adds its terms to ax if ux and to ay if uy
 // (a side not used belongs to another lane or is not updated by this tile).
+// The pressure term p = c dh enters each momentum sum through one fused multiply-add.
 template <int D>
 __device__ __forceinline__ void edge(const StepArgs &a, const Cell &X, const Cell &Y, float kl2,
                                      Acc &ax, bool ux, Acc &ay, bool uy)
 {
-    float q, f1, f2, p1, p2;
-    edge_terms<D>(X, Y, kl2, 0.25f * a.l, a.cpe[D][0], a.cpe[D][1], q, f1, f2, p1, p2);
-    if (ux) acc_in(ax, -q, p1 - f1, p2 - f2);
-    if (uy) acc_in(ay, q, p1 + f1, p2 + f2);
+    float q, f1, f2, dh;
+    edge_core<D>(X, Y, kl2, 0.25f * a.l, q, f1, f2, dh);
+    const float c1 = a.cpe[D][0], c2 = a.cpe[D][1];
+    if (ux) {
+        acc_add(ax.hi, ax.lo, -q);
+        ax.m1 = __fsub_rn(__fmaf_rn(c1, dh, ax.m1), f1);
+        ax.m2 = __fsub_rn(__fmaf_rn(c2, dh, ax.m2), f2);
+    }
+    if (uy) {
+        acc_add(ay.hi, ay.lo, q);
+        ay.m1 = __fadd_rn(__fmaf_rn(c1, dh, ay.m1), f1);
+        ay.m2 = __fadd_rn(__fmaf_rn(c2, dh, ay.m2), f2);
+    }
 }
 
 // Free-discharge contribution of a boundary edge of cell X in direction d (walls: none).
@@ -155,39 +159,6 @@ __device__ __forceinline__ void bnd(const StepArgs &a, const Cell &X, int d, int
                                     float kl2, Acc &A, FF &outd)
 {
     if (side_is_free(a, side, pos)) free_edge(X, d, kl2, 0.5f * a.l, A.hi, A.lo, A.m1, A.m2, outd);
-}
-
-__device__ __forceinline__ Cell shfl_cell_up(const Cell &c)
-{
-    Cell o;
-    o.m = __shfl_up_sync(0xffffffffu, c.m, 1);
-    o.v1 = __shfl_up_sync(0xffffffffu, c.v1, 1);
-    o.v2 = __shfl_up_sync(0xffffffffu, c.v2, 1);
-    o.z = __shfl_up_sync(0xffffffffu, c.z, 1);
-    o.h = __shfl_up_sync(0xffffffffu, c.h, 1);
-    return o;
-}
-
-__device__ __forceinline__ Cell shfl_cell_down(const Cell &c)
-{
-    Cell o;
-    o.m = __shfl_down_sync(0xffffffffu, c.m, 1);
-    o.v1 = __shfl_down_sync(0xffffffffu, c.v1, 1);
-    o.v2 = __shfl_down_sync(0xffffffffu, c.v2, 1);
-    o.z = __shfl_down_sync(0xffffffffu, c.z, 1);
-    o.h = __shfl_down_sync(0xffffffffu, c.h, 1);
-    return o;
-}
-
-__device__ __forceinline__ Cell pick(bool take_b, const Cell &a, const Cell &b)
-{
-    Cell o;
-    o.m = take_b ? b.m : a.m;
-    o.v1 = take_b ? b.v1 : a.v1;
-    o.v2 = take_b ? b.v2 : a.v2;
-    o.z = take_b ? b.z : a.z;
-    o.h = take_b ? b.h : a.h;
-    return o;
 }
 
 // Per-lane state of one row: four cells, their porosity (theta, or in class mode the
@@ -276,8 +247,8 @@ struct Tile {
         return c;
     }
 
-    // Halo cell of local row jr at ring x index x (the row's chunk is still resident).
-    __device__ __forceinline__ Cell halo(int jr, int x) const
+    // The cell of local row jr at ring x index x (the row's chunk is still resident).
+    __device__ __forceinline__ Cell ring_at(int jr, int x) const
     {
         return ring_cell(S.ring[(jr / kRB) % kNC], jr % kRB, x);
     }
@@ -345,9 +316,11 @@ struct Tile {
     template <int ODD>
     __device__ __forceinline__ void edges(int j, Row &C, Row &N)
     {
-        // neighbour cells held by the lanes to the west / east, or the halo at tile ends
-        const Cell Wc = pick(lane == 0, shfl_cell_up(C.X[3]), halo(j, kXO - 1));
-        const Cell Ec = pick(lane == 31, shfl_cell_down(C.X[0]), halo(j, kXO + kSW));
+        // the cells west and east of this lane's four, read from the ring (the same
+        // values, hence the same h, as the neighbouring lane's own cells)
+        const int xw = kXO + 4 * lane - 1, xe = kXO + 4 * lane + 4;
+        const Cell Wc = ring_at(j, xw);
+        const Cell Ec = ring_at(j, xe);
         // ---- east edges of row r (the west edge of c_0 is the west lane's, again)
         edge<0>(a, Wc, C.X[0], kl2, C.A[0], false, C.A[0], true);
 #pragma unroll
@@ -355,7 +328,7 @@ struct Tile {
         edge<0>(a, C.X[3], Ec, kl2, C.A[3], true, C.A[3], false);
         if (ODD) {
             // odd r: NE(c) = (r+1, c+1), NW(c) = (r+1, c)
-            const Cell On = pick(lane == 31, shfl_cell_down(N.X[0]), halo(j + 1, kXO + kSW));   // (r+1, c_3 + 1)
+            const Cell On = ring_at(j + 1, xe);                                   // (r+1, c_3 + 1)
 #pragma unroll
             for (int e = 0; e < 4; e++) {
                 edge<2>(a, C.X[e], N.X[e], kl2, C.A[e], true, N.A[e], true);        // NW
@@ -366,7 +339,7 @@ struct Tile {
             edge<1>(a, Wc, N.X[0], kl2, N.A[0], false, N.A[0], true);
         } else {
             // even r: NE(c) = (r+1, c), NW(c) = (r+1, c-1)
-            const Cell On = pick(lane == 0, shfl_cell_up(N.X[3]), halo(j + 1, kXO - 1));      // (r+1, c_0 - 1)
+            const Cell On = ring_at(j + 1, xw);                                   // (r+1, c_0 - 1)
 #pragma unroll
             for (int e = 0; e < 4; e++) {
                 edge<1>(a, C.X[e], N.X[e], kl2, C.A[e], true, N.A[e], true);        // NE

@@ -274,8 +274,10 @@ __device__ __forceinline__ CellNew cell_update(float shi, float slo, float M1, f
         w1 = __fmul_rn(g1, inv2);
         w2 = __fmul_rn(g2, inv2);
     } else if (den > 0.0f) {
-        w1 = __fdiv_rn(2.0f * g1, den);
-        w2 = __fdiv_rn(2.0f * g2, den);
+        // tiny or subnormal denominator: scale it (and the numerators) by 2^64 first
+        const float inv2 = __fmul_rn(2.0f, fast_rcp(__fmul_rn(den, 0x1p64f)));
+        w1 = __fmul_rn(__fmul_rn(g1, 0x1p64f), inv2);
+        w2 = __fmul_rn(__fmul_rn(g2, 0x1p64f), inv2);
     }
     o.hi = hi;
     o.lo = lo;

@@ -499,7 +499,7 @@ __device__ __forceinline__ void layer_mma(unsigned tmem, const unsigned char *a,
 
 // Hidden-layer epilogue of accumulator row r (this thread's TMEM lane): + bias, ReLU,
 // BF16 (round to nearest even), into the activation image.
-__device__ __forceinline__ void epi_hidden(unsigned trow, const float *__restrict__ bias, unsigned char *act, int r)
+__device__ __forceinline__ void epi_hidden(unsigned trow, const float *bias, unsigned char *act, int r)
 {
     for (int nc = 0; nc < kHid; nc += 16) {
         float v[16];
@@ -507,8 +507,8 @@ __device__ __forceinline__ void epi_hidden(unsigned trow, const float *__restric
         unsigned w[8];
 #pragma unroll
         for (int j = 0; j < 8; j++) {
-            const float a = fmaxf(v[2 * j] + __ldg(bias + nc + 2 * j), 0.0f);
-            const float b = fmaxf(v[2 * j + 1] + __ldg(bias + nc + 2 * j + 1), 0.0f);
+            const float a = fmaxf(v[2 * j] + bias[nc + 2 * j], 0.0f);
+            const float b = fmaxf(v[2 * j + 1] + bias[nc + 2 * j + 1], 0.0f);
             const __nv_bfloat162 h = __floats2bfloat162_rn(a, b);
             w[j] = *reinterpret_cast<const unsigned *>(&h);
         }
@@ -524,7 +524,14 @@ __global__ void __launch_bounds__(kFusedThreads, 1) mlp_fused_fwd_kernel(const F
     unsigned char *sX = base, *sAct = base + kSmX, *sW = base + kSmX + kSmAct;
     __shared__ __align__(8) unsigned long long bar_a, bar_w, bar_m;   // W1 image, weight buffer, MMAs
     __shared__ unsigned tmem_base;
+    __shared__ float s_bias[3 * kHid + kOut];                          // b1 | b2 | b3 | b4
     const int tid = threadIdx.x, warp = tid >> 5;
+    for (int i = tid; i < kHid; i += kFusedThreads) {
+        s_bias[i] = f.b1[i];
+        s_bias[kHid + i] = f.b2[i];
+        s_bias[2 * kHid + i] = f.b3[i];
+        if (i < kOut) s_bias[3 * kHid + i] = f.b4[i];
+    }
     const int ntiles = (f.batch + kTM - 1) / kTM;
     if (warp == 0) {
         asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(su32(&tmem_base)),
@@ -553,7 +560,8 @@ __global__ void __launch_bounds__(kFusedThreads, 1) mlp_fused_fwd_kernel(const F
     if ((int)blockIdx.x < ntiles) a_out = w_out = 1;
     const unsigned char *wnext[3] = {f.wt + kWtOff3, f.wt + kWtOff4, nullptr};
     const unsigned wbytes[3] = {kWtBytesH, kWtBytes4, 0};
-    const float *bias[3] = {f.b1, f.b2, f.b3};
+    const float *bias[3] = {s_bias, s_bias + kHid, s_bias + 2 * kHid};
+    const float *b4 = s_bias + 3 * kHid;
     for (int t = blockIdx.x; t < ntiles && ok; t += gridDim.x) {
         const int m0 = t * kTM;
         // ---- input tile: thread r converts query row m0 + r to BF16, K padded to 64
@@ -648,9 +656,8 @@ __global__ void __launch_bounds__(kFusedThreads, 1) mlp_fused_fwd_kernel(const F
                         float4 *yr = reinterpret_cast<float4 *>(f.y + (size_t)m * kOut + nc);
 #pragma unroll
                         for (int q = 0; q < 4; q++)
-                            yr[q] = make_float4(v[4 * q] + __ldg(f.b4 + nc + 4 * q), v[4 * q + 1] + __ldg(f.b4 + nc + 4 * q + 1),
-                                                v[4 * q + 2] + __ldg(f.b4 + nc + 4 * q + 2),
-                                                v[4 * q + 3] + __ldg(f.b4 + nc + 4 * q + 3));
+                            yr[q] = make_float4(v[4 * q] + b4[nc + 4 * q], v[4 * q + 1] + b4[nc + 4 * q + 1],
+                                                v[4 * q + 2] + b4[nc + 4 * q + 2], v[4 * q + 3] + b4[nc + 4 * q + 3]);
                     }
                 }
             }

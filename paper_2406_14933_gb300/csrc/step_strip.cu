@@ -176,6 +176,7 @@ template <bool CLS>
 struct Tile {
     const StepArgs &a;
     StripSmem<CLS> &S;
+    const float (*cls)[kMaxClasses];   // shared copies of the class tables 1/theta, a, b
     const StripMaps &maps;
     int par, np, lane, c0, r0, Hn, nchunks;
     float kappa, kl2, qr, dtf;
@@ -187,9 +188,9 @@ struct Tile {
     int jown;          // first local row this tile writes
     bool lane_own;     // this lane's four columns are written by this tile
 
-    __device__ __forceinline__ Tile(const StepArgs &a_, StripSmem<CLS> &S_, const StripMaps &m_, int c0_,
-                                    int r0_, int own_c, int own_r)
-        : a(a_), S(S_), maps(m_)
+    __device__ __forceinline__ Tile(const StepArgs &a_, StripSmem<CLS> &S_, const float (*cls_)[kMaxClasses],
+                                    const StripMaps &m_, int c0_, int r0_, int own_c, int own_r)
+        : a(a_), S(S_), cls(cls_), maps(m_)
     {
         const DevCtl *ctl = a.ctl;
         par = ctl->parity;
@@ -241,7 +242,7 @@ struct Tile {
         c.v2 = ch.v2.v[rr][x];
         c.z = ch.z.v[rr][x];
         float rt;
-        if constexpr (CLS) rt = a.cls_rth[ch.th.v[rr][x - kXO + kXOC]];
+        if constexpr (CLS) rt = cls[0][ch.th.v[rr][x - kXO + kXOC]];
         else rt = fast_rcp(ch.th.v[rr][x]);
         c.h = __fmul_rn(c.m, rt);
         return c;
@@ -288,7 +289,7 @@ struct Tile {
 #pragma unroll
             for (int e = 0; e < 4; e++) {
                 R.th[e] = __int_as_float(cc[e]);
-                R.X[e].h = __fmul_rn(mm[e], a.cls_rth[cc[e]]);
+                R.X[e].h = __fmul_rn(mm[e], cls[0][cc[e]]);
             }
         } else {
             const float4 t4 = *reinterpret_cast<const float4 *>(&ch.th.v[rr][x]);
@@ -361,9 +362,9 @@ struct Tile {
             float rt, ka, kb;
             if constexpr (CLS) {
                 const int k = __float_as_int(C.th[e]);
-                rt = a.cls_rth[k];
-                ka = a.cls_a[k];
-                kb = a.cls_b[k];
+                rt = cls[0][k];
+                ka = cls[1][k];
+                kb = cls[2][k];
             } else {
                 const float t = C.th[e];
                 rt = fast_rcp(t);
@@ -456,6 +457,14 @@ __global__ void __launch_bounds__(32, ASX_STRIP_MINB) step_strip_kernel(const St
     StripSmem<CLS> &S = *reinterpret_cast<StripSmem<CLS> *>(
         smem_raw + ((128u - (smem_u32(smem_raw) & 127u)) & 127u));
     if (!a.ctl->active) return;
+    // class tables, indexed per cell: from the parameter space into shared memory
+    __shared__ float s_cls[3][kMaxClasses];
+    if (CLS && threadIdx.x < kMaxClasses) {
+        s_cls[0][threadIdx.x] = a.cls_rth[threadIdx.x];
+        s_cls[1][threadIdx.x] = a.cls_a[threadIdx.x];
+        s_cls[2][threadIdx.x] = a.cls_b[threadIdx.x];
+    }
+    __syncwarp();
     unsigned cwb = 0u;
     double outq = 0.0, clq = 0.0;
     if ((int)blockIdx.x < a.ntiles) {
@@ -471,7 +480,7 @@ __global__ void __launch_bounds__(32, ASX_STRIP_MINB) step_strip_kernel(const St
             if (threadIdx.x == 0) atomicOr(&a.ctl->err, kErrTimeout);
             return;
         }
-        Tile<CLS> T(a, S, maps, c0, r0, own_c, own_r);
+        Tile<CLS> T(a, S, s_cls, maps, c0, r0, own_c, own_r);
         T.run();
         if (__any_sync(0xffffffffu, T.timed_out)) {
             // a tensor copy did not arrive in time: flag the error, wait (bounded) for

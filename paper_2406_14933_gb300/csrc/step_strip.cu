@@ -154,13 +154,6 @@ __device__ __forceinline__ void edge(const StepArgs &a, const Cell &X, const Cel
     }
 }
 
-// Free-discharge contribution of a boundary edge of cell X in direction d (walls: none).
-__device__ __forceinline__ void bnd(const StepArgs &a, const Cell &X, int d, int side, int pos,
-                                    float kl2, Acc &A, FF &outd)
-{
-    if (side_is_free(a, side, pos)) free_edge(X, d, kl2, 0.5f * a.l, A.hi, A.lo, A.m1, A.m2, outd);
-}
-
 // Per-lane state of one row: four cells, their porosity (theta, or in class mode the
 // class id's bits) and the accumulators of their edge terms.  The halo cells at both ends
 // of the tile row are read from the ring when needed.

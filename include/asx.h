@@ -93,6 +93,11 @@ typedef struct {
  *                            pointers; n_rain <= ASX_MAX_RAIN (0 = no rain)
  *   sample_dt                hydrograph sample interval [s]; steps are cut at the
  *                            sample times (0 = none)
+ *   viscosity                1: add the artificial viscosity l c_(i,j) mu_(i,j) (v_j - v_i)
+ *                            to the momentum flux of every interior edge (Appendix A,
+ *                            Eqs. eq_artif_visc, eq_visc1: c_(i,j) = max(c_i, c_j) with
+ *                            c = |v| + sqrt(g h), mu_(i,j) the harmonic mean of theta h,
+ *                            0 when both cells are dry); raster sides add none.  0: off.
  * ASX_EINVAL on any value out of range. */
 typedef struct {
     double g, cfl, dt_max;
@@ -101,6 +106,7 @@ typedef struct {
     int n_rain;
     const double *rain_t, *rain_r;
     double sample_dt;
+    int viscosity;
 } asx_params;
 
 /* Water budget since the last asx_set_fields, all in m^3 (float64):

@@ -201,8 +201,11 @@ class Problem:
                     samples=samples[:min(ns.value, int(sample_cap))].copy())
 
 
-def from_scenario(sc, viscosity=False):
-    """Oracle problem for an ``inputs.Scenario`` (per-cell coefficient arrays)."""
+def from_scenario(sc, viscosity=None):
+    """Oracle problem for an ``inputs.Scenario`` (per-cell coefficient arrays); viscosity
+    defaults to the scenario's setting."""
+    if viscosity is None:
+        viscosity = bool(getattr(sc, "viscosity", False))
     return Problem(sc.rows, sc.cols, sc.l, sc.z, sc.theta, sc.alpha_s, sc.alpha_p, bc=sc.bc,
                    g=sc.g, cfl=sc.cfl, dt_max=sc.dt_max, rain_t=sc.rain_t, rain_r=sc.rain_r,
                    viscosity=viscosity, free_range=sc.free_range)

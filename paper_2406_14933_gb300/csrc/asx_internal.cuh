@@ -94,6 +94,7 @@ struct StepArgs {
     float cpe[3][2];                   // -1/2 l g n for owned directions E, NE, NW
     // boundaries
     int bc[4], fb[4], fe[4];
+    int visc;                          // 1: artificial viscosity on interior edges
     DevCtl *ctl;
 };
 

@@ -238,6 +238,18 @@ __device__ __forceinline__ void edge_terms(const Cell &A, const Cell &B, float k
     p2 = __fmul_rn(c2, dh);
 }
 
+// Artificial-viscosity coefficient of edge (A, B) (Appendix A, Eqs. eq_artif_visc,
+// eq_visc1): t = l c_(A,B) mu_(A,B), c_(A,B) = max(c_A, c_B) with c = |v| + sqrt(g h),
+// mu_(A,B) = 2 m_A m_B / (m_A + m_B) (0 when both are dry).  Symmetric in A and B bit
+// for bit; cell A's momentum sum gains t (v_B - v_A), cell B's t (v_A - v_B).
+__device__ __forceinline__ float visc_coef(const Cell &A, const Cell &B, float l, float g)
+{
+    const float c = fmaxf(wave_speed(A.v1, A.v2, A.h, g), wave_speed(B.v1, B.v2, B.h, g));
+    const float den = __fadd_rn(A.m, B.m);
+    const float mu = den > 1.0e-30f ? __fmul_rn(__fmul_rn(2.0f, __fmul_rn(A.m, B.m)), fast_rcp(den)) : 0.0f;
+    return __fmul_rn(__fmul_rn(l, c), mu);
+}
+
 // Update of one cell once all its edge terms are in (Appendix A): rain at t^{n+1},
 // clamp of a negative mass, theta h v^* = theta h^n v^n + dt / sigma (J + S), and the
 // closed-form implicit friction v^{n+1} = 2 gamma / (alpha + sqrt(alpha^2 + 4 beta |gamma|))
@@ -391,6 +403,11 @@ __device__ __forceinline__ void gather_cell(const StepArgs &a, const StepScalars
                 acc_add(shi, slo, q);
                 M1 += p1 + f1;
                 M2 += p2 + f2;
+            }
+            if (a.visc) {
+                const float t = visc_coef(I, J, a.l, a.g);
+                M1 += __fmul_rn(t, __fsub_rn(J.v1, I.v1));
+                M2 += __fmul_rn(t, __fsub_rn(J.v2, I.v2));
             }
         } else {
             const int pos = (side == ASX_SIDE_S || side == ASX_SIDE_N) ? c : r;

@@ -134,8 +134,9 @@ struct Acc {
 
 // Edge (X lower, Y upper) in direction D; adds its terms to ax if ux and to ay if uy
 // (a side not used belongs to another lane or is not updated by this tile).
-// The pressure term p = c dh enters each momentum sum through one fused multiply-add.
-template <int D>
+// The pressure term p = c dh enters each momentum sum through one fused multiply-add;
+// VISC adds the artificial viscosity t (v_Y - v_X) to X and t (v_X - v_Y) to Y.
+template <int D, bool VISC>
 __device__ __forceinline__ void edge(const StepArgs &a, const Cell &X, const Cell &Y, float kl2,
                                      Acc &ax, bool ux, Acc &ay, bool uy)
 {
@@ -152,6 +153,18 @@ __device__ __forceinline__ void edge(const StepArgs &a, const Cell &X, const Cel
         ay.m1 = __fadd_rn(__fmaf_rn(c1, dh, ay.m1), f1);
         ay.m2 = __fadd_rn(__fmaf_rn(c2, dh, ay.m2), f2);
     }
+    if constexpr (VISC) {
+        const float t = visc_coef(X, Y, a.l, a.g);
+        const float d1 = __fsub_rn(Y.v1, X.v1), d2 = __fsub_rn(Y.v2, X.v2);
+        if (ux) {
+            ax.m1 = __fmaf_rn(t, d1, ax.m1);
+            ax.m2 = __fmaf_rn(t, d2, ax.m2);
+        }
+        if (uy) {
+            ay.m1 = __fmaf_rn(-t, d1, ay.m1);
+            ay.m2 = __fmaf_rn(-t, d2, ay.m2);
+        }
+    }
 }
 
 // Per-lane state of one row: four cells, their porosity (theta, or in class mode the
@@ -165,7 +178,7 @@ struct Row {
 
 // ----------------------------------------------------------------- the tile
 
-template <bool CLS>
+template <bool CLS, bool VISC>
 struct Tile {
     const StepArgs &a;
     StripSmem<CLS> &S;
@@ -316,32 +329,32 @@ struct Tile {
         const Cell Wc = ring_at(j, xw);
         const Cell Ec = ring_at(j, xe);
         // ---- east edges of row r (the west edge of c_0 is the west lane's, again)
-        edge<0>(a, Wc, C.X[0], kl2, C.A[0], false, C.A[0], true);
+        edge<0, VISC>(a, Wc, C.X[0], kl2, C.A[0], false, C.A[0], true);
 #pragma unroll
-        for (int e = 0; e < 3; e++) edge<0>(a, C.X[e], C.X[e + 1], kl2, C.A[e], true, C.A[e + 1], true);
-        edge<0>(a, C.X[3], Ec, kl2, C.A[3], true, C.A[3], false);
+        for (int e = 0; e < 3; e++) edge<0, VISC>(a, C.X[e], C.X[e + 1], kl2, C.A[e], true, C.A[e + 1], true);
+        edge<0, VISC>(a, C.X[3], Ec, kl2, C.A[3], true, C.A[3], false);
         if (ODD) {
             // odd r: NE(c) = (r+1, c+1), NW(c) = (r+1, c)
             const Cell On = ring_at(j + 1, xe);                                   // (r+1, c_3 + 1)
 #pragma unroll
             for (int e = 0; e < 4; e++) {
-                edge<2>(a, C.X[e], N.X[e], kl2, C.A[e], true, N.A[e], true);        // NW
-                if (e < 3) edge<1>(a, C.X[e], N.X[e + 1], kl2, C.A[e], true, N.A[e + 1], true);
-                else edge<1>(a, C.X[3], On, kl2, C.A[3], true, C.A[3], false);
+                edge<2, VISC>(a, C.X[e], N.X[e], kl2, C.A[e], true, N.A[e], true);        // NW
+                if (e < 3) edge<1, VISC>(a, C.X[e], N.X[e + 1], kl2, C.A[e], true, N.A[e + 1], true);
+                else edge<1, VISC>(a, C.X[3], On, kl2, C.A[3], true, C.A[3], false);
             }
             // SW edge of (r+1, c_0): the NE edge of (r, c_0 - 1)
-            edge<1>(a, Wc, N.X[0], kl2, N.A[0], false, N.A[0], true);
+            edge<1, VISC>(a, Wc, N.X[0], kl2, N.A[0], false, N.A[0], true);
         } else {
             // even r: NE(c) = (r+1, c), NW(c) = (r+1, c-1)
             const Cell On = ring_at(j + 1, xw);                                   // (r+1, c_0 - 1)
 #pragma unroll
             for (int e = 0; e < 4; e++) {
-                edge<1>(a, C.X[e], N.X[e], kl2, C.A[e], true, N.A[e], true);        // NE
-                if (e >= 1) edge<2>(a, C.X[e], N.X[e - 1], kl2, C.A[e], true, N.A[e - 1], true);
-                else edge<2>(a, C.X[0], On, kl2, C.A[0], true, C.A[0], false);
+                edge<1, VISC>(a, C.X[e], N.X[e], kl2, C.A[e], true, N.A[e], true);        // NE
+                if (e >= 1) edge<2, VISC>(a, C.X[e], N.X[e - 1], kl2, C.A[e], true, N.A[e - 1], true);
+                else edge<2, VISC>(a, C.X[0], On, kl2, C.A[0], true, C.A[0], false);
             }
             // SE edge of (r+1, c_3): the NW edge of (r, c_3 + 1)
-            edge<2>(a, Ec, N.X[3], kl2, N.A[3], false, N.A[3], true);
+            edge<2, VISC>(a, Ec, N.X[3], kl2, N.A[3], false, N.A[3], true);
         }
     }
 
@@ -442,7 +455,7 @@ __device__ __forceinline__ void frame_cells(const StepArgs &a, long long f0, uns
 }
 
 // 128 registers and a 2 x 2-row ring (13.6 KB) let 15-16 one-warp CTAs share an SM
-template <bool CLS>
+template <bool CLS, bool VISC>
 __global__ void __launch_bounds__(32, ASX_STRIP_MINB) step_strip_kernel(const StepArgs a, const __grid_constant__ StripMaps maps)
 {
     extern __shared__ __align__(128) unsigned char smem_raw[];
@@ -473,7 +486,7 @@ __global__ void __launch_bounds__(32, ASX_STRIP_MINB) step_strip_kernel(const St
             if (threadIdx.x == 0) atomicOr(&a.ctl->err, kErrTimeout);
             return;
         }
-        Tile<CLS> T(a, S, s_cls, maps, c0, r0, own_c, own_r);
+        Tile<CLS, VISC> T(a, S, s_cls, maps, c0, r0, own_c, own_r);
         T.run();
         if (__any_sync(0xffffffffu, T.timed_out)) {
             // a tensor copy did not arrive in time: flag the error, wait (bounded) for
@@ -545,18 +558,31 @@ void step_strip_layout(StepArgs &a)
 
 cudaError_t step_strip_configure()
 {
-    cudaError_t e = cudaFuncSetAttribute(step_strip_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         (int)strip_smem<false>());
-    if (e != cudaSuccess) return e;
-    return cudaFuncSetAttribute(step_strip_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                (int)strip_smem<true>());
+    cudaError_t e = cudaFuncSetAttribute(step_strip_kernel<false, false>,
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)strip_smem<false>());
+    if (e == cudaSuccess)
+        e = cudaFuncSetAttribute(step_strip_kernel<true, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 (int)strip_smem<true>());
+    if (e == cudaSuccess)
+        e = cudaFuncSetAttribute(step_strip_kernel<false, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 (int)strip_smem<false>());
+    if (e == cudaSuccess)
+        e = cudaFuncSetAttribute(step_strip_kernel<true, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 (int)strip_smem<true>());
+    return e;
 }
 
 cudaError_t launch_step_strip(const StepArgs &a, const StripMaps &maps, cudaStream_t s)
 {
-    // land-cover classes (uint8 ids and per-class tables) or per-cell theta
-    if (a.cls) step_strip_kernel<true><<<a.nblocks, 32, strip_smem<true>(), s>>>(a, maps);
-    else step_strip_kernel<false><<<a.nblocks, 32, strip_smem<false>(), s>>>(a, maps);
+    // land-cover classes (uint8 ids and per-class tables) or per-cell theta; with or
+    // without the artificial viscosity
+    if (a.cls) {
+        if (a.visc) step_strip_kernel<true, true><<<a.nblocks, 32, strip_smem<true>(), s>>>(a, maps);
+        else step_strip_kernel<true, false><<<a.nblocks, 32, strip_smem<true>(), s>>>(a, maps);
+    } else {
+        if (a.visc) step_strip_kernel<false, true><<<a.nblocks, 32, strip_smem<false>(), s>>>(a, maps);
+        else step_strip_kernel<false, false><<<a.nblocks, 32, strip_smem<false>(), s>>>(a, maps);
+    }
     return cudaGetLastError();
 }
 

@@ -62,6 +62,7 @@ class Scenario:
     class_alpha_p: np.ndarray | None = None
     class_alpha_s: np.ndarray | None = None
     meta: dict = field(default_factory=dict)
+    viscosity: bool = False            # artificial viscosity on (Appendix A, Eq. eq_artif_visc)
 
     @property
     def n(self) -> int:

@@ -57,6 +57,7 @@ class Raster:
         p.g = sc.g
         p.cfl = sc.cfl if cfl is None else cfl
         p.dt_max = sc.dt_max if dt_max is None else dt_max
+        p.viscosity = int(bool(getattr(sc, "viscosity", False)))
         if self.desc.n_classes:
             ct = _f32(sc.class_theta, -1)
             cp = _f32(sc.class_alpha_p, -1)

@@ -274,3 +274,53 @@ def test_invalid_arguments(asx):
     with pytest.raises(A.AsxError):
         R.set_params(cfl=1.5)
     R.close()
+
+
+# ----------------------------------------------------------------------------- artificial viscosity
+
+@pytest.mark.parametrize("rows,cols,bc", [(2, 3, (0, 0, 0, 0)), (16, 16, (1, 1, 1, 1)), (77, 130, (1, 0, 1, 0)),
+                                          (133, 389, (0, 1, 0, 1))])
+def test_viscosity_one_step(asx, orc, rows, cols, bc):
+    """Appendix A, Eqs. eq_artif_visc / eq_visc1 on: one step against the oracle (same
+    dt), the same float32 tolerance as without viscosity; the viscous flux changes the
+    result measurably."""
+    sc = inputs.tiny(rows, cols, seed=31 * rows + cols, bc=bc, rain_mm_h=30.0)
+    sc.viscosity = True
+    R = _raster(asx, sc)
+    p = _oracle_problem(orc, sc)
+    m0 = p.mass(sc.h0)
+    t1 = R.step(1)
+    mo, ao, bo = p.step(m0, sc.v1_0, sc.v2_0, t1, t1)
+    _, ao_inv, bo_inv = orc.from_scenario(sc, viscosity=False).step(m0, sc.v1_0, sc.v2_0, t1, t1)
+    mg, vg1, vg2 = R.mass64()
+    mg = mg.ravel()
+    assert np.abs(mg - mo).max() <= 2e-6 * max(np.abs(mo).max(), 1e-30)
+    qo1, qo2, qg1, qg2 = mo * ao, mo * bo, mg * vg1.ravel(), mg * vg2.ravel()
+    scale_q = max(np.abs(qo1).max(), np.abs(qo2).max(), 1e-30)
+    assert np.abs(qg1 - qo1).max() <= 2e-6 * scale_q
+    assert np.abs(qg2 - qo2).max() <= 2e-6 * scale_q
+    dq = max(np.abs(mo * (ao - ao_inv)).max(), np.abs(mo * (bo - bo_inv)).max())
+    assert dq >= 100 * 2e-6 * scale_q
+    assert R.ledger().defect_rel <= 1e-10
+    R.close()
+
+
+@pytest.mark.parametrize("rows,cols,bc", [(33, 70, (1, 0, 1, 0)), (66, 270, (1, 1, 0, 1))])
+def test_viscosity_many_steps(asx, orc, rows, cols, bc):
+    """200 steps with viscosity on a smooth bed, the oracle replaying the GPU's time
+    levels: depth and discharge relative L2 <= 1e-4, budget defect <= 1e-10."""
+    sc = inputs.tiny(rows, cols, seed=7 + rows, bc=bc, rain_mm_h=40.0, smooth=True)
+    sc.viscosity = True
+    R = _raster(asx, sc)
+    ts = [R.step(1) for _ in range(200)]
+    p = _oracle_problem(orc, sc)
+    res = p.run(p.mass(sc.h0), sc.v1_0, sc.v2_0, 0.0, ts[-1], t_replay=np.array(ts))
+    mg, vg1, vg2 = R.mass64()
+    eh = _rel_l2(p.depth(mg.ravel()), p.depth(res["m"]))
+    qo = np.concatenate([res["m"] * res["v1"], res["m"] * res["v2"]])
+    qg = np.concatenate([mg.ravel() * vg1.ravel(), mg.ravel() * vg2.ravel()])
+    eq = _rel_l2(qg, qo)
+    print(f"[viscosity] {rows}x{cols}: depth {eh:.2e} discharge {eq:.2e}")
+    assert eh <= 1e-4 and eq <= 1e-4
+    assert R.ledger().defect_rel <= 1e-10
+    R.close()

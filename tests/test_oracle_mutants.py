@@ -13,6 +13,15 @@ SRC = os.path.join(ROOT, "oracle", "asx_oracle.c")
 
 # name: (passage, original text, mutated text)
 MUTANTS = {
+    "visc_sign": ("Eq. eq_visc1 (v_j - v_i)", "J2 += l * cij * mu * (v2[j] - v2[i]);",
+                  "J2 += l * cij * mu * (v2[i] - v2[j]);"),
+    "visc_min_speed": ("Eq. eq_visc1 (c_(i,j) = max)", "const double cij = ci > cj ? ci : cj;",
+                       "const double cij = ci < cj ? ci : cj;"),
+    "visc_arithmetic_mean": ("Eq. eq_visc1 (harmonic mean mu)",
+                             "const double mu = den > 0.0 ? 2.0 * m[i] * m[j] / den : 0.0;",
+                             "const double mu = 0.5 * den;"),
+    "visc_without_edge_length": ("Eq. eq_artif_visc (l_(i,j))", "J2 += l * cij * mu * (v2[j] - v2[i]);",
+                                 "J2 += cij * mu * (v2[j] - v2[i]);"),
     "pressure_sign": ("Eq. fvm_2D_eq_frac.01 (S)", "S1 -= 0.5 * l * dw * hat * n1;", "S1 += 0.5 * l * dw * hat * n1;"),
     "pressure_half": ("Eq. fvm_2D_eq_frac.01 (S, factor 1/2)",
                       "S1 -= 0.5 * l * dw * hat * n1;\n                    S2 -= 0.5 * l * dw * hat * n2;",

@@ -367,3 +367,69 @@ def test_free_outflow_only(orc):
     q = orc.Problem(4, 4, 1.0, 0.0, 1.0, 0.0, 0.0, bc=(1, 0, 0, 0))
     res2 = q.run(m, 0.5, 0.0, 0.0, 1.0e9, max_steps=1)
     assert res2["ledger"].outflow == 0.0
+
+
+# ----------------------------------------------------------------------------- artificial viscosity
+
+def _two_cells(orc, hA, hB, vA, vB, viscosity, l=2.0, dt=0.01):
+    """A 1 x 2 raster (walls all round, flat bed, no friction, no rain): one step."""
+    p = orc.Problem(1, 2, l, np.zeros(2), np.ones(2), np.zeros(2), np.zeros(2), viscosity=viscosity,
+                    dt_max=dt)
+    m = np.array([hA, hB], dtype=np.float64)
+    v1 = np.array([vA[0], vB[0]], dtype=np.float64)
+    v2 = np.array([vA[1], vB[1]], dtype=np.float64)
+    res = p.run(m, v1, v2, 0.0, dt, max_steps=1)
+    return p, res
+
+
+def test_viscosity_two_cells_closed_form(orc):
+    """Appendix A, Eqs. eq_artif_visc and eq_visc1, worked by hand.  Two cells share an
+    east-west edge (normal (1, 0)); both move along the edge (v = (0, v_2)), so v_n = 0: no
+    mass moves, and the pressure term acts along the normal only.  With no friction the
+    tangential velocity after one step is
+      v_2A' = v_2A + dt / sigma * l c mu (v_2B - v_2A) / m_A,
+    c = max(c_A, c_B), c = |v| + sqrt(g h), mu = 2 m_A m_B / (m_A + m_B)."""
+    g, l, dt = 9.81, 2.0, 0.01
+    hA, hB, vA, vB = 0.2, 0.1, (0.0, 0.3), (0.0, -0.1)
+    p, off = _two_cells(orc, hA, hB, vA, vB, False, l, dt)
+    assert off["v2"][0] == pytest.approx(vA[1], abs=1e-15)
+    assert off["v2"][1] == pytest.approx(vB[1], abs=1e-15)
+    p, on = _two_cells(orc, hA, hB, vA, vB, True, l, dt)
+    sigma = 1.5 * math.sqrt(3.0) * l * l
+    c = max(abs(vA[1]) + math.sqrt(g * hA), abs(vB[1]) + math.sqrt(g * hB))
+    mu = 2.0 * hA * hB / (hA + hB)
+    t = l * c * mu
+    assert on["m"] == pytest.approx([hA, hB], abs=1e-15)
+    assert on["v2"][0] == pytest.approx(vA[1] + dt / sigma * t * (vB[1] - vA[1]) / hA, rel=1e-13)
+    assert on["v2"][1] == pytest.approx(vB[1] + dt / sigma * t * (vA[1] - vB[1]) / hB, rel=1e-13)
+    # the normal component is the pressure term alone, as without viscosity (v_1 = 0)
+    assert on["v1"] == pytest.approx(off["v1"], rel=1e-13)
+
+
+def test_viscosity_conserves_momentum_and_dry_pairs(orc):
+    """The viscous flux is antisymmetric: from the same state one step with and one
+    without viscosity (same dt and masses, no friction) differ in total momentum
+    sum(theta h v) only by rounding, although single velocities change; the field gets
+    smoother than without viscosity; between two dry cells (0/0 := 0) nothing moves.
+    (Total momentum itself is not conserved: the pressure term is the non-conservative
+    g h grad w form of Eq. fvm_2D_eq_frac.01.)"""
+    rng = np.random.default_rng(4)
+    R, Cc, l = 12, 14, 1.0
+    m = np.full(R * Cc, 0.8 * 0.05) * rng.uniform(0.5, 1.5, R * Cc)
+    v1 = rng.uniform(-0.2, 0.2, R * Cc)
+    v2 = rng.uniform(-0.2, 0.2, R * Cc)
+    out = {}
+    for visc in (False, True):
+        p = orc.Problem(R, Cc, l, np.zeros(R * Cc), np.full(R * Cc, 0.8), np.zeros(R * Cc), np.zeros(R * Cc),
+                        viscosity=visc, dt_max=0.002)
+        one = p.run(m, v1, v2, 0.0, 1.0, max_steps=1)
+        ten = p.run(m, v1, v2, 0.0, 1.0, max_steps=10)
+        out[visc] = (one, ten)
+    (o0, t0), (o1, t1) = out[False], out[True]
+    assert o0["t"] == o1["t"] and np.array_equal(o0["m"], o1["m"])
+    for k, a0 in (("v1", v1), ("v2", v2)):
+        assert np.max(np.abs(o1[k] - o0[k])) > 1e-6
+        assert abs(np.sum(o1["m"] * o1[k]) - np.sum(o0["m"] * o0[k])) <= 1e-14 * np.sum(m * np.abs(a0))
+        assert np.std(t1[k]) < np.std(t0[k])
+    _, dry = _two_cells(orc, 0.0, 0.0, (0.0, 0.3), (0.0, -0.1), True)
+    assert np.all(np.isfinite(dry["v2"])) and np.all(dry["m"] == 0.0)

@@ -98,6 +98,14 @@ typedef struct {
  *                            Eqs. eq_artif_visc, eq_visc1: c_(i,j) = max(c_i, c_j) with
  *                            c = |v| + sqrt(g h), mu_(i,j) the harmonic mean of theta h,
  *                            0 when both cells are dry); raster sides add none.  0: off.
+ *   tau                      linear soil resistance -tau h v [1/s] (>= 0) of Thacker's
+ *                            problem (Sec. 4, Eq. eq_soil_friction_thacker), taken
+ *                            implicitly with the other resistances:
+ *                            (theta h + dt tau h) v + dt K |v| v = gamma.  0: none.
+ *   h_dry                    depth [m] (>= 0) below which a cell's new velocity is set to
+ *                            zero (a wet/dry threshold the paper does not print; without
+ *                            resistance, films at a moving shoreline otherwise accelerate
+ *                            without bound).  0: none (a cell is dry only when empty).
  * ASX_EINVAL on any value out of range. */
 typedef struct {
     double g, cfl, dt_max;
@@ -107,6 +115,7 @@ typedef struct {
     const double *rain_t, *rain_r;
     double sample_dt;
     int viscosity;
+    double tau, h_dry;
 } asx_params;
 
 /* Water budget since the last asx_set_fields, all in m^3 (float64):

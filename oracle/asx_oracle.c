@@ -21,6 +21,8 @@
  *   - time-step restriction:  Appendix A, Eqs. fvm_2D_eq_frac.12 and .13
  *   - implicit friction:      Appendix A, Eq. miu-formula
  *   - artificial viscosity:   Appendix A, Eqs. eq_artif_visc, eq_visc1 (optional)
+ *   - linear soil resistance: Sec. 4 (Thacker's problem), Eq. eq_soil_friction_thacker
+ *                             (optional, tau = 0 by default)
  *   - rain:                   Appendix C (piecewise-linear hyetograph)
  *   - boundary types:         Sec. 3 "Data In" (free discharge default, wall)
  *
@@ -77,6 +79,10 @@ typedef struct {
     const double *rain_t;   /* [s], increasing */
     const double *rain_r;   /* [m/s] */
     int viscosity;          /* 1 = add the artificial viscosity flux */
+    double tau;             /* linear soil resistance -tau h v [1/s] of Thacker's problem
+                               (Sec. 4, Eq. eq_soil_friction_thacker); 0 = none */
+    double h_dry;           /* depth [m] below which a cell's velocity is set to zero after
+                               the friction step; 0 = none (dry means m = 0 exactly) */
 } orc_problem;
 
 typedef struct {
@@ -290,11 +296,17 @@ int orc_step(const orc_problem *p, const double *m, const double *v1, const doub
                     clamp_total += -m_new * sigma;
                     m_new = 0.0;
                 }
-                /* Eq. fvm_2D_eq_frac.06-2 via Eq. miu-formula */
+                /* Eq. fvm_2D_eq_frac.06-2 via Eq. miu-formula; a linear resistance
+                 * -tau h v, taken implicitly like the rest, adds dt tau h^{n+1} to alpha:
+                 * (theta h + dt tau h) v + beta |v| v = gamma */
                 h_new = m_new / p->theta[i];
                 beta = dt * orc_K(p, i, h_new);
                 m_out[i] = m_new;
-                orc_friction(m_new, beta, g1, g2, &v1_out[i], &v2_out[i]);
+                orc_friction(m_new + dt * p->tau * h_new, beta, g1, g2, &v1_out[i], &v2_out[i]);
+                if (h_new < p->h_dry) {
+                    v1_out[i] = 0.0;
+                    v2_out[i] = 0.0;
+                }
                 if (!isfinite(m_new) || !isfinite(v1_out[i]) || !isfinite(v2_out[i])) bad = 1;
             }
             out_rate_total += out_rate;

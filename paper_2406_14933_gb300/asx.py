@@ -43,7 +43,8 @@ class asx_params(C.Structure):
                 ("class_theta", C.POINTER(C.c_float)), ("class_alpha_p", C.POINTER(C.c_float)),
                 ("class_alpha_s", C.POINTER(C.c_float)), ("n_rain", C.c_int),
                 ("rain_t", C.POINTER(C.c_double)), ("rain_r", C.POINTER(C.c_double)),
-                ("sample_dt", C.c_double), ("viscosity", C.c_int)]
+                ("sample_dt", C.c_double), ("viscosity", C.c_int), ("tau", C.c_double),
+                ("h_dry", C.c_double)]
 
 
 class asx_ledger(C.Structure):

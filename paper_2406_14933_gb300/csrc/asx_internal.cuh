@@ -95,6 +95,8 @@ struct StepArgs {
     // boundaries
     int bc[4], fb[4], fe[4];
     int visc;                          // 1: artificial viscosity on interior edges
+    float tau;                         // linear soil resistance -tau h v [1/s] (0: none)
+    float h_dry;                       // depth below which velocities are zeroed [m] (0: none)
     DevCtl *ctl;
 };
 

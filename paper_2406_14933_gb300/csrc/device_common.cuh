@@ -262,7 +262,8 @@ struct CellNew {
 
 __device__ __forceinline__ CellNew cell_update(float shi, float slo, float M1, float M2, float m_old,
                                                float v1_old, float v2_old, float rth, float ka, float kb,
-                                               float kappa, float qr, float dtf, float g, FF &clq)
+                                               float kappa, float qr, float dtf, float g, float dtau,
+                                               float h_dry, FF &clq)
 {
     CellNew o;
     acc_add(shi, slo, qr);
@@ -279,7 +280,10 @@ __device__ __forceinline__ CellNew cell_update(float shi, float slo, float M1, f
     const float h = __fmul_rn(hi, rth);
     const float beta = __fmul_rn(dtf, __fmaf_rn(ka, h, kb));
     const float ng = norm2(g1, g2);
-    const float den = __fadd_rn(hi, fast_sqrt(__fmaf_rn(hi, hi, __fmul_rn(4.0f * beta, ng))));
+    // a linear resistance -tau h v (Thacker's problem), implicit like the rest, adds
+    // dt tau h^{n+1} to alpha (dtau = dt tau; 0 leaves alpha = theta h bit for bit)
+    const float ap = __fmaf_rn(dtau, h, hi);
+    const float den = __fadd_rn(ap, fast_sqrt(__fmaf_rn(ap, ap, __fmul_rn(4.0f * beta, ng))));
     float w1 = 0.0f, w2 = 0.0f;
     if (den > 1.0e-30f) {
         const float inv2 = __fmul_rn(2.0f, fast_rcp(den));
@@ -290,6 +294,10 @@ __device__ __forceinline__ CellNew cell_update(float shi, float slo, float M1, f
         const float inv2 = __fmul_rn(2.0f, fast_rcp(__fmul_rn(den, 0x1p64f)));
         w1 = __fmul_rn(__fmul_rn(g1, 0x1p64f), inv2);
         w2 = __fmul_rn(__fmul_rn(g2, 0x1p64f), inv2);
+    }
+    if (h < h_dry) {             // optional dry threshold (0: none)
+        w1 = 0.0f;
+        w2 = 0.0f;
     }
     o.hi = hi;
     o.lo = lo;
@@ -429,7 +437,7 @@ __device__ __forceinline__ void gather_cell(const StepArgs &a, const StepScalars
         kb = th * a.alpha_s;
     }
     const CellNew o = cell_update(shi, slo, M1, M2, I.m, I.v1, I.v2, rth, ka, kb, s.kappa, s.qr, s.dtf,
-                                  a.g, clq);
+                                  a.g, __fmul_rn(s.dtf, a.tau), a.h_dry, clq);
     const int np = s.par ^ 1;
     a.mhi[np][k] = o.hi;
     a.mlo[np][k] = o.lo;

@@ -376,6 +376,8 @@ asx_status asx_set_params(asx_raster *r, const asx_params *p)
     if (!(p->sample_dt >= 0) || !std::isfinite(p->sample_dt)) return fail(r, ASX_EINVAL, "sample_dt must be >= 0");
     if (p->n_rain < 0 || p->n_rain > kMaxRain) return fail(r, ASX_EINVAL, "n_rain out of range");
     if (p->viscosity != 0 && p->viscosity != 1) return fail(r, ASX_EINVAL, "viscosity must be 0 or 1");
+    if (!(p->tau >= 0) || !std::isfinite(p->tau)) return fail(r, ASX_EINVAL, "tau must be >= 0");
+    if (!(p->h_dry >= 0) || !std::isfinite(p->h_dry)) return fail(r, ASX_EINVAL, "h_dry must be >= 0");
     if (p->n_rain > 0 && (!p->rain_t || !p->rain_r)) return fail(r, ASX_EINVAL, "rain table missing");
     for (int k = 0; k < p->n_rain; k++) {
         if (!std::isfinite(p->rain_t[k]) || !std::isfinite(p->rain_r[k]) || p->rain_r[k] < 0)
@@ -406,6 +408,8 @@ asx_status asx_set_params(asx_raster *r, const asx_params *p)
     a.l = (float)l;
     a.g = (float)p->g;
     a.visc = p->viscosity;
+    a.tau = (float)p->tau;
+    a.h_dry = (float)p->h_dry;
     const double s3 = std::sqrt(3.0) / 2.0;
     const double n1[3] = {1.0, 0.5, -0.5}, n2[3] = {0.0, s3, s3};
     for (int d = 0; d < 3; d++) {

@@ -378,7 +378,7 @@ struct Tile {
                 kb = t * a.alpha_s;
             }
             o[e] = cell_update(C.A[e].hi, C.A[e].lo, C.A[e].m1, C.A[e].m2, C.X[e].m, C.X[e].v1, C.X[e].v2,
-                               rt, ka, kb, kappa, qr, dtf, a.g, cl);
+                               rt, ka, kb, kappa, qr, dtf, a.g, __fmul_rn(dtf, a.tau), a.h_dry, cl);
         }
         if (!lane_own) return;       // columns written by the neighbouring tile
         if (cl.hi != 0.0f || cl.lo != 0.0f) {

@@ -63,6 +63,8 @@ class Scenario:
     class_alpha_s: np.ndarray | None = None
     meta: dict = field(default_factory=dict)
     viscosity: bool = False            # artificial viscosity on (Appendix A, Eq. eq_artif_visc)
+    tau: float = 0.0                   # linear soil resistance -tau h v [1/s] (Thacker's problem)
+    h_dry: float = 0.0                 # depth below which velocities are zeroed [m] (0 = none)
 
     @property
     def n(self) -> int:
@@ -353,4 +355,37 @@ def tiny(rows, cols, seed, l=1.0, bc=(WALL, WALL, WALL, WALL), relief=0.2, theta
     sc.h0, sc.v1_0, sc.v2_0 = h, v1, v2
     if rain_mm_h > 0:
         sc.rain_t, sc.rain_r = constant_rain(rain_mm_h, 1.0e6)
+    return sc
+
+
+THACKER = dict(a=1.25e-3, b=5.0e-3, x0=500.0, y0=500.0, tau=0.7, w0=15.0, du0=0.02 * 9.81, dv0=-0.1 * 9.81,
+               g=9.81)
+
+
+def thacker(l=1.0, x_range=(250.0, 750.0), y_range=(350.0, 650.0), t_end=10.0) -> Scenario:
+    """Thacker's problem in its non-oscillating form (Sec. 4, Appendix B): paraboloid bed
+    z = a (x - x0)^2 + b (y - y0)^2 (a = 1.25e-3, b = 5e-3 1/m, x0 = y0 = 500 m), no
+    vegetation (theta = 1) and no rain, linear soil resistance -tau h v (tau = 0.7 1/s)
+    and no other friction; at rest at t = 0 under the planar free surface
+    w = 15 - 0.02 (x - x0) + 0.1 (y - y0) m (u'(0) = 0.02 g, v'(0) = -0.1 g).  The raster
+    covers x_range x y_range (the water stays within about 110 m x 55 m of the centre,
+    where the bed is far below the walls of the window); cells of edge l.  Velocities of
+    cells shallower than 1 mm are set to zero (h_dry): with no resistance but the linear
+    one, films at the moving shoreline otherwise accelerate without bound."""
+    T = THACKER
+    cols = int(round((x_range[1] - x_range[0]) / (math.sqrt(3.0) * l)))
+    rows = int(round((y_range[1] - y_range[0]) / (1.5 * l)))
+    x, y = cell_centres(rows, cols, l)
+    x = x + x_range[0]
+    y = y + y_range[0]
+    z = T["a"] * (x - T["x0"]) ** 2 + T["b"] * (y - T["y0"]) ** 2
+    w = T["w0"] - (x - T["x0"]) * T["du0"] / T["g"] - (y - T["y0"]) * T["dv0"] / T["g"]
+    sh = (rows, cols)
+    z32 = z.astype(np.float32)
+    h0 = np.maximum(w - z32.astype(np.float64), 0.0).astype(np.float32)
+    sc = Scenario(f"thacker_l{l:g}", rows, cols, l, z32, _fill(sh, 1.0), _fill(sh, 0.0), _fill(sh, 0.0), h0,
+                  _fill(sh, 0.0), _fill(sh, 0.0), bc=(WALL, WALL, WALL, WALL), t_end=t_end, g=T["g"],
+                  meta=dict(T, x_origin=x_range[0], y_origin=y_range[0]))
+    sc.tau = T["tau"]
+    sc.h_dry = 1.0e-3
     return sc

@@ -58,6 +58,8 @@ class Raster:
         p.cfl = sc.cfl if cfl is None else cfl
         p.dt_max = sc.dt_max if dt_max is None else dt_max
         p.viscosity = int(bool(getattr(sc, "viscosity", False)))
+        p.tau = float(getattr(sc, "tau", 0.0))
+        p.h_dry = float(getattr(sc, "h_dry", 0.0))
         if self.desc.n_classes:
             ct = _f32(sc.class_theta, -1)
             cp = _f32(sc.class_alpha_p, -1)

@@ -324,3 +324,33 @@ def test_viscosity_many_steps(asx, orc, rows, cols, bc):
     assert eh <= 1e-4 and eq <= 1e-4
     assert R.ledger().defect_rel <= 1e-10
     R.close()
+
+
+# ----------------------------------------------------------------------------- Thacker's problem
+
+def test_thacker_against_oracle_and_analytic(asx, orc):
+    """Thacker's problem (Sec. 4, Appendix B: paraboloid bowl, linear resistance -tau h v,
+    1 mm dry threshold) at l = 2 m (100 x 144 cells: strip tiles and frame), stepped past
+    t = 10 s.  The oracle replays the GPU's time levels: depth and discharge relative L2
+    <= 1e-4.  Against the analytic solution, the same bound as the oracle's own pin:
+    relative L1 depth error <= 1.5 %."""
+    import thacker_exact as TE
+    sc = inputs.thacker(l=2.0)
+    R = _raster(asx, sc)
+    ts = [R.step(1)]
+    while ts[-1] < 10.0:
+        ts.append(R.step(1))
+    p = _oracle_problem(orc, sc)
+    res = p.run(p.mass(sc.h0), sc.v1_0, sc.v2_0, 0.0, ts[-1], t_replay=np.array(ts))
+    mg, vg1, vg2 = R.mass64()
+    R.close()
+    eh = _rel_l2(p.depth(mg.ravel()), p.depth(res["m"]))
+    qo = np.concatenate([res["m"] * res["v1"], res["m"] * res["v2"]])
+    qg = np.concatenate([mg.ravel() * vg1.ravel(), mg.ravel() * vg2.ravel()])
+    eq = _rel_l2(qg, qo)
+    x, y = inputs.cell_centres(sc.rows, sc.cols, sc.l)
+    _, _, _, h = TE.solution(inputs.THACKER, ts[-1], x + sc.meta["x_origin"], y + sc.meta["y_origin"])
+    l1 = float(np.abs(mg - h).sum() / h.sum())
+    print(f"[thacker] {len(ts)} steps: depth {eh:.2e} discharge {eq:.2e} vs oracle; L1 depth {l1:.4f} vs analytic")
+    assert eh <= 1e-4 and eq <= 1e-4
+    assert l1 <= 0.015

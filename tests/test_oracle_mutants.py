@@ -13,6 +13,9 @@ SRC = os.path.join(ROOT, "oracle", "asx_oracle.c")
 
 # name: (passage, original text, mutated text)
 MUTANTS = {
+    "thacker_no_linear_resistance": ("Eq. eq_soil_friction_thacker (tau h v)",
+                                     "orc_friction(m_new + dt * p->tau * h_new, beta",
+                                     "orc_friction(m_new, beta"),
     "visc_sign": ("Eq. eq_visc1 (v_j - v_i)", "J2 += l * cij * mu * (v2[j] - v2[i]);",
                   "J2 += l * cij * mu * (v2[i] - v2[j]);"),
     "visc_min_speed": ("Eq. eq_visc1 (c_(i,j) = max)", "const double cij = ci > cj ? ci : cj;",

@@ -433,3 +433,52 @@ def test_viscosity_conserves_momentum_and_dry_pairs(orc):
         assert np.std(t1[k]) < np.std(t0[k])
     _, dry = _two_cells(orc, 0.0, 0.0, (0.0, 0.3), (0.0, -0.1), True)
     assert np.all(np.isfinite(dry["v2"])) and np.all(dry["m"] == 0.0)
+
+
+# ----------------------------------------------------------------------------- Thacker's problem
+
+def test_thacker_exact_solution_transcription():
+    """The analytic solution of Appendix B, as written in tests/thacker_exact.py, satisfies
+    the continuity equation h_t + u h_x + v h_y = 0 (uniform velocity) in the wet region,
+    and starts at rest under the stated plane (checked by central differences)."""
+    import thacker_exact as TE
+    T = inputs.THACKER
+    x, y = np.array([480.0, 520.0, 500.0]), np.array([495.0, 505.0, 500.0])
+    e = 1e-4
+    for t in (1.0, 10.0, 30.0):
+        u, v, _, h = TE.solution(T, t, x, y)
+        assert np.all(h > 1.0)
+        ht = (TE.solution(T, t + e, x, y)[3] - TE.solution(T, t - e, x, y)[3]) / (2 * e)
+        hx = (TE.solution(T, t, x + e, y)[3] - TE.solution(T, t, x - e, y)[3]) / (2 * e)
+        hy = (TE.solution(T, t, x, y + e)[3] - TE.solution(T, t, x, y - e)[3]) / (2 * e)
+        assert np.max(np.abs(ht + u * hx + v * hy)) <= 1e-8
+    u0, v0, w0, _ = TE.solution(T, 0.0, x, y)
+    assert u0 == 0.0 and v0 == 0.0
+    assert np.allclose(w0, 15.0 - 0.02 * (x - 500.0) + 0.1 * (y - 500.0), atol=1e-12)
+
+
+def _thacker_run(orc, l):
+    import thacker_exact as TE
+    sc = inputs.thacker(l=l)
+    p = orc.from_scenario(sc)
+    res = p.run(p.mass(sc.h0), sc.v1_0, sc.v2_0, 0.0, 10.0)
+    x, y = inputs.cell_centres(sc.rows, sc.cols, l)
+    x, y = x + sc.meta["x_origin"], y + sc.meta["y_origin"]
+    u, v, w, h = TE.solution(inputs.THACKER, 10.0, x, y)
+    m = res["m"].reshape(sc.rows, sc.cols)
+    wet = h > 0.1
+    return dict(l1=float(np.abs(m - h).sum() / h.sum()),
+                u=float(res["v1"].reshape(h.shape)[wet].mean()), v=float(res["v2"].reshape(h.shape)[wet].mean()),
+                u_ex=float(u), v_ex=float(v))
+
+
+def test_thacker_oracle_converges_to_analytic(orc):
+    """Thacker's problem (Sec. 4, Appendix B): with the linear resistance -tau h v the
+    oracle approaches the analytic solution at first order.  At t = 10 s the relative L1
+    depth error roughly halves from l = 4 m to l = 2 m, and the mean velocity of the wet
+    region matches the analytic uniform velocity."""
+    c, f = _thacker_run(orc, 4.0), _thacker_run(orc, 2.0)
+    assert c["l1"] <= 0.03 and f["l1"] <= 0.015
+    assert f["l1"] <= 0.6 * c["l1"]
+    assert f["u"] == pytest.approx(f["u_ex"], rel=0.03)
+    assert f["v"] == pytest.approx(f["v_ex"], rel=0.06)

@@ -242,8 +242,10 @@ asx_status asx_destroy_ensemble(asx_ensemble *e);
 asx_status asx_ensemble_set_fields(asx_ensemble *e, int s, const float *z, const float *theta,
                                    const float *h0, const float *v1, const float *v2, int ptr_kind);
 
-/* Times every launch shape on the ensemble with each scenario cut to max_steps steps and
- * keeps the fastest for asx_ensemble_run; *best_out (may be NULL) receives it. */
+/* Times every launch shape on the ensemble with each scenario cut to max_steps steps (after
+ * one untimed launch; each shape twice, the faster counts) and keeps the fastest for
+ * asx_ensemble_run; *best_out (may be NULL) receives it.  The scenarios' states are reset
+ * to their initial state afterwards by the next asx_ensemble_run. */
 asx_status asx_ensemble_autotune(asx_ensemble *e, int max_steps, asx_ensemble_tuning *best_out);
 
 /* Runs every scenario from its initial state to its t_end in one persistent launch

@@ -254,12 +254,15 @@ __device__ __forceinline__ float visc_coef(const Cell &A, const Cell &B, float l
 // clamp of a negative mass, theta h v^* = theta h^n v^n + dt / sigma (J + S), and the
 // closed-form implicit friction v^{n+1} = 2 gamma / (alpha + sqrt(alpha^2 + 4 beta |gamma|))
 // with alpha = theta h^{n+1}, beta = dt K(h^{n+1}, theta) (Eq. miu-formula).  Returns the
-// new state, the bits of the new wave speed, and adds clamped mass to clq.
+// new state, the bits of the new wave speed, and adds clamped mass to clq.  EXT: the
+// optional linear resistance (dtau = dt tau) and dry threshold are compiled in; without
+// them (callers that never set them) the code is the plain update.
 struct CellNew {
     float hi, lo, v1, v2;
     unsigned cbits;
 };
 
+template <bool EXT = true>
 __device__ __forceinline__ CellNew cell_update(float shi, float slo, float M1, float M2, float m_old,
                                                float v1_old, float v2_old, float rth, float ka, float kb,
                                                float kappa, float qr, float dtf, float g, float dtau,
@@ -282,7 +285,8 @@ __device__ __forceinline__ CellNew cell_update(float shi, float slo, float M1, f
     const float ng = norm2(g1, g2);
     // a linear resistance -tau h v (Thacker's problem), implicit like the rest, adds
     // dt tau h^{n+1} to alpha (dtau = dt tau; 0 leaves alpha = theta h bit for bit)
-    const float ap = __fmaf_rn(dtau, h, hi);
+    float ap = hi;
+    if constexpr (EXT) ap = __fmaf_rn(dtau, h, hi);
     const float den = __fadd_rn(ap, fast_sqrt(__fmaf_rn(ap, ap, __fmul_rn(4.0f * beta, ng))));
     float w1 = 0.0f, w2 = 0.0f;
     if (den > 1.0e-30f) {
@@ -295,9 +299,11 @@ __device__ __forceinline__ CellNew cell_update(float shi, float slo, float M1, f
         w1 = __fmul_rn(__fmul_rn(g1, 0x1p64f), inv2);
         w2 = __fmul_rn(__fmul_rn(g2, 0x1p64f), inv2);
     }
-    if (h < h_dry) {             // optional dry threshold (0: none)
-        w1 = 0.0f;
-        w2 = 0.0f;
+    if constexpr (EXT) {
+        if (h < h_dry) {         // optional dry threshold (0: none)
+            w1 = 0.0f;
+            w2 = 0.0f;
+        }
     }
     o.hi = hi;
     o.lo = lo;
@@ -381,6 +387,9 @@ __device__ __forceinline__ StepScalars step_scalars(const StepArgs &a)
 // The whole step for one cell (r, c), gathering its six neighbours from global memory:
 // each edge is evaluated in its canonical orientation (the lower cell first), so a
 // shared edge gives both cells the same mass increment wherever it is evaluated.
+// EXT: the optional terms (artificial viscosity, linear resistance, dry threshold) are
+// compiled in; the ensemble, whose scenarios never set them, leaves them out.
+template <bool EXT = true>
 __device__ __forceinline__ void gather_cell(const StepArgs &a, const StepScalars &s, int r, int c,
                                             unsigned &cb, FF &outd, FF &clq)
 {
@@ -412,7 +421,7 @@ __device__ __forceinline__ void gather_cell(const StepArgs &a, const StepScalars
                 M1 += p1 + f1;
                 M2 += p2 + f2;
             }
-            if (a.visc) {
+            if (EXT && a.visc) {
                 const float t = visc_coef(I, J, a.l, a.g);
                 M1 += __fmul_rn(t, __fsub_rn(J.v1, I.v1));
                 M2 += __fmul_rn(t, __fsub_rn(J.v2, I.v2));
@@ -436,7 +445,7 @@ __device__ __forceinline__ void gather_cell(const StepArgs &a, const StepScalars
         ka = a.alpha_p * (1.0f - th);
         kb = th * a.alpha_s;
     }
-    const CellNew o = cell_update(shi, slo, M1, M2, I.m, I.v1, I.v2, rth, ka, kb, s.kappa, s.qr, s.dtf,
+    const CellNew o = cell_update<EXT>(shi, slo, M1, M2, I.m, I.v1, I.v2, rth, ka, kb, s.kappa, s.qr, s.dtf,
                                   a.g, __fmul_rn(s.dtf, a.tau), a.h_dry, clq);
     const int np = s.par ^ 1;
     a.mhi[np][k] = o.hi;

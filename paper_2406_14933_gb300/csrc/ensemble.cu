@@ -227,7 +227,7 @@ __global__ void __launch_bounds__(NT) ensemble_kernel(EnsScenario *scen, const i
 #pragma unroll
                 for (int u = 0; u < K; u++) {
                     const int i = i0 + u * NT;
-                    if (i < band) gather_cell(sa, sc, rb0 + i / cols, i % cols, cb, outd, clq);
+                    if (i < band) gather_cell<false>(sa, sc, rb0 + i / cols, i % cols, cb, outd, clq);
                 }
             }
             double out = outd.value(), cl = clq.value(), sto = 0.0;

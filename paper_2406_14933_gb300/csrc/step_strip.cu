@@ -134,9 +134,10 @@ struct Acc {
 
 // Edge (X lower, Y upper) in direction D; adds its terms to ax if ux and to ay if uy
 // (a side not used belongs to another lane or is not updated by this tile).
-// The pressure term p = c dh enters each momentum sum through one fused multiply-add;
-// VISC adds the artificial viscosity t (v_Y - v_X) to X and t (v_X - v_Y) to Y.
-template <int D, bool VISC>
+// The pressure term p = c dh enters each momentum sum through one fused multiply-add.
+// EXT: the optional terms are compiled in; with a.visc the artificial viscosity adds
+// t (v_Y - v_X) to X and t (v_X - v_Y) to Y.
+template <int D, bool EXT>
 __device__ __forceinline__ void edge(const StepArgs &a, const Cell &X, const Cell &Y, float kl2,
                                      Acc &ax, bool ux, Acc &ay, bool uy)
 {
@@ -153,7 +154,7 @@ __device__ __forceinline__ void edge(const StepArgs &a, const Cell &X, const Cel
         ay.m1 = __fadd_rn(__fmaf_rn(c1, dh, ay.m1), f1);
         ay.m2 = __fadd_rn(__fmaf_rn(c2, dh, ay.m2), f2);
     }
-    if constexpr (VISC) {
+    if (EXT && a.visc) {
         const float t = visc_coef(X, Y, a.l, a.g);
         const float d1 = __fsub_rn(Y.v1, X.v1), d2 = __fsub_rn(Y.v2, X.v2);
         if (ux) {
@@ -178,7 +179,7 @@ struct Row {
 
 // ----------------------------------------------------------------- the tile
 
-template <bool CLS, bool VISC>
+template <bool CLS, bool EXT>
 struct Tile {
     const StepArgs &a;
     StripSmem<CLS> &S;
@@ -329,32 +330,32 @@ struct Tile {
         const Cell Wc = ring_at(j, xw);
         const Cell Ec = ring_at(j, xe);
         // ---- east edges of row r (the west edge of c_0 is the west lane's, again)
-        edge<0, VISC>(a, Wc, C.X[0], kl2, C.A[0], false, C.A[0], true);
+        edge<0, EXT>(a, Wc, C.X[0], kl2, C.A[0], false, C.A[0], true);
 #pragma unroll
-        for (int e = 0; e < 3; e++) edge<0, VISC>(a, C.X[e], C.X[e + 1], kl2, C.A[e], true, C.A[e + 1], true);
-        edge<0, VISC>(a, C.X[3], Ec, kl2, C.A[3], true, C.A[3], false);
+        for (int e = 0; e < 3; e++) edge<0, EXT>(a, C.X[e], C.X[e + 1], kl2, C.A[e], true, C.A[e + 1], true);
+        edge<0, EXT>(a, C.X[3], Ec, kl2, C.A[3], true, C.A[3], false);
         if (ODD) {
             // odd r: NE(c) = (r+1, c+1), NW(c) = (r+1, c)
             const Cell On = ring_at(j + 1, xe);                                   // (r+1, c_3 + 1)
 #pragma unroll
             for (int e = 0; e < 4; e++) {
-                edge<2, VISC>(a, C.X[e], N.X[e], kl2, C.A[e], true, N.A[e], true);        // NW
-                if (e < 3) edge<1, VISC>(a, C.X[e], N.X[e + 1], kl2, C.A[e], true, N.A[e + 1], true);
-                else edge<1, VISC>(a, C.X[3], On, kl2, C.A[3], true, C.A[3], false);
+                edge<2, EXT>(a, C.X[e], N.X[e], kl2, C.A[e], true, N.A[e], true);        // NW
+                if (e < 3) edge<1, EXT>(a, C.X[e], N.X[e + 1], kl2, C.A[e], true, N.A[e + 1], true);
+                else edge<1, EXT>(a, C.X[3], On, kl2, C.A[3], true, C.A[3], false);
             }
             // SW edge of (r+1, c_0): the NE edge of (r, c_0 - 1)
-            edge<1, VISC>(a, Wc, N.X[0], kl2, N.A[0], false, N.A[0], true);
+            edge<1, EXT>(a, Wc, N.X[0], kl2, N.A[0], false, N.A[0], true);
         } else {
             // even r: NE(c) = (r+1, c), NW(c) = (r+1, c-1)
             const Cell On = ring_at(j + 1, xw);                                   // (r+1, c_0 - 1)
 #pragma unroll
             for (int e = 0; e < 4; e++) {
-                edge<1, VISC>(a, C.X[e], N.X[e], kl2, C.A[e], true, N.A[e], true);        // NE
-                if (e >= 1) edge<2, VISC>(a, C.X[e], N.X[e - 1], kl2, C.A[e], true, N.A[e - 1], true);
-                else edge<2, VISC>(a, C.X[0], On, kl2, C.A[0], true, C.A[0], false);
+                edge<1, EXT>(a, C.X[e], N.X[e], kl2, C.A[e], true, N.A[e], true);        // NE
+                if (e >= 1) edge<2, EXT>(a, C.X[e], N.X[e - 1], kl2, C.A[e], true, N.A[e - 1], true);
+                else edge<2, EXT>(a, C.X[0], On, kl2, C.A[0], true, C.A[0], false);
             }
             // SE edge of (r+1, c_3): the NW edge of (r, c_3 + 1)
-            edge<2, VISC>(a, Ec, N.X[3], kl2, N.A[3], false, N.A[3], true);
+            edge<2, EXT>(a, Ec, N.X[3], kl2, N.A[3], false, N.A[3], true);
         }
     }
 
@@ -377,7 +378,7 @@ struct Tile {
                 ka = a.alpha_p * (1.0f - t);
                 kb = t * a.alpha_s;
             }
-            o[e] = cell_update(C.A[e].hi, C.A[e].lo, C.A[e].m1, C.A[e].m2, C.X[e].m, C.X[e].v1, C.X[e].v2,
+            o[e] = cell_update<EXT>(C.A[e].hi, C.A[e].lo, C.A[e].m1, C.A[e].m2, C.X[e].m, C.X[e].v1, C.X[e].v2,
                                rt, ka, kb, kappa, qr, dtf, a.g, __fmul_rn(dtf, a.tau), a.h_dry, cl);
         }
         if (!lane_own) return;       // columns written by the neighbouring tile
@@ -430,6 +431,7 @@ struct Tile {
 };
 
 // Frame CTA: kFrameCells consecutive cells of the frame, one per lane per round.
+template <bool EXT>
 __device__ __forceinline__ void frame_cells(const StepArgs &a, long long f0, unsigned &cwb, FF &outd,
                                             FF &clq)
 {
@@ -450,12 +452,12 @@ __device__ __forceinline__ void frame_cells(const StepArgs &a, long long f0, uns
             r = a.ry0 + rb;
             c = cb < a.cx0 ? cb : cx1 + (cb - a.cx0);
         }
-        gather_cell(a, sc, r, c, cwb, outd, clq);
+        gather_cell<EXT>(a, sc, r, c, cwb, outd, clq);
     }
 }
 
 // 128 registers and a 2 x 2-row ring (13.6 KB) let 15-16 one-warp CTAs share an SM
-template <bool CLS, bool VISC>
+template <bool CLS, bool EXT>
 __global__ void __launch_bounds__(32, ASX_STRIP_MINB) step_strip_kernel(const StepArgs a, const __grid_constant__ StripMaps maps)
 {
     extern __shared__ __align__(128) unsigned char smem_raw[];
@@ -486,7 +488,7 @@ __global__ void __launch_bounds__(32, ASX_STRIP_MINB) step_strip_kernel(const St
             if (threadIdx.x == 0) atomicOr(&a.ctl->err, kErrTimeout);
             return;
         }
-        Tile<CLS, VISC> T(a, S, s_cls, maps, c0, r0, own_c, own_r);
+        Tile<CLS, EXT> T(a, S, s_cls, maps, c0, r0, own_c, own_r);
         T.run();
         if (__any_sync(0xffffffffu, T.timed_out)) {
             // a tensor copy did not arrive in time: flag the error, wait (bounded) for
@@ -503,7 +505,7 @@ __global__ void __launch_bounds__(32, ASX_STRIP_MINB) step_strip_kernel(const St
         clq = T.clq.value();
     } else {
         FF o, cl;
-        frame_cells(a, (long long)(blockIdx.x - a.ntiles) * kFrameCells, cwb, o, cl);
+        frame_cells<EXT>(a, (long long)(blockIdx.x - a.ntiles) * kFrameCells, cwb, o, cl);
         outq = o.value();
         clq = cl.value();
     }
@@ -574,13 +576,14 @@ cudaError_t step_strip_configure()
 
 cudaError_t launch_step_strip(const StepArgs &a, const StripMaps &maps, cudaStream_t s)
 {
-    // land-cover classes (uint8 ids and per-class tables) or per-cell theta; with or
-    // without the artificial viscosity
+    // land-cover classes (uint8 ids and per-class tables) or per-cell theta; with the
+    // optional terms (viscosity, linear resistance, dry threshold) or the plain scheme
+    const bool ext = a.visc || a.tau > 0.0f || a.h_dry > 0.0f;
     if (a.cls) {
-        if (a.visc) step_strip_kernel<true, true><<<a.nblocks, 32, strip_smem<true>(), s>>>(a, maps);
+        if (ext) step_strip_kernel<true, true><<<a.nblocks, 32, strip_smem<true>(), s>>>(a, maps);
         else step_strip_kernel<true, false><<<a.nblocks, 32, strip_smem<true>(), s>>>(a, maps);
     } else {
-        if (a.visc) step_strip_kernel<false, true><<<a.nblocks, 32, strip_smem<false>(), s>>>(a, maps);
+        if (ext) step_strip_kernel<false, true><<<a.nblocks, 32, strip_smem<false>(), s>>>(a, maps);
         else step_strip_kernel<false, false><<<a.nblocks, 32, strip_smem<false>(), s>>>(a, maps);
     }
     return cudaGetLastError();

@@ -49,7 +49,7 @@ typedef enum {
     ASX_ETIMEOUT = 6   /* a bounded wait inside a kernel ran out */
 } asx_status;
 
-enum { ASX_BC_WALL = 0, ASX_BC_FREE = 1 };
+enum { ASX_BC_WALL = 0, ASX_BC_FREE = 1, ASX_BC_FLUX = 2, ASX_BC_DIRICHLET = 3 };
 enum { ASX_SIDE_W = 0, ASX_SIDE_E = 1, ASX_SIDE_S = 2, ASX_SIDE_N = 3 };
 enum { ASX_PTR_HOST = 0, ASX_PTR_DEVICE = 1 };
 #define ASX_MAX_CLASSES 16
@@ -58,11 +58,20 @@ enum { ASX_PTR_HOST = 0, ASX_PTR_DEVICE = 1 };
 typedef struct asx_raster asx_raster;      /* opaque, owned by the library */
 
 /* Geometry and boundaries of one raster (Sec. 2.2 (a); boundary types of Sec. 3).
- *   bc[side]            ASX_BC_WALL (mirror: the edge carries nothing) or ASX_BC_FREE
- *                       (free discharge: a ghost copy of the inner cell, outflow only).
- *   free_begin/free_end with bc = FREE, free discharge applies to the positions
- *                       [begin, end) along that side (the column for S/N, the row for
- *                       W/E) and the rest of the side is a wall; begin == end: all.
+ *   bc[side]            ASX_BC_WALL (mirror: the edge carries nothing), ASX_BC_FREE
+ *                       (free discharge: a ghost copy of the inner cell, outflow only),
+ *                       ASX_BC_FLUX (given mass flux asx_params.bc_q[side] per unit
+ *                       length, entering along the side's inward normal; an edge of the
+ *                       side admits l q (n_side . n_edge), carrying the velocity q / h of
+ *                       the cell's depth h, at least the critical depth (q^2/g)^(1/3);
+ *                       no pressure term) or ASX_BC_DIRICHLET (Sec. 4, Eq. numerics-bc: a
+ *                       ghost cell on the inner cell's bed and porosity with depth
+ *                       asx_params.bc_h[side] and velocity -bc_u[side] n_side, through the
+ *                       interior edge formulas).  Mass through FLUX and DIRICHLET edges
+ *                       is booked in the ledger's outflow (inflow negative).
+ *   free_begin/free_end the side's type applies to the positions [begin, end) along it
+ *                       (the column for S/N, the row for W/E) and the rest of the side is
+ *                       a wall; begin == end: all of it.
  *   n_classes           0: porosity is a float per cell; 1..ASX_MAX_CLASSES: each cell
  *                       holds a uint8 land-cover class and asx_params gives per-class
  *                       porosity and coefficients.
@@ -116,6 +125,7 @@ typedef struct {
     double sample_dt;
     int viscosity;
     double tau, h_dry;
+    double bc_q[4], bc_h[4], bc_u[4];   /* per side, see asx_raster_desc.bc */
 } asx_params;
 
 /* Water budget since the last asx_set_fields, all in m^3 (float64):
@@ -211,7 +221,8 @@ typedef struct asx_ensemble asx_ensemble;
 /* One scenario: geometry, boundaries and parameters as in asx_raster_desc / asx_params
  * (per-cell porosity, scalar alpha_s / alpha_p), a rain table of at most 8 points (host
  * pointers, copied), the end time t_end [s] the scenario runs to, the hydrograph interval
- * sample_dt and capacity max_samples, and max_steps (0 = no limit). */
+ * sample_dt and capacity max_samples, max_steps (0 = no limit), and the per-side values of
+ * ASX_BC_FLUX / ASX_BC_DIRICHLET sides (bc_q, bc_h, bc_u as in asx_params). */
 typedef struct {
     int rows, cols;
     double edge_m;
@@ -222,6 +233,7 @@ typedef struct {
     double t_end, sample_dt;
     int max_samples;
     long long max_steps;
+    double bc_q[4], bc_h[4], bc_u[4];
 } asx_scenario_desc;
 
 /* Launch shape of the ensemble kernel: CTAs per cluster (1, 2, 4, 8) sharing one

@@ -24,7 +24,8 @@
  *   - linear soil resistance: Sec. 4 (Thacker's problem), Eq. eq_soil_friction_thacker
  *                             (optional, tau = 0 by default)
  *   - rain:                   Appendix C (piecewise-linear hyetograph)
- *   - boundary types:         Sec. 3 "Data In" (free discharge default, wall)
+ *   - boundary types:         Sec. 3 "Data In" (free discharge default, wall, given
+ *                             mass flux) and Sec. 4, Eq. numerics-bc (Dirichlet)
  *
  * Readings of points the paper leaves open (each is listed in the design notes):
  *   - raster: pointy-top hexagons in rows along x, every row `cols` cells long, odd
@@ -61,6 +62,8 @@
 #define ORC_N 3
 #define ORC_WALL 0
 #define ORC_FREE 1
+#define ORC_FLUX 2          /* given mass flux (Sec. 3, boundary conditions) */
+#define ORC_DIRICHLET 3     /* given depth and velocity (Sec. 4, Eq. numerics-bc) */
 
 typedef struct {
     int rows, cols;
@@ -83,6 +86,9 @@ typedef struct {
                                (Sec. 4, Eq. eq_soil_friction_thacker); 0 = none */
     double h_dry;           /* depth [m] below which a cell's velocity is set to zero after
                                the friction step; 0 = none (dry means m = 0 exactly) */
+    double bc_q[4];         /* ORC_FLUX: inflow per unit length of the side [m^2/s] */
+    double bc_h[4];         /* ORC_DIRICHLET: ghost depth [m] */
+    double bc_u[4];         /* ORC_DIRICHLET: ghost speed along the inward normal [m/s] */
 } orc_problem;
 
 typedef struct {
@@ -126,13 +132,13 @@ int orc_neighbour(int rows, int cols, int r, int c, int d, int *j, int *side)
     return 1;
 }
 
-/* Boundary type of the edge of cell (r, c) on `side`. */
-static int orc_is_free(const orc_problem *p, int side, int r, int c)
+/* Boundary type of the edge of cell (r, c) on `side`: the side's type inside its interval
+ * [free_begin, free_end) of positions (all of it when begin == end), a wall outside. */
+static int orc_bc_at(const orc_problem *p, int side, int r, int c)
 {
     int pos = (side == ORC_S || side == ORC_N) ? c : r;
-    if (p->bc[side] != ORC_FREE) return 0;
-    if (p->free_begin[side] == p->free_end[side]) return 1;
-    return pos >= p->free_begin[side] && pos < p->free_end[side];
+    if (p->free_begin[side] == p->free_end[side]) return p->bc[side];
+    return (pos >= p->free_begin[side] && pos < p->free_end[side]) ? p->bc[side] : ORC_WALL;
 }
 
 double orc_sigma(double l) { return 1.5 * sqrt(3.0) * l * l; }
@@ -270,17 +276,57 @@ int orc_step(const orc_problem *p, const double *m, const double *v1, const doub
                         J1 += l * cij * mu * (v1[j] - v1[i]);
                         J2 += l * cij * mu * (v2[j] - v2[i]);
                     }
-                } else if (orc_is_free(p, side, r, c)) {
-                    /* free discharge: ghost = copy of cell i, outflow only */
-                    const double vn = v1[i] * n1 + v2[i] * n2;
-                    if (vn > 0.0) {
-                        L -= l * m[i] * vn;
-                        J1 -= l * m[i] * v1[i] * vn;
-                        J2 -= l * m[i] * v2[i] * vn;
-                        out_rate += l * m[i] * vn;
+                } else {
+                    const int bt = orc_bc_at(p, side, r, c);
+                    /* outward unit normal of the side */
+                    const double ns1 = side == ORC_W ? -1.0 : side == ORC_E ? 1.0 : 0.0;
+                    const double ns2 = side == ORC_S ? -1.0 : side == ORC_N ? 1.0 : 0.0;
+                    if (bt == ORC_FREE) {
+                        /* free discharge: ghost = copy of cell i, outflow only */
+                        const double vn = v1[i] * n1 + v2[i] * n2;
+                        if (vn > 0.0) {
+                            L -= l * m[i] * vn;
+                            J1 -= l * m[i] * v1[i] * vn;
+                            J2 -= l * m[i] * v2[i] * vn;
+                            out_rate += l * m[i] * vn;
+                        }
+                    } else if (bt == ORC_FLUX && p->bc_q[side] > 0.0) {
+                        /* given mass flux q along the inward side normal: the edge admits
+                         * l q (n_side . n); the water enters with speed q / h, h the
+                         * cell's depth but at least the critical depth (q^2 / g)^(1/3);
+                         * the ghost's surface is the cell's, so no pressure term */
+                        const double q = p->bc_q[side];
+                        const double qin = l * q * (ns1 * n1 + ns2 * n2);
+                        const double hc = cbrt(q * q / g);
+                        const double uin = q / (hi > hc ? hi : hc);
+                        L += qin;
+                        J1 += qin * uin * (-ns1);
+                        J2 += qin * uin * (-ns2);
+                        out_rate -= qin;
+                    } else if (bt == ORC_DIRICHLET) {
+                        /* given depth and velocity: a ghost cell on cell i's bed and
+                         * porosity with h = h_b and v = -u_b n_side, through the same
+                         * edge formulas as an interior neighbour (no viscosity) */
+                        const double hg = p->bc_h[side], mg = p->theta[i] * hg;
+                        const double vg1 = -p->bc_u[side] * ns1, vg2 = -p->bc_u[side] * ns2;
+                        const double vb1 = (v1[i] + vg1) / 2.0;
+                        const double vb2 = (v2[i] + vg2) / 2.0;
+                        const double vn = vb1 * n1 + vb2 * n2;
+                        const double dw = g * (hg - hi);
+                        double thh = 0.0, hat;
+                        if (vn > 0.0) thh = m[i];
+                        else if (vn < 0.0) thh = mg;
+                        if (vn != 0.0) hat = thh;
+                        else hat = (dw < 0.0) ? m[i] : mg;
+                        L -= l * thh * vn;
+                        J1 -= l * thh * vb1 * vn;
+                        J2 -= l * thh * vb2 * vn;
+                        S1 -= 0.5 * l * dw * hat * n1;
+                        S2 -= 0.5 * l * dw * hat * n2;
+                        out_rate += l * thh * vn;
                     }
+                    /* wall: mirror ghost, v_n = 0 and w_j = w_i, nothing to add */
                 }
-                /* wall: mirror ghost, v_n = 0 and w_j = w_i, nothing to add */
             }
 
             {

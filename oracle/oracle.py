@@ -51,7 +51,8 @@ class _Problem(C.Structure):
                 ("alpha_s", C.POINTER(C.c_double)), ("alpha_p", C.POINTER(C.c_double)),
                 ("n_rain", C.c_int), ("rain_t", C.POINTER(C.c_double)),
                 ("rain_r", C.POINTER(C.c_double)), ("viscosity", C.c_int), ("tau", C.c_double),
-                ("h_dry", C.c_double)]
+                ("h_dry", C.c_double), ("bc_q", C.c_double * 4), ("bc_h", C.c_double * 4),
+                ("bc_u", C.c_double * 4)]
 
 
 class Ledger(C.Structure):
@@ -109,7 +110,8 @@ class Problem:
 
     def __init__(self, rows, cols, l, z, theta, alpha_s, alpha_p, bc=(WALL, WALL, WALL, WALL),
                  g=9.81, cfl=0.5, dt_max=1.0, rain_t=(), rain_r=(), viscosity=False,
-                 free_range=((0, 0), (0, 0), (0, 0), (0, 0)), tau=0.0, h_dry=0.0):
+                 free_range=((0, 0), (0, 0), (0, 0), (0, 0)), tau=0.0, h_dry=0.0, bc_q=(0.0,) * 4,
+                 bc_h=(0.0,) * 4, bc_u=(0.0,) * 4):
         n = rows * cols
         self.rows, self.cols, self.l = int(rows), int(cols), float(l)
         self.z = _f64(z, n)
@@ -125,12 +127,15 @@ class Problem:
         self.viscosity = bool(viscosity)
         self.tau = float(tau)
         self.h_dry = float(h_dry)
+        self.bc_q, self.bc_h, self.bc_u = (tuple(float(x) for x in v) for v in (bc_q, bc_h, bc_u))
         self._s = _Problem(self.rows, self.cols, self.l, (C.c_int * 4)(*self.bc),
                            (C.c_int * 4)(*[a for a, _ in self.free_range]),
                            (C.c_int * 4)(*[b for _, b in self.free_range]), self.g, self.cfl,
                            self.dt_max, _dp(self.z), _dp(self.theta), _dp(self.alpha_s),
                            _dp(self.alpha_p), int(self.rain_t.size), _dp(self.rain_t),
-                           _dp(self.rain_r), int(self.viscosity), self.tau, self.h_dry)
+                           _dp(self.rain_r), int(self.viscosity), self.tau, self.h_dry,
+                           (C.c_double * 4)(*self.bc_q), (C.c_double * 4)(*self.bc_h),
+                           (C.c_double * 4)(*self.bc_u))
 
     @property
     def n(self):
@@ -212,7 +217,8 @@ def from_scenario(sc, viscosity=None):
     return Problem(sc.rows, sc.cols, sc.l, sc.z, sc.theta, sc.alpha_s, sc.alpha_p, bc=sc.bc,
                    g=sc.g, cfl=sc.cfl, dt_max=sc.dt_max, rain_t=sc.rain_t, rain_r=sc.rain_r,
                    viscosity=viscosity, free_range=sc.free_range, tau=getattr(sc, "tau", 0.0),
-                   h_dry=getattr(sc, "h_dry", 0.0))
+                   h_dry=getattr(sc, "h_dry", 0.0), bc_q=getattr(sc, "bc_q", (0.0,) * 4),
+                   bc_h=getattr(sc, "bc_h", (0.0,) * 4), bc_u=getattr(sc, "bc_u", (0.0,) * 4))
 
 
 def friction(alpha, beta, g1, g2):

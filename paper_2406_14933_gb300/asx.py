@@ -44,7 +44,8 @@ class asx_params(C.Structure):
                 ("class_alpha_s", C.POINTER(C.c_float)), ("n_rain", C.c_int),
                 ("rain_t", C.POINTER(C.c_double)), ("rain_r", C.POINTER(C.c_double)),
                 ("sample_dt", C.c_double), ("viscosity", C.c_int), ("tau", C.c_double),
-                ("h_dry", C.c_double)]
+                ("h_dry", C.c_double), ("bc_q", C.c_double * 4), ("bc_h", C.c_double * 4),
+                ("bc_u", C.c_double * 4)]
 
 
 class asx_ledger(C.Structure):
@@ -62,7 +63,8 @@ class asx_scenario_desc(C.Structure):
                 ("cfl", C.c_double), ("dt_max", C.c_double), ("alpha_s", C.c_double),
                 ("alpha_p", C.c_double), ("n_rain", C.c_int), ("rain_t", C.POINTER(C.c_double)),
                 ("rain_r", C.POINTER(C.c_double)), ("t_end", C.c_double), ("sample_dt", C.c_double),
-                ("max_samples", C.c_int), ("max_steps", C.c_longlong)]
+                ("max_samples", C.c_int), ("max_steps", C.c_longlong), ("bc_q", C.c_double * 4),
+                ("bc_h", C.c_double * 4), ("bc_u", C.c_double * 4)]
 
 
 class asx_ensemble_tuning(C.Structure):

@@ -97,6 +97,8 @@ struct StepArgs {
     int visc;                          // 1: artificial viscosity on interior edges
     float tau;                         // linear soil resistance -tau h v [1/s] (0: none)
     float h_dry;                       // depth below which velocities are zeroed [m] (0: none)
+    float bq[4], bhc[4];               // FLUX sides: inflow per unit length, critical depth
+    float bh[4], bu[4];                // DIRICHLET sides: ghost depth, inflow speed
     DevCtl *ctl;
 };
 

@@ -313,11 +313,12 @@ __device__ __forceinline__ CellNew cell_update(float shi, float slo, float M1, f
     return o;
 }
 
-__device__ __forceinline__ bool side_is_free(const StepArgs &a, int side, int pos)
+// Boundary type at position pos along `side`: the side's type inside its interval
+// [fb, fe) (all of it when fb == fe), a wall outside.
+__device__ __forceinline__ int side_type(const StepArgs &a, int side, int pos)
 {
-    if (a.bc[side] != ASX_BC_FREE) return false;
-    if (a.fb[side] == a.fe[side]) return true;
-    return pos >= a.fb[side] && pos < a.fe[side];
+    if (a.fb[side] == a.fe[side]) return a.bc[side];
+    return (pos >= a.fb[side] && pos < a.fe[side]) ? a.bc[side] : ASX_BC_WALL;
 }
 
 // Neighbour of (r, c) in direction d (0 E, 1 NE, 2 NW, 3 W, 4 SW, 5 SE); odd rows are
@@ -384,6 +385,65 @@ __device__ __forceinline__ StepScalars step_scalars(const StepArgs &a)
     return s;
 }
 
+// Given-mass-flux edge of cell X in direction d on `side` (Sec. 3): the edge admits
+// l q (n_side . n_d) per unit time, entering along the inward side normal with speed
+// q / max(h, h_c), h_c = (q^2/g)^(1/3) the critical depth; no pressure term (the ghost's
+// surface is the cell's).  The depth increment kappa l q (n_side . n_d) is booked in outd
+// as negative outflow, exactly as applied.
+__device__ __forceinline__ void flux_edge(const StepArgs &a, const Cell &X, int d, int side, float kappa,
+                                          float &shi, float &slo, float &M1, float &M2, FF &outd)
+{
+    const float q = a.bq[side];
+    if (!(q > 0.0f)) return;
+    const float ns1 = side == ASX_SIDE_W ? -1.0f : side == ASX_SIDE_E ? 1.0f : 0.0f;
+    const float ns2 = side == ASX_SIDE_S ? -1.0f : side == ASX_SIDE_N ? 1.0f : 0.0f;
+    const float fin = __fmul_rn(__fmul_rn(a.l, q), __fmaf_rn(ns1, kN1[d], __fmul_rn(ns2, kN2[d])));
+    const float qd = __fmul_rn(kappa, fin);
+    const float mom = __fmul_rn(fin, __fdiv_rn(q, fmaxf(X.h, a.bhc[side])));
+    acc_add(shi, slo, qd);
+    M1 -= __fmul_rn(mom, ns1);
+    M2 -= __fmul_rn(mom, ns2);
+    outd.add(-qd);
+}
+
+// Dirichlet edge of cell X (stored at index k) in direction d on `side` (Sec. 4, Eq.
+// numerics-bc): a ghost cell on X's bed and porosity with depth h_b and velocity
+// -u_b n_side, through the interior edge function in its canonical orientation; the
+// mass through the edge is booked in outd (outflow positive).
+__device__ __forceinline__ void dirichlet_edge(const StepArgs &a, const StepScalars &s, const Cell &X, size_t k,
+                                               int d, int side, float &shi, float &slo, float &M1, float &M2,
+                                               FF &outd)
+{
+    const float ns1 = side == ASX_SIDE_W ? -1.0f : side == ASX_SIDE_E ? 1.0f : 0.0f;
+    const float ns2 = side == ASX_SIDE_S ? -1.0f : side == ASX_SIDE_N ? 1.0f : 0.0f;
+    Cell G;
+    G.h = a.bh[side];
+    G.m = __fmul_rn(cell_theta(a, k), G.h);
+    G.v1 = __fmul_rn(-a.bu[side], ns1);
+    G.v2 = __fmul_rn(-a.bu[side], ns2);
+    G.z = X.z;
+    float q, f1, f2, p1, p2;
+    switch (d) {
+    case 0: edge_terms<0>(X, G, s.kl2, s.l4, a.cpe[0][0], a.cpe[0][1], q, f1, f2, p1, p2); break;
+    case 1: edge_terms<1>(X, G, s.kl2, s.l4, a.cpe[1][0], a.cpe[1][1], q, f1, f2, p1, p2); break;
+    case 2: edge_terms<2>(X, G, s.kl2, s.l4, a.cpe[2][0], a.cpe[2][1], q, f1, f2, p1, p2); break;
+    case 3: edge_terms<0>(G, X, s.kl2, s.l4, a.cpe[0][0], a.cpe[0][1], q, f1, f2, p1, p2); break;
+    case 4: edge_terms<1>(G, X, s.kl2, s.l4, a.cpe[1][0], a.cpe[1][1], q, f1, f2, p1, p2); break;
+    default: edge_terms<2>(G, X, s.kl2, s.l4, a.cpe[2][0], a.cpe[2][1], q, f1, f2, p1, p2); break;
+    }
+    if (d < 3) {                  // X is the lower cell: it loses q
+        acc_add(shi, slo, -q);
+        M1 += p1 - f1;
+        M2 += p2 - f2;
+        outd.add(q);
+    } else {
+        acc_add(shi, slo, q);
+        M1 += p1 + f1;
+        M2 += p2 + f2;
+        outd.add(-q);
+    }
+}
+
 // The whole step for one cell (r, c), gathering its six neighbours from global memory:
 // each edge is evaluated in its canonical orientation (the lower cell first), so a
 // shared edge gives both cells the same mass increment wherever it is evaluated.
@@ -428,7 +488,10 @@ __device__ __forceinline__ void gather_cell(const StepArgs &a, const StepScalars
             }
         } else {
             const int pos = (side == ASX_SIDE_S || side == ASX_SIDE_N) ? c : r;
-            if (side_is_free(a, side, pos)) free_edge(I, d, s.kl2, s.l2, shi, slo, M1, M2, outd);
+            const int bt = side_type(a, side, pos);
+            if (bt == ASX_BC_FREE) free_edge(I, d, s.kl2, s.l2, shi, slo, M1, M2, outd);
+            else if (bt == ASX_BC_FLUX) flux_edge(a, I, d, side, s.kappa, shi, slo, M1, M2, outd);
+            else if (bt == ASX_BC_DIRICHLET) dirichlet_edge(a, s, I, k, d, side, shi, slo, M1, M2, outd);
             // wall: mirror ghost, the edge carries nothing
         }
     }

@@ -427,8 +427,12 @@ asx_status asx_create_ensemble(int n, const asx_scenario_desc *descs, void *cuda
     for (int i = 0; i < n; i++) {
         const asx_scenario_desc &d = descs[i];
         if (d.rows < 2 || d.cols < 2 || (long long)d.rows * d.cols >= (1LL << 31) || !(d.edge_m > 0)) return ASX_EINVAL;
-        for (int s = 0; s < 4; s++)
-            if (d.bc[s] != ASX_BC_WALL && d.bc[s] != ASX_BC_FREE) return ASX_EINVAL;
+        for (int s = 0; s < 4; s++) {
+            if (d.bc[s] < ASX_BC_WALL || d.bc[s] > ASX_BC_DIRICHLET) return ASX_EINVAL;
+            if (!(d.bc_q[s] >= 0) || !std::isfinite(d.bc_q[s]) || !(d.bc_h[s] >= 0) || !std::isfinite(d.bc_h[s]) ||
+                !std::isfinite(d.bc_u[s]))
+                return ASX_EINVAL;
+        }
         if (!(d.g > 0) || !(d.cfl > 0) || !(d.cfl <= 1) || !(d.dt_max > 0) || !(d.alpha_s >= 0) || !(d.alpha_p >= 0))
             return ASX_EINVAL;
         if (d.n_rain < 0 || d.n_rain > kEnsMaxRain || (d.n_rain > 0 && (!d.rain_t || !d.rain_r))) return ASX_EINVAL;
@@ -498,6 +502,10 @@ asx_status asx_create_ensemble(int n, const asx_scenario_desc *descs, void *cuda
             a.bc[s] = d.bc[s];
             a.fb[s] = d.free_begin[s];
             a.fe[s] = d.free_end[s];
+            a.bq[s] = (float)d.bc_q[s];
+            a.bhc[s] = (float)std::cbrt(d.bc_q[s] * d.bc_q[s] / d.g);
+            a.bh[s] = (float)d.bc_h[s];
+            a.bu[s] = (float)d.bc_u[s];
         }
         h.t_end = d.t_end;
         h.cfl = d.cfl;

@@ -261,7 +261,7 @@ asx_status asx_create_raster(const asx_raster_desc *desc, asx_raster **out)
         return ASX_EINVAL;
     if ((long long)desc->rows * desc->cols >= (1LL << 31)) return ASX_EINVAL;
     for (int s = 0; s < 4; s++) {
-        if (desc->bc[s] != ASX_BC_WALL && desc->bc[s] != ASX_BC_FREE) return ASX_EINVAL;
+        if (desc->bc[s] < ASX_BC_WALL || desc->bc[s] > ASX_BC_DIRICHLET) return ASX_EINVAL;
         if (desc->free_begin[s] < 0 || desc->free_end[s] < desc->free_begin[s]) return ASX_EINVAL;
     }
     if (desc->n_classes < 0 || desc->n_classes > kMaxClasses || desc->max_samples < 0) return ASX_EINVAL;
@@ -378,6 +378,10 @@ asx_status asx_set_params(asx_raster *r, const asx_params *p)
     if (p->viscosity != 0 && p->viscosity != 1) return fail(r, ASX_EINVAL, "viscosity must be 0 or 1");
     if (!(p->tau >= 0) || !std::isfinite(p->tau)) return fail(r, ASX_EINVAL, "tau must be >= 0");
     if (!(p->h_dry >= 0) || !std::isfinite(p->h_dry)) return fail(r, ASX_EINVAL, "h_dry must be >= 0");
+    for (int s = 0; s < 4; s++)
+        if (!(p->bc_q[s] >= 0) || !std::isfinite(p->bc_q[s]) || !(p->bc_h[s] >= 0) || !std::isfinite(p->bc_h[s]) ||
+            !std::isfinite(p->bc_u[s]))
+            return fail(r, ASX_EINVAL, "boundary values out of range (bc_q, bc_h >= 0, finite)");
     if (p->n_rain > 0 && (!p->rain_t || !p->rain_r)) return fail(r, ASX_EINVAL, "rain table missing");
     for (int k = 0; k < p->n_rain; k++) {
         if (!std::isfinite(p->rain_t[k]) || !std::isfinite(p->rain_r[k]) || p->rain_r[k] < 0)
@@ -410,6 +414,12 @@ asx_status asx_set_params(asx_raster *r, const asx_params *p)
     a.visc = p->viscosity;
     a.tau = (float)p->tau;
     a.h_dry = (float)p->h_dry;
+    for (int s = 0; s < 4; s++) {
+        a.bq[s] = (float)p->bc_q[s];
+        a.bhc[s] = (float)std::cbrt(p->bc_q[s] * p->bc_q[s] / p->g);
+        a.bh[s] = (float)p->bc_h[s];
+        a.bu[s] = (float)p->bc_u[s];
+    }
     const double s3 = std::sqrt(3.0) / 2.0;
     const double n1[3] = {1.0, 0.5, -0.5}, n2[3] = {0.0, s3, s3};
     for (int d = 0; d < 3; d++) {

@@ -51,6 +51,8 @@ class Ensemble:
             else:
                 d.max_samples = int(np.ceil(sc.t_end / sc.sample_dt)) + 2 if sc.sample_dt > 0 else 0
             d.max_steps = int(max_steps)
+            for s in range(4):
+                d.bc_q[s], d.bc_h[s], d.bc_u[s] = float(sc.bc_q[s]), float(sc.bc_h[s]), float(sc.bc_u[s])
             descs.append(d)
         self.handle = _a.asx_create_ensemble(descs, stream, device)
         for i, sc in enumerate(scenarios):

@@ -29,7 +29,7 @@ from dataclasses import dataclass, field
 import numpy as np
 
 MM_PER_H = 1.0e-3 / 3600.0          # 1 mm/h in m/s
-WALL, FREE = 0, 1
+WALL, FREE, FLUX, DIRICHLET = 0, 1, 2, 3
 ALPHA_S_DEFAULT = 0.00709           # soil friction coefficient fitted in the flume study (Sec. 4.3)
 ALPHA_P_DEFAULT = 73.39             # plant drag coefficient fitted in the flume study (Sec. 4.3)
 
@@ -65,6 +65,9 @@ class Scenario:
     viscosity: bool = False            # artificial viscosity on (Appendix A, Eq. eq_artif_visc)
     tau: float = 0.0                   # linear soil resistance -tau h v [1/s] (Thacker's problem)
     h_dry: float = 0.0                 # depth below which velocities are zeroed [m] (0 = none)
+    bc_q: tuple = (0.0, 0.0, 0.0, 0.0)  # FLUX sides: inflow per unit length [m^2/s]
+    bc_h: tuple = (0.0, 0.0, 0.0, 0.0)  # DIRICHLET sides: ghost depth [m]
+    bc_u: tuple = (0.0, 0.0, 0.0, 0.0)  # DIRICHLET sides: ghost speed along the inward normal [m/s]
 
     @property
     def n(self) -> int:

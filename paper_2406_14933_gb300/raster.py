@@ -60,6 +60,10 @@ class Raster:
         p.viscosity = int(bool(getattr(sc, "viscosity", False)))
         p.tau = float(getattr(sc, "tau", 0.0))
         p.h_dry = float(getattr(sc, "h_dry", 0.0))
+        for s in range(4):
+            p.bc_q[s] = float(sc.bc_q[s])
+            p.bc_h[s] = float(sc.bc_h[s])
+            p.bc_u[s] = float(sc.bc_u[s])
         if self.desc.n_classes:
             ct = _f32(sc.class_theta, -1)
             cp = _f32(sc.class_alpha_p, -1)

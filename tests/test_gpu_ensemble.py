@@ -95,3 +95,27 @@ def test_ensemble_autotune_and_oracle(asx, orc):
         qh = np.diff(np.concatenate([[0.0], res["samples"]])) / sc.sample_dt
         assert _rel_l2(E.hydrograph(i), qh) <= 1e-4
     E.close()
+
+
+def test_ensemble_inflow_boundary_matches_single_raster(asx, monkeypatch):
+    """A scenario fed through a given-mass-flux side runs in the ensemble exactly as a
+    single raster with the gather kernel (bit for bit), the inflow booked alike."""
+    import numpy as np
+    from paper_2406_14933_gb300 import inputs
+    from paper_2406_14933_gb300.ensemble import Ensemble
+    from paper_2406_14933_gb300.raster import Raster
+    monkeypatch.setenv("ASX_STEP_KERNEL", "gather")
+    sc = inputs.ensemble_member(5, n_override=96, t_end=60.0)
+    sc.bc = (inputs.FLUX, inputs.FREE, inputs.WALL, inputs.WALL)
+    sc.bc_q = (0.01, 0.0, 0.0, 0.0)
+    sc2 = inputs.ensemble_member(6, n_override=64, t_end=40.0)
+    E = Ensemble([sc, sc2])
+    E.run()
+    R = Raster(sc)
+    R.run_until(sc.t_end)
+    for a, b in zip(E.state(0), R.state()):
+        assert np.array_equal(a, b)
+    le, lr = E.ledger(0), R.ledger()
+    assert le.outflow == lr.outflow and le.outflow < 0.0
+    E.close()
+    R.close()

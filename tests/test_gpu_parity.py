@@ -354,3 +354,44 @@ def test_thacker_against_oracle_and_analytic(asx, orc):
     print(f"[thacker] {len(ts)} steps: depth {eh:.2e} discharge {eq:.2e} vs oracle; L1 depth {l1:.4f} vs analytic")
     assert eh <= 1e-4 and eq <= 1e-4
     assert l1 <= 0.015
+
+
+# ----------------------------------------------------------------------------- given flux, Dirichlet sides
+
+def _channel(rows, cols, l, slope, west, **kw):
+    x, _ = inputs.cell_centres(rows, cols, l)
+    sh = (rows, cols)
+    z = (slope * (x.max() - x)).astype(np.float32)
+    sc = inputs.Scenario(f"channel{rows}x{cols}", rows, cols, l, z, np.full(sh, 0.95, np.float32),
+                         np.full(sh, 0.00709, np.float32), np.full(sh, 30.0, np.float32),
+                         np.full(sh, 0.02, np.float32), np.zeros(sh, np.float32), np.zeros(sh, np.float32),
+                         bc=(west, inputs.FREE, inputs.WALL, inputs.WALL), **kw)
+    return sc
+
+
+@pytest.mark.parametrize("west", ["flux", "dirichlet"])
+def test_inflow_boundaries_against_oracle(asx, orc, west):
+    """A sloping vegetated channel (36 x 150 cells: strip tiles, with the boundary cells in
+    the frame) fed through its west side by a given mass flux (Sec. 3) or a Dirichlet
+    ghost (Sec. 4, Eq. numerics-bc), free at the east end: 200 steps with the oracle
+    replaying the GPU's time levels, depth and discharge relative L2 <= 1e-4, and the
+    budget (the inflow booked as negative outflow) closing to <= 1e-10."""
+    if west == "flux":
+        sc = _channel(36, 150, 1.0, 0.01, inputs.FLUX, bc_q=(0.02, 0.0, 0.0, 0.0))
+    else:
+        sc = _channel(36, 150, 1.0, 0.01, inputs.DIRICHLET, bc_h=(0.06, 0.0, 0.0, 0.0), bc_u=(0.4, 0.0, 0.0, 0.0))
+    R = _raster(asx, sc)
+    ts = [R.step(1) for _ in range(200)]
+    p = _oracle_problem(orc, sc)
+    res = p.run(p.mass(sc.h0), sc.v1_0, sc.v2_0, 0.0, ts[-1], t_replay=np.array(ts))
+    mg, vg1, vg2 = R.mass64()
+    eh = _rel_l2(p.depth(mg.ravel()), p.depth(res["m"]))
+    qo = np.concatenate([res["m"] * res["v1"], res["m"] * res["v2"]])
+    qg = np.concatenate([mg.ravel() * vg1.ravel(), mg.ravel() * vg2.ravel()])
+    eq = _rel_l2(qg, qo)
+    led = R.ledger()
+    print(f"[{west}] depth {eh:.2e} discharge {eq:.2e} outflow {led.outflow:.4e} oracle {res['ledger'].outflow:.4e}")
+    assert eh <= 1e-4 and eq <= 1e-4
+    assert led.outflow < 0.0 and led.outflow == pytest.approx(res["ledger"].outflow, rel=1e-4)
+    assert led.defect_rel <= 1e-10
+    R.close()

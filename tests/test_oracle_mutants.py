@@ -13,6 +13,13 @@ SRC = os.path.join(ROOT, "oracle", "asx_oracle.c")
 
 # name: (passage, original text, mutated text)
 MUTANTS = {
+    "flux_without_projection": ("given mass flux reading (l q n_side . n)",
+                                "const double qin = l * q * (ns1 * n1 + ns2 * n2);", "const double qin = l * q;"),
+    "flux_without_momentum": ("given mass flux reading (inflow momentum)", "J1 += qin * uin * (-ns1);",
+                              "J1 += 0.0 * uin;"),
+    "dirichlet_pressure_sign": ("Eq. numerics-bc ghost through Eq. fvm_2D_eq_frac.01",
+                                "S1 -= 0.5 * l * dw * hat * n1;\n                        S2 -= 0.5 * l * dw * hat * n2;\n                        out_rate += l * thh * vn;",
+                                "S1 += 0.5 * l * dw * hat * n1;\n                        S2 += 0.5 * l * dw * hat * n2;\n                        out_rate += l * thh * vn;"),
     "thacker_no_linear_resistance": ("Eq. eq_soil_friction_thacker (tau h v)",
                                      "orc_friction(m_new + dt * p->tau * h_new, beta",
                                      "orc_friction(m_new, beta"),
@@ -62,8 +69,8 @@ MUTANTS = {
                    "double c = sqrt(v1[i] * v1[i] + v2[i] * v2[i]) + sqrt(p->g * h);",
                    "double c = sqrt(v1[i] * v1[i] + v2[i] * v2[i]) + p->g * h;"),
     "free_side_inflow": ("free discharge reading (outflow only)",
-                         "if (vn > 0.0) {\n                        L -= l * m[i] * vn;",
-                         "if (vn != 0.0) {\n                        L -= l * m[i] * vn;"),
+                         "if (vn > 0.0) {\n                            L -= l * m[i] * vn;",
+                         "if (vn != 0.0) {\n                            L -= l * m[i] * vn;"),
     "outflow_misbooked": ("ledger (Table table_BasinSusita identity)", "out_rate += l * m[i] * vn;",
                           "out_rate += 0.5 * l * m[i] * vn;"),
     "cell_area_apothem": ("hexagon area with l = circumradius",

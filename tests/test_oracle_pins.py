@@ -482,3 +482,86 @@ def test_thacker_oracle_converges_to_analytic(orc):
     assert f["l1"] <= 0.6 * c["l1"]
     assert f["u"] == pytest.approx(f["u_ex"], rel=0.03)
     assert f["v"] == pytest.approx(f["v_ex"], rel=0.06)
+
+
+# ----------------------------------------------------------------------------- given mass flux, Dirichlet
+
+def _flux_problem(orc, rows, cols, l, q, z=None, h0=0.1, alpha_s=0.0, east=0):
+    n = rows * cols
+    zz = np.zeros(n) if z is None else z
+    p = orc.Problem(rows, cols, l, zz, np.ones(n), np.full(n, alpha_s), np.zeros(n), bc=(2, east, 0, 0),
+                    bc_q=(q, 0.0, 0.0, 0.0), dt_max=0.05)
+    return p, np.full(n, h0)
+
+
+def test_flux_boundary_inflow_by_hand(orc):
+    """Given mass flux q on the west side (Sec. 3): the edges on that side admit
+    l q (n_side . n_edge).  On 4 rows: every row's west edge (4 l) plus, for the even
+    rows 0 and 2, the NW / SW edges that leave the raster through the west side
+    (row 0: NW only, its SW leaves through the south side; row 2: both), each l / 2:
+    5.5 l in all.  One step from a lake at rest gains exactly dt q 5.5 l, and the ledger
+    books it as negative outflow."""
+    l, q = 1.0, 0.02
+    p, h = _flux_problem(orc, 4, 3, l, q)
+    m = p.mass(h)
+    res = p.run(m, np.zeros(12), np.zeros(12), 0.0, 0.05, max_steps=1)
+    dt = res["t"]
+    gain = (np.sum(res["m"]) - np.sum(m)) * p.sigma
+    assert gain == pytest.approx(dt * q * 5.5 * l, rel=1e-12)
+    led = res["ledger"]
+    assert led.outflow == pytest.approx(-dt * q * 5.5 * l, rel=1e-12)
+    # the inflow carries momentum east at q / h (h = 0.1 m above the critical depth): from
+    # rest, with no friction and no pressure term yet, v_1 = dt / sigma q_in (q / h) / m'
+    v1 = res["v1"].reshape(4, 3)
+    mn = res["m"].reshape(4, 3)
+    for r, share in ((1, 1.0), (2, 2.0), (3, 1.0)):
+        qin = l * q * share
+        assert v1[r, 0] == pytest.approx(dt / p.sigma * qin * (q / 0.1) / mn[r, 0], rel=1e-12)
+    assert np.max(np.abs(res["v2"])) <= 1e-12 * np.abs(v1).max()
+
+
+def test_flux_boundary_reaches_normal_depth(orc):
+    """A sloping channel (s = 1 %) fed by q = 0.01 m^2/s through its west side, free at
+    the east end, soil friction only: the flow settles to the uniform normal depth of
+    the friction balance alpha_s v^2 = g s h with v h = q, h_n = (alpha_s q^2 / (g s))^(1/3),
+    in the middle of the channel (Eqs. eq_tsa_darcy, fvm_2D_eq_frac.07 in steady state)."""
+    rows, cols, l, q, s, a_s, g = 12, 60, 1.0, 0.01, 0.01, 0.00709, 9.81
+    x, _ = inputs.cell_centres(rows, cols, l)
+    z = (s * (x.max() - x)).ravel()
+    hn = (a_s * q * q / (g * s)) ** (1.0 / 3.0)
+    p, h = _flux_problem(orc, rows, cols, l, q, z=z, h0=hn, alpha_s=a_s, east=1)
+    m = p.mass(h)
+    res = p.run(m, np.full(rows * cols, q / hn), np.zeros(rows * cols), 0.0, 300.0)
+    hm = res["m"].reshape(rows, cols)
+    mid = hm[rows // 2 - 1:rows // 2 + 1, cols // 3:2 * cols // 3]
+    qm = (res["m"] * res["v1"]).reshape(rows, cols)[rows // 2 - 1:rows // 2 + 1, cols // 3:2 * cols // 3]
+    assert np.mean(mid) == pytest.approx(hn, rel=0.03)
+    assert np.mean(qm) == pytest.approx(q, rel=0.03)
+    # steady: the outflow through the east side equals the inflow
+    p2 = orc.Problem(rows, cols, l, z, np.ones(rows * cols), np.full(rows * cols, a_s), np.zeros(rows * cols),
+                     bc=(2, 1, 0, 0), bc_q=(q, 0, 0, 0), dt_max=0.05)
+    one = p2.run(res["m"], res["v1"], res["v2"], 0.0, 10.0)
+    inflow_rate = q * (rows * 1.5 * l)            # projected west side, about 1.5 l per row
+    # over 10 more seconds storage hardly changes: net boundary flow ~ 0 against 10 s of inflow
+    assert abs(np.sum(one["m"]) - np.sum(res["m"])) * p2.sigma <= 0.02 * inflow_rate * 10.0
+    assert abs(one["ledger"].outflow) <= 0.02 * inflow_rate * 10.0
+
+
+def test_dirichlet_boundary_rest_and_inflow(orc):
+    """Dirichlet side (Sec. 4, Eq. numerics-bc): a ghost at the lake's own level and at
+    rest leaves the lake exactly at rest; a higher ghost level drives water in, and the
+    ledger books the inflow (storage gain = -outflow, no rain)."""
+    rows, cols, l = 6, 8, 1.0
+    n = rows * cols
+    for hb, moves in ((0.1, False), (0.15, True)):
+        p = orc.Problem(rows, cols, l, np.zeros(n), np.ones(n), np.zeros(n), np.zeros(n), bc=(3, 0, 0, 0),
+                        bc_h=(hb, 0, 0, 0), bc_u=(0.0, 0, 0, 0), dt_max=0.02)
+        m = p.mass(np.full(n, 0.1))
+        res = p.run(m, np.zeros(n), np.zeros(n), 0.0, 0.4)
+        led = res["ledger"]
+        if not moves:
+            assert np.max(np.abs(res["m"] - m)) == 0.0 and np.max(np.abs(res["v1"])) == 0.0
+        else:
+            gain = (np.sum(res["m"]) - np.sum(m)) * p.sigma
+            assert gain > 0 and gain == pytest.approx(-led.outflow, rel=1e-12)
+            assert np.all(res["v1"].reshape(rows, cols)[:, 0] > 0.0)

@@ -448,8 +448,9 @@ __device__ __forceinline__ void dirichlet_edge(const StepArgs &a, const StepScal
 // each edge is evaluated in its canonical orientation (the lower cell first), so a
 // shared edge gives both cells the same mass increment wherever it is evaluated.
 // EXT: the optional terms (artificial viscosity, linear resistance, dry threshold) are
-// compiled in; the ensemble, whose scenarios never set them, leaves them out.
-template <bool EXT = true>
+// compiled in; the ensemble, whose scenarios never set them, leaves them out.  BND: the
+// inflow sides (given mass flux, Dirichlet) are compiled in.
+template <bool EXT = true, bool BND = true>
 __device__ __forceinline__ void gather_cell(const StepArgs &a, const StepScalars &s, int r, int c,
                                             unsigned &cb, FF &outd, FF &clq)
 {
@@ -490,8 +491,8 @@ __device__ __forceinline__ void gather_cell(const StepArgs &a, const StepScalars
             const int pos = (side == ASX_SIDE_S || side == ASX_SIDE_N) ? c : r;
             const int bt = side_type(a, side, pos);
             if (bt == ASX_BC_FREE) free_edge(I, d, s.kl2, s.l2, shi, slo, M1, M2, outd);
-            else if (bt == ASX_BC_FLUX) flux_edge(a, I, d, side, s.kappa, shi, slo, M1, M2, outd);
-            else if (bt == ASX_BC_DIRICHLET) dirichlet_edge(a, s, I, k, d, side, shi, slo, M1, M2, outd);
+            else if (BND && bt == ASX_BC_FLUX) flux_edge(a, I, d, side, s.kappa, shi, slo, M1, M2, outd);
+            else if (BND && bt == ASX_BC_DIRICHLET) dirichlet_edge(a, s, I, k, d, side, shi, slo, M1, M2, outd);
             // wall: mirror ghost, the edge carries nothing
         }
     }

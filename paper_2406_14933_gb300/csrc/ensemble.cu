@@ -142,8 +142,9 @@ __device__ __forceinline__ void block_reduce(unsigned &cb, double &out, double &
     }
 }
 
-// The persistent ensemble kernel.  NT threads per CTA, K cells per thread per round.
-template <int NT, int K>
+// The persistent ensemble kernel.  NT threads per CTA, K cells per thread per round;
+// BND: scenarios with inflow sides (given mass flux, Dirichlet) are present.
+template <int NT, int K, bool BND>
 __global__ void __launch_bounds__(NT) ensemble_kernel(EnsScenario *scen, const int *order, int n_scen,
                                                      unsigned *queue)
 {
@@ -227,7 +228,7 @@ __global__ void __launch_bounds__(NT) ensemble_kernel(EnsScenario *scen, const i
 #pragma unroll
                 for (int u = 0; u < K; u++) {
                     const int i = i0 + u * NT;
-                    if (i < band) gather_cell<false>(sa, sc, rb0 + i / cols, i % cols, cb, outd, clq);
+                    if (i < band) gather_cell<false, BND>(sa, sc, rb0 + i / cols, i % cols, cb, outd, clq);
                 }
             }
             double out = outd.value(), cl = clq.value(), sto = 0.0;
@@ -296,18 +297,23 @@ __global__ void __launch_bounds__(NT) ensemble_kernel(EnsScenario *scen, const i
 
 using EnsKernel = void (*)(EnsScenario *, const int *, int, unsigned *);
 
-template <int NT, int K>
+template <int NT, int K, bool BND>
 EnsKernel ens_kernel_ptr()
 {
-    return ensemble_kernel<NT, K>;
+    return ensemble_kernel<NT, K, BND>;
 }
 
-EnsKernel ens_kernel(int nt, int k)
+template <bool BND>
+EnsKernel ens_kernel_b(int nt, int k)
 {
-    if (nt == 256) return k == 1 ? ens_kernel_ptr<256, 1>() : k == 2 ? ens_kernel_ptr<256, 2>() : ens_kernel_ptr<256, 4>();
-    if (nt == 512) return k == 1 ? ens_kernel_ptr<512, 1>() : k == 2 ? ens_kernel_ptr<512, 2>() : ens_kernel_ptr<512, 4>();
-    return k == 1 ? ens_kernel_ptr<128, 1>() : k == 2 ? ens_kernel_ptr<128, 2>() : ens_kernel_ptr<128, 4>();
+    if (nt == 256)
+        return k == 1 ? ens_kernel_ptr<256, 1, BND>() : k == 2 ? ens_kernel_ptr<256, 2, BND>() : ens_kernel_ptr<256, 4, BND>();
+    if (nt == 512)
+        return k == 1 ? ens_kernel_ptr<512, 1, BND>() : k == 2 ? ens_kernel_ptr<512, 2, BND>() : ens_kernel_ptr<512, 4, BND>();
+    return k == 1 ? ens_kernel_ptr<128, 1, BND>() : k == 2 ? ens_kernel_ptr<128, 2, BND>() : ens_kernel_ptr<128, 4, BND>();
 }
+
+EnsKernel ens_kernel(int nt, int k, bool bnd) { return bnd ? ens_kernel_b<true>(nt, k) : ens_kernel_b<false>(nt, k); }
 
 }  // namespace
 }  // namespace asx
@@ -330,6 +336,7 @@ struct asx_ensemble {
     unsigned *queue = nullptr;
     asx_ensemble_tuning tuning{};
     bool tuned = false, have_fields_all = false;
+    bool bnd = false;                       // some scenario has an inflow side
     std::vector<char> have_fields;
     cudaGraphExec_t graph = nullptr;
     asx_ensemble_tuning graph_tuning{};
@@ -360,9 +367,9 @@ bool tuning_valid(const asx_ensemble_tuning &t)
 }
 
 // Clusters of this shape that fit on the device at once.
-int resident_clusters(const asx_ensemble_tuning &t)
+int resident_clusters(const asx_ensemble_tuning &t, bool bnd)
 {
-    EnsKernel f = ens_kernel(t.threads, t.cells_per_thread);
+    EnsKernel f = ens_kernel(t.threads, t.cells_per_thread, bnd);
     cudaLaunchConfig_t cfg{};
     cudaLaunchAttribute at[1];
     at[0].id = cudaLaunchAttributeClusterDimension;
@@ -380,8 +387,8 @@ int resident_clusters(const asx_ensemble_tuning &t)
 
 cudaError_t launch_ensemble(asx_ensemble *e, const asx_ensemble_tuning &t, cudaStream_t s)
 {
-    EnsKernel f = ens_kernel(t.threads, t.cells_per_thread);
-    const int nc = std::min(resident_clusters(t), e->n);
+    EnsKernel f = ens_kernel(t.threads, t.cells_per_thread, e->bnd);
+    const int nc = std::min(resident_clusters(t, e->bnd), e->n);
     cudaLaunchConfig_t cfg{};
     cudaLaunchAttribute at[1];
     at[0].id = cudaLaunchAttributeClusterDimension;
@@ -444,6 +451,9 @@ asx_status asx_create_ensemble(int n, const asx_scenario_desc *descs, void *cuda
     e->device = device;
     e->stream = (cudaStream_t)cuda_stream;
     e->desc.assign(descs, descs + n);
+    for (int i = 0; i < n; i++)
+        for (int sd = 0; sd < 4; sd++)
+            if (descs[i].bc[sd] == ASX_BC_FLUX || descs[i].bc[sd] == ASX_BC_DIRICHLET) e->bnd = true;
     e->have_fields.assign(n, 0);
     if (cudaSetDevice(device) != cudaSuccess) { delete e; return ASX_ECUDA; }
     // planes per scenario: 8 state (2 parities x m_hi, m_lo, v1, v2), z, theta, 4 initial

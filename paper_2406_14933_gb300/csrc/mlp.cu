@@ -416,7 +416,8 @@ namespace {
 // each as soon as the previous layer's MMAs have finished reading it.  CTAs are persistent
 // over the tiles.  Shared memory: 16 KB input + 64 KB activations + 128 KB weights.
 
-constexpr int kFusedThreads = 128;
+constexpr int kFusedThreads = 512;     // 16 warps: warp w reads TMEM lanes 32 (w % 4) .. +31
+constexpr int kColGroups = kFusedThreads / 128;   // ... and a quarter of the columns, w / 4
 constexpr unsigned kWtBytes1 = (unsigned)kHid * kInPad * 2;   // W1: 32 KB
 constexpr unsigned kWtBytesH = (unsigned)kHid * kHid * 2;     // W2, W3: 128 KB each
 constexpr unsigned kWtBytes4 = (unsigned)kOut * kHid * 2;     // W4: 64 KB
@@ -497,11 +498,12 @@ __device__ __forceinline__ void layer_mma(unsigned tmem, const unsigned char *a,
     }
 }
 
-// Hidden-layer epilogue of accumulator row r (this thread's TMEM lane): + bias, ReLU,
-// BF16 (round to nearest even), into the activation image.
-__device__ __forceinline__ void epi_hidden(unsigned trow, const float *bias, unsigned char *act, int r)
+// Hidden-layer epilogue of accumulator row r (this thread's TMEM lane), columns
+// [c0, c1): + bias, ReLU, BF16 (round to nearest even), into the activation image.
+__device__ __forceinline__ void epi_hidden(unsigned trow, const float *bias, unsigned char *act, int r, int c0,
+                                           int c1)
 {
-    for (int nc = 0; nc < kHid; nc += 16) {
+    for (int nc = c0; nc < c1; nc += 16) {
         float v[16];
         tc_ld16(trow + (unsigned)nc, v);
         unsigned w[8];
@@ -549,7 +551,9 @@ __global__ void __launch_bounds__(kFusedThreads, 1) mlp_fused_fwd_kernel(const F
     __syncthreads();
     asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
     const unsigned tmem = tmem_base;
-    const unsigned trow = tmem + ((unsigned)(warp * 32) << 16);
+    const int quarter = warp & 3, cgroup = warp >> 2;
+    const int row = quarter * 32 + (tid & 31);              // this thread's accumulator row
+    const unsigned trow = tmem + ((unsigned)(quarter * 32) << 16);
     unsigned pa = 0, pw = 0, pm = 0;          // phases of the three barriers
     int a_out = 0, w_out = 0, m_out = 0;      // completions issued but not yet waited for
     bool ok = true;
@@ -564,38 +568,32 @@ __global__ void __launch_bounds__(kFusedThreads, 1) mlp_fused_fwd_kernel(const F
     const float *b4 = s_bias + 3 * kHid;
     for (int t = blockIdx.x; t < ntiles && ok; t += gridDim.x) {
         const int m0 = t * kTM;
-        // ---- input tile: thread r converts query row m0 + r to BF16, K padded to 64
-        {
-            const int m = m0 + tid;
-            float xv[40];
-            if (m < f.batch) {
-                const float4 *xr = reinterpret_cast<const float4 *>(f.x + (size_t)m * kIn);
-#pragma unroll
-                for (int q = 0; q < kIn / 4; q++) {
-                    const float4 v = xr[q];
-                    xv[4 * q] = v.x;
-                    xv[4 * q + 1] = v.y;
-                    xv[4 * q + 2] = v.z;
-                    xv[4 * q + 3] = v.w;
+        // ---- input tile to BF16, K padded to 64: one (row, 8-column group) per thread and pass
+        for (int u = tid; u < kTM * (kInPad / 8); u += kFusedThreads) {
+            const int r = u % kTM, kg = u / kTM, m = m0 + r;
+            float xv[8] = {0.0f, 0.0f, 0.0f, 0.0f, 0.0f, 0.0f, 0.0f, 0.0f};
+            if (m < f.batch && kg * 8 < kIn) {
+                const float4 *xr = reinterpret_cast<const float4 *>(f.x + (size_t)m * kIn + kg * 8);
+                const float4 a4 = xr[0];
+                xv[0] = a4.x;
+                xv[1] = a4.y;
+                xv[2] = a4.z;
+                xv[3] = a4.w;
+                if (kg * 8 + 4 < kIn) {
+                    const float4 b4v = xr[1];
+                    xv[4] = b4v.x;
+                    xv[5] = b4v.y;
+                    xv[6] = b4v.z;
+                    xv[7] = b4v.w;
                 }
-            } else {
-#pragma unroll
-                for (int q = 0; q < kIn; q++) xv[q] = 0.0f;
             }
+            unsigned w[4];
 #pragma unroll
-            for (int q = kIn; q < 40; q++) xv[q] = 0.0f;
-#pragma unroll
-            for (int kg = 0; kg < kInPad / 8; kg++) {
-                unsigned w[4] = {0u, 0u, 0u, 0u};
-                if (kg < 5) {
-#pragma unroll
-                    for (int j = 0; j < 4; j++) {
-                        const __nv_bfloat162 h = __floats2bfloat162_rn(xv[8 * kg + 2 * j], xv[8 * kg + 2 * j + 1]);
-                        w[j] = *reinterpret_cast<const unsigned *>(&h);
-                    }
-                }
-                *reinterpret_cast<uint4 *>(sX + cm_off(tid, kg * 8)) = make_uint4(w[0], w[1], w[2], w[3]);
+            for (int j = 0; j < 4; j++) {
+                const __nv_bfloat162 h = __floats2bfloat162_rn(xv[2 * j], xv[2 * j + 1]);
+                w[j] = *reinterpret_cast<const unsigned *>(&h);
             }
+            *reinterpret_cast<uint4 *>(sX + cm_off(r, kg * 8)) = make_uint4(w[0], w[1], w[2], w[3]);
         }
         asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
         __syncthreads();
@@ -645,11 +643,11 @@ __global__ void __launch_bounds__(kFusedThreads, 1) mlp_fused_fwd_kernel(const F
                 a_out = w_out = 1;
             }
             if (l < 3) {
-                epi_hidden(trow, bias[l], sAct, tid);
+                epi_hidden(trow, bias[l], sAct, row, cgroup * (kHid / kColGroups), (cgroup + 1) * (kHid / kColGroups));
                 asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
             } else {
-                const int m = m0 + tid;
-                for (int nc = 0; nc < kOut; nc += 16) {
+                const int m = m0 + row;
+                for (int nc = cgroup * (kOut / kColGroups); nc < (cgroup + 1) * (kOut / kColGroups); nc += 16) {
                     float v[16];
                     tc_ld16(trow + (unsigned)nc, v);
                     if (m < f.batch) {

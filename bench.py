@@ -106,6 +106,22 @@ def _dist():
     return ws, rank
 
 
+def max_over_ranks(vals, device):
+    """Each value's maximum over the ranks of the process group (the slowest replica sets
+    the job's time)."""
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor(vals, dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return [float(x) for x in t]
+
+
+def job_rate(ws, cells, steps, seconds):
+    """Whole-job cell-updates per second: every replica updates `cells` cells `steps`
+    times; the job takes the slowest replica's time."""
+    return ws * cells * steps / seconds
+
+
 def _workload_config(sc, k, t_warm=T_WARM):
     return {"workload": f"carved catchment {sc.rows}x{sc.cols} hex, edge {sc.l:g} m, "
                         f"3 land-cover classes, double-peak storm, window from t={t_warm:.0f} s",
@@ -171,14 +187,11 @@ def run_cuda(args):
     e2e_s = time.perf_counter() - w0
     R.close()
     if ws > 1:
-        import torch.distributed as dist
-        t = torch.tensor([ms, e2e_s], device="cuda", dtype=torch.float64)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms, e2e_s = float(t[0]), float(t[1])
+        ms, e2e_s = max_over_ranks([ms, e2e_s], "cuda")
     if rank != 0:
         return None
     ms_step = ms / args.steps
-    value = ws * n * args.steps / (ms / 1e3)
+    value = job_rate(ws, n, args.steps, ms / 1e3)
     peak, peak_kind = _peaks()
     achieved = BYTES_PER_CELL * n / (ms_step / 1e3) / 1e9
     traffic = _read_traffic(n) if os.environ.get("ASX_STEP_KERNEL", "strip") == "strip" else None
@@ -195,7 +208,7 @@ def run_cuda(args):
                      "peak_source": f"{peak_kind} copy bandwidth",
                      "note": "32 B algorithmic per cell-update / (step time incl. launch gap); "
                              "traffic: ncu DRAM bytes of a 2048x2048 window scaled by cells"},
-        "e2e": {"value": ws * n * args.steps / e2e_s, "unit": UNIT,
+        "e2e": {"value": job_rate(ws, n, args.steps, e2e_s), "unit": UNIT,
                 "h2d_bytes_per_step": 16 * n / args.steps, "d2h_bytes_per_step": 16 * n / args.steps},
         "gpu_launches": args.steps + 1,
         "clocks": clk.summary(),

@@ -405,31 +405,27 @@ namespace {
 
 // ----------------------------------------------------------------- the fused forward pass
 //
-// A CTA (eight warps) carries a tile of 128 queries through all four layers, and two CTAs
-// share an SM so that one's epilogues overlap the other's products.  The activations
-// (128 x 256 BF16, 64 KB; the first 16 KB hold the layer-1 input, K padded to 64, until
-// layer 1's products have read it) stay in shared memory in the tensor core's core-matrix
-// layout; every product accumulates in the CTA's 256-column TMEM accumulator (two halves
-// of 128 columns, one per 128-row half of the weights), and each layer's epilogue (bias,
-// ReLU, BF16) writes the next layer's operand straight back to shared memory.  The weights
-// stream through a ring of three 16 KB slots, two units ahead of the products: a unit is a
-// 128-row half of a 64-wide K chunk of one layer's weights, contiguous in a copy of the
-// weights kept in exactly the shared-memory image (22 units per tile), loaded by bulk copy
-// (cp.async.bulk) on the slot's "full" mbarrier and released by the products' commit on
-// its "empty" mbarrier.  CTAs are persistent over the tiles.  Shared memory: 64 KB + 48 KB.
+// One CTA (four warps) carries a tile of 128 queries through all four layers: the input
+// tile (BF16, K padded to 64) and the activations (128 x 256 BF16) stay in shared memory
+// in the tensor core's core-matrix layout, every product accumulates in one 256-column
+// TMEM accumulator, and each layer's epilogue (bias, ReLU, BF16) writes the next layer's
+// operand straight back to shared memory.  The weights come from a copy kept in exactly
+// the shared-memory image (per layer, K/64 chunks of N x 64 core matrices), so a layer's
+// weights arrive with a few bulk copies (cp.async.bulk) on an mbarrier: W1 into the
+// activation buffer (dead until layer 1's epilogue), W2..W4 into a 128 KB weight buffer,
+// each as soon as the previous layer's MMAs have finished reading it.  CTAs are persistent
+// over the tiles.  Shared memory: 16 KB input + 64 KB activations + 128 KB weights.
 
-constexpr int kFusedThreads = 256;     // 8 warps: warp w reads TMEM lanes 32 (w % 4) .. +31
-constexpr int kColGroups = kFusedThreads / 128;   // ... and a half of the columns, w / 4
+constexpr int kFusedThreads = 512;     // 16 warps: warp w reads TMEM lanes 32 (w % 4) .. +31
+constexpr int kColGroups = kFusedThreads / 128;   // ... and a quarter of the columns, w / 4
 constexpr unsigned kWtBytes1 = (unsigned)kHid * kInPad * 2;   // W1: 32 KB
 constexpr unsigned kWtBytesH = (unsigned)kHid * kHid * 2;     // W2, W3: 128 KB each
 constexpr unsigned kWtBytes4 = (unsigned)kOut * kHid * 2;     // W4: 64 KB
 constexpr unsigned kWtOff1 = 0, kWtOff2 = kWtBytes1, kWtOff3 = kWtOff2 + kWtBytesH, kWtOff4 = kWtOff3 + kWtBytesH;
 constexpr unsigned kWtTotal = kWtOff4 + kWtBytes4;
+constexpr int kSmX = kTM * kInPad * 2;                        // 16 KB
 constexpr int kSmAct = kTM * kHid * 2;                        // 64 KB
-constexpr unsigned kUnitBytes = 16384;                        // 128 rows x 64 K BF16
-constexpr int kRing = 3;
-constexpr int kUnitsPerTile = 22;                             // 2 + 8 + 8 + 4
-constexpr int kFusedSmem = kSmAct + kRing * (int)kUnitBytes + 128;
+constexpr int kFusedSmem = kSmX + kSmAct + (int)kWtBytesH + 128;
 
 // Byte offset of element (r, k) of an R-row K-major operand stored as K/64 chunks of
 // R x 64 in core-matrix layout (chunk c at c * R * 128 bytes).
@@ -502,40 +498,43 @@ __device__ __forceinline__ void layer_mma(unsigned tmem, const unsigned char *a,
     }
 }
 
-// Unit u of a tile: layer l, K chunk c, weight-row half h, and its offset in the image.
-__device__ __forceinline__ void unit_of(int u, int &l, int &c, int &h)
+// Hidden-layer epilogue of accumulator row r (this thread's TMEM lane), columns
+// [c0, c1): + bias, ReLU, BF16 (round to nearest even), into the activation image.
+__device__ __forceinline__ void epi_hidden(unsigned trow, const float *bias, unsigned char *act, int r, int c0,
+                                           int c1)
 {
-    if (u < 2) {
-        l = 0, c = 0, h = u;
-    } else if (u < 10) {
-        l = 1, c = (u - 2) >> 1, h = (u - 2) & 1;
-    } else if (u < 18) {
-        l = 2, c = (u - 10) >> 1, h = (u - 10) & 1;
-    } else {
-        l = 3, c = u - 18, h = 0;
+    for (int nc = c0; nc < c1; nc += 16) {
+        float v[16];
+        tc_ld16(trow + (unsigned)nc, v);
+        unsigned w[8];
+#pragma unroll
+        for (int j = 0; j < 8; j++) {
+            const float a = fmaxf(v[2 * j] + bias[nc + 2 * j], 0.0f);
+            const float b = fmaxf(v[2 * j + 1] + bias[nc + 2 * j + 1], 0.0f);
+            const __nv_bfloat162 h = __floats2bfloat162_rn(a, b);
+            w[j] = *reinterpret_cast<const unsigned *>(&h);
+        }
+        *reinterpret_cast<uint4 *>(act + cm_off_k(kTM, r, nc)) = make_uint4(w[0], w[1], w[2], w[3]);
+        *reinterpret_cast<uint4 *>(act + cm_off_k(kTM, r, nc + 8)) = make_uint4(w[4], w[5], w[6], w[7]);
     }
 }
 
-__device__ __forceinline__ unsigned unit_src(int u)
-{
-    int l, c, h;
-    unit_of(u, l, c, h);
-    const unsigned base = l == 0 ? kWtOff1 : l == 1 ? kWtOff2 : l == 2 ? kWtOff3 : kWtOff4;
-    const unsigned N = l == 3 ? kOut : kHid;
-    return base + (unsigned)c * N * 128u + (unsigned)h * kUnitBytes;
-}
-
-__global__ void __launch_bounds__(kFusedThreads, 2) mlp_fused_fwd_kernel(const FusedArgs f)
+__global__ void __launch_bounds__(kFusedThreads, 1) mlp_fused_fwd_kernel(const FusedArgs f)
 {
     extern __shared__ __align__(128) unsigned char fsm[];
     unsigned char *base = fsm + ((128u - (su32(fsm) & 127u)) & 127u);
-    unsigned char *sAct = base, *ring = base + kSmAct;
-    __shared__ __align__(8) unsigned long long full[kRing], empty[kRing], bar_m;
+    unsigned char *sX = base, *sAct = base + kSmX, *sW = base + kSmX + kSmAct;
+    __shared__ __align__(8) unsigned long long bar_a, bar_w, bar_m;   // W1 image, weight buffer, MMAs
     __shared__ unsigned tmem_base;
+    __shared__ float s_bias[3 * kHid + kOut];                          // b1 | b2 | b3 | b4
     const int tid = threadIdx.x, warp = tid >> 5;
+    for (int i = tid; i < kHid; i += kFusedThreads) {
+        s_bias[i] = f.b1[i];
+        s_bias[kHid + i] = f.b2[i];
+        s_bias[2 * kHid + i] = f.b3[i];
+        if (i < kOut) s_bias[3 * kHid + i] = f.b4[i];
+    }
     const int ntiles = (f.batch + kTM - 1) / kTM;
-    const int my_tiles = (int)blockIdx.x < ntiles ? (ntiles - 1 - (int)blockIdx.x) / (int)gridDim.x + 1 : 0;
-    const int G = my_tiles * kUnitsPerTile;                      // weight units this CTA consumes
     if (warp == 0) {
         asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(su32(&tmem_base)),
                      "r"(kHid)
@@ -543,14 +542,10 @@ __global__ void __launch_bounds__(kFusedThreads, 2) mlp_fused_fwd_kernel(const F
         asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
     }
     if (tid == 0) {
-        for (int k = 0; k < kRing; k++) {
-            mbar_init1(&full[k]);
-            mbar_init1(&empty[k]);
-        }
+        mbar_init1(&bar_a);
+        mbar_init1(&bar_w);
         mbar_init1(&bar_m);
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
-        // the first two units
-        for (int g = 0; g < 2 && g < G; g++) load_image(ring + g * kUnitBytes, f.wt + unit_src(g), kUnitBytes, &full[g]);
     }
     asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
     __syncthreads();
@@ -559,14 +554,21 @@ __global__ void __launch_bounds__(kFusedThreads, 2) mlp_fused_fwd_kernel(const F
     const int quarter = warp & 3, cgroup = warp >> 2;
     const int row = quarter * 32 + (tid & 31);              // this thread's accumulator row
     const unsigned trow = tmem + ((unsigned)(quarter * 32) << 16);
-    int loaded = G < 2 ? G : 2;                             // units whose copy was issued (thread 0)
-    unsigned pm = 0;
+    unsigned pa = 0, pw = 0, pm = 0;          // phases of the three barriers
+    int a_out = 0, w_out = 0, m_out = 0;      // completions issued but not yet waited for
     bool ok = true;
-    int g = 0;                                              // this CTA's unit counter
-    const float *bias[3] = {f.b1, f.b2, f.b3};
+    if (tid == 0 && (int)blockIdx.x < ntiles) {
+        load_image(sAct, f.wt + kWtOff1, kWtBytes1, &bar_a);
+        load_image(sW, f.wt + kWtOff2, kWtBytesH, &bar_w);
+    }
+    if ((int)blockIdx.x < ntiles) a_out = w_out = 1;
+    const unsigned char *wnext[3] = {f.wt + kWtOff3, f.wt + kWtOff4, nullptr};
+    const unsigned wbytes[3] = {kWtBytesH, kWtBytes4, 0};
+    const float *bias[3] = {s_bias, s_bias + kHid, s_bias + 2 * kHid};
+    const float *b4 = s_bias + 3 * kHid;
     for (int t = blockIdx.x; t < ntiles && ok; t += gridDim.x) {
         const int m0 = t * kTM;
-        // ---- input tile into the first 16 KB of the activation buffer (BF16, K padded)
+        // ---- input tile to BF16, K padded to 64: one (row, 8-column group) per thread and pass
         for (int u = tid; u < kTM * (kInPad / 8); u += kFusedThreads) {
             const int r = u % kTM, kg = u / kTM, m = m0 + r;
             float xv[8] = {0.0f, 0.0f, 0.0f, 0.0f, 0.0f, 0.0f, 0.0f, 0.0f};
@@ -588,88 +590,72 @@ __global__ void __launch_bounds__(kFusedThreads, 2) mlp_fused_fwd_kernel(const F
             unsigned w[4];
 #pragma unroll
             for (int j = 0; j < 4; j++) {
-                const __nv_bfloat162 hh = __floats2bfloat162_rn(xv[2 * j], xv[2 * j + 1]);
-                w[j] = *reinterpret_cast<const unsigned *>(&hh);
+                const __nv_bfloat162 h = __floats2bfloat162_rn(xv[2 * j], xv[2 * j + 1]);
+                w[j] = *reinterpret_cast<const unsigned *>(&h);
             }
-            *reinterpret_cast<uint4 *>(sAct + cm_off(r, kg * 8)) = make_uint4(w[0], w[1], w[2], w[3]);
+            *reinterpret_cast<uint4 *>(sX + cm_off(r, kg * 8)) = make_uint4(w[0], w[1], w[2], w[3]);
         }
         asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
         __syncthreads();
+        // ---- layers 1..4
         for (int l = 0; l < 4; l++) {
-            const int u_end = l == 0 ? 2 : l == 1 ? 10 : l == 2 ? 18 : 22;
             if (tid == 0) {
-                asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-                for (int u = l == 0 ? 0 : l == 1 ? 2 : l == 2 ? 10 : 18; u < u_end && ok; u++, g++) {
-                    const int slot = g % kRing;
-                    ok = mbar_wait_bounded1(&full[slot], (unsigned)((g / kRing) & 1));
-                    if (!ok) break;
-                    int ll, c, h;
-                    unit_of(u, ll, c, h);
-                    const unsigned char *A = sAct + c * kTM * 128;
-                    const unsigned char *B = ring + slot * kUnitBytes;
-                    const unsigned idesc = instr_desc(128);
-#pragma unroll
-                    for (int k = 0; k < 4; k++) {
-                        const unsigned long long da = smem_desc(su32(A) + (unsigned)(k * 256), 128, 1024);
-                        const unsigned long long db = smem_desc(su32(B) + (unsigned)(k * 256), 128, 1024);
-                        tc_mma(tmem + (unsigned)(h * 128), da, db, idesc, (c > 0 || k > 0) ? 1u : 0u);
-                    }
-                    tc_commit(&empty[slot]);
-                    // refill: unit g+2 goes to the slot unit g-1 used, once its products are done
-                    if (loaded < G && loaded == g + 2) {
-                        const int ps = loaded % kRing;
-                        if (loaded >= kRing) {
-                            ok = mbar_wait_bounded1(&empty[ps], (unsigned)(((loaded - kRing) / kRing) & 1));
-                            if (!ok) break;
-                        }
-                        load_image(ring + ps * kUnitBytes, f.wt + unit_src(loaded % kUnitsPerTile), kUnitBytes,
-                                   &full[ps]);
-                        loaded++;
-                    }
+                if (l == 0) {
+                    ok = ok && mbar_wait_bounded1(&bar_a, pa);
+                } else {
+                    ok = ok && mbar_wait_bounded1(&bar_w, pw);
                 }
-                if (ok) tc_commit(&bar_m);
+                if (ok) {
+                    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+                    if (l == 0) layer_mma(tmem, sX, sAct, kHid, kInPad / 16);
+                    else layer_mma(tmem, sAct, sW, l == 3 ? kOut : kHid, kHid / 16);
+                    tc_commit(&bar_m);
+                    m_out = 1;
+                }
             }
-            if (__syncthreads_or(!ok)) {
-                ok = false;
-                break;
+            if (l == 0) {
+                pa ^= 1u;
+                a_out = 0;
+            } else {
+                pw ^= 1u;
+                w_out = 0;
             }
+            ok = !__syncthreads_or(!ok);
+            if (!ok) break;
             ok = mbar_wait_bounded1(&bar_m, pm);
             pm ^= 1u;
+            m_out = 0;
             asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
             if (__syncthreads_or(!ok)) {
                 ok = false;
                 break;
             }
-            if (l < 3) {
-                const int c0 = cgroup * (kHid / kColGroups), c1 = c0 + kHid / kColGroups;
-                for (int nc = c0; nc < c1; nc += 16) {
-                    float v[16];
-                    tc_ld16(trow + (unsigned)nc, v);
-                    unsigned w[8];
-#pragma unroll
-                    for (int j = 0; j < 8; j++) {
-                        const float x0 = fmaxf(v[2 * j] + __ldg(bias[l] + nc + 2 * j), 0.0f);
-                        const float x1 = fmaxf(v[2 * j + 1] + __ldg(bias[l] + nc + 2 * j + 1), 0.0f);
-                        const __nv_bfloat162 hh = __floats2bfloat162_rn(x0, x1);
-                        w[j] = *reinterpret_cast<const unsigned *>(&hh);
-                    }
-                    *reinterpret_cast<uint4 *>(sAct + cm_off_k(kTM, row, nc)) = make_uint4(w[0], w[1], w[2], w[3]);
-                    *reinterpret_cast<uint4 *>(sAct + cm_off_k(kTM, row, nc + 8)) = make_uint4(w[4], w[5], w[6], w[7]);
+            // the MMAs are done with their operands: refill the freed buffers
+            if (l >= 1 && l <= 2) {
+                if (tid == 0) load_image(sW, wnext[l - 1], wbytes[l - 1], &bar_w);
+                w_out = 1;
+            }
+            if (l == 3 && t + (int)gridDim.x < ntiles) {
+                if (tid == 0) {
+                    load_image(sAct, f.wt + kWtOff1, kWtBytes1, &bar_a);
+                    load_image(sW, f.wt + kWtOff2, kWtBytesH, &bar_w);
                 }
+                a_out = w_out = 1;
+            }
+            if (l < 3) {
+                epi_hidden(trow, bias[l], sAct, row, cgroup * (kHid / kColGroups), (cgroup + 1) * (kHid / kColGroups));
                 asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
             } else {
                 const int m = m0 + row;
-                const int c0 = cgroup * (kOut / kColGroups), c1 = c0 + kOut / kColGroups;
-                for (int nc = c0; nc < c1; nc += 16) {
+                for (int nc = cgroup * (kOut / kColGroups); nc < (cgroup + 1) * (kOut / kColGroups); nc += 16) {
                     float v[16];
                     tc_ld16(trow + (unsigned)nc, v);
                     if (m < f.batch) {
                         float4 *yr = reinterpret_cast<float4 *>(f.y + (size_t)m * kOut + nc);
 #pragma unroll
                         for (int q = 0; q < 4; q++)
-                            yr[q] = make_float4(v[4 * q] + __ldg(f.b4 + nc + 4 * q), v[4 * q + 1] + __ldg(f.b4 + nc + 4 * q + 1),
-                                                v[4 * q + 2] + __ldg(f.b4 + nc + 4 * q + 2),
-                                                v[4 * q + 3] + __ldg(f.b4 + nc + 4 * q + 3));
+                            yr[q] = make_float4(v[4 * q] + b4[nc + 4 * q], v[4 * q + 1] + b4[nc + 4 * q + 1],
+                                                v[4 * q + 2] + b4[nc + 4 * q + 2], v[4 * q + 3] + b4[nc + 4 * q + 3]);
                     }
                 }
             }
@@ -677,15 +663,16 @@ __global__ void __launch_bounds__(kFusedThreads, 2) mlp_fused_fwd_kernel(const F
             __syncthreads();
         }
     }
-    // On the normal path every issued copy was waited for and the last layer's commit covered
-    // every product.  After a wait ran out: flag it, let the copies not yet consumed land,
-    // and commit once more to wait for every product issued (all bounded), before the TMEM
-    // is released.
-    if (!ok && tid == 0) {
-        if (f.err) atomicOr(f.err, 1);
-        for (int q = g; q < loaded; q++) mbar_wait_bounded1(&full[q % kRing], (unsigned)((q / kRing) & 1));
-        tc_commit(&bar_m);
-        mbar_wait_bounded1(&bar_m, pm);
+    if (!ok) {
+        // a wait ran out: flag it, and let the copies and MMAs still in flight land
+        // (bounded) before the tensor memory is released
+        if (tid == 0) {
+            if (f.err) atomicOr(f.err, 1);
+            if (a_out) mbar_wait_bounded1(&bar_a, pa);
+            if (w_out) mbar_wait_bounded1(&bar_w, pw);
+            if (m_out) mbar_wait_bounded1(&bar_m, pm);
+        }
+        __syncthreads();
     }
     asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
     __syncthreads();
@@ -873,7 +860,7 @@ cudaError_t fused_forward(asx_mlp *p, int B, const float *x, float *y)
     }
     FusedArgs f{x, y, p->wt, p->w + oB1, p->w + oB2, p->w + oB3, p->w + oB4, B, p->err};
     const int ntiles = (B + kTM - 1) / kTM;
-    const int grid = ntiles < 2 * p->n_sm ? ntiles : 2 * p->n_sm;     // two CTAs per SM
+    const int grid = ntiles < p->n_sm ? ntiles : p->n_sm;
     mlp_fused_fwd_kernel<<<grid, kFusedThreads, kFusedSmem, p->stream>>>(f);
     return cudaGetLastError();
 }
@@ -955,8 +942,6 @@ asx_status asx_mlp_create(int device, void *cuda_stream, int max_batch, asx_mlp 
     if (e == cudaSuccess) e = cudaDeviceGetAttribute(&p->n_sm, cudaDevAttrMultiProcessorCount, device);
     if (e == cudaSuccess)
         e = cudaFuncSetAttribute(mlp_fused_fwd_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, kFusedSmem);
-    if (e == cudaSuccess)   // two CTAs per SM need the largest shared-memory carveout
-        e = cudaFuncSetAttribute(mlp_fused_fwd_kernel, cudaFuncAttributePreferredSharedMemoryCarveout, 100);
     if (e == cudaSuccess) e = cudaStreamSynchronize(p->stream);
     if (e != cudaSuccess) {
         asx_mlp_destroy(p);

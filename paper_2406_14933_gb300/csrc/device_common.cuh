@@ -216,14 +216,16 @@ __device__ __forceinline__ void edge_core(const Cell &A, const Cell &B, float kl
     if (D == 0) vn2 = s1;
     else if (D == 1) vn2 = __fmaf_rn(kS32, s2, __fmul_rn(0.5f, s1));
     else vn2 = __fmaf_rn(kS32, s2, __fmul_rn(-0.5f, s1));
-    const float mu = vn2 > 0.0f ? A.m : B.m;         // upwind theta h (any side if v_n = 0)
+    // the upwind theta h depends on v_n alone (any side if v_n = 0), so the mass
+    // increment does not wait for the surface difference
+    const float mu = vn2 > 0.0f ? A.m : B.m;
     const float G = __fmul_rn(mu, vn2);
     q = __fmul_rn(kl2, G);
     const float gl = __fmul_rn(l4, G);
     fa1 = __fmul_rn(gl, s1);
     fa2 = __fmul_rn(gl, s2);
     const float dw = __fadd_rn(__fsub_rn(B.z, A.z), __fsub_rn(B.h, A.h));   // (w_B - w_A) / g
-    const float hat = vn2 != 0.0f ? mu : (dw < 0.0f ? A.m : B.m);
+    const float hat = vn2 != 0.0f ? mu : (dw < 0.0f ? A.m : B.m);           // tie: higher surface
     dh = __fmul_rn(dw, hat);
 }
 

@@ -1,10 +1,14 @@
 // step_strip.cu -- the main step kernel: one warp marches down a 128-column tile fed by
-// TMA, four cells per lane.
+// TMA, four cells per lane, two at a time in the packed float32 pairs of sm_100+.
 //
 // Same arithmetic as the gather kernel (Sec. 2.2, Eq. fvm_2D_eq_frac.07 in the form of
 // Appendix A), organised for GB300:
-//   * a CTA is one warp and owns kSW = 128 columns x H rows; lane L owns the four
-//     adjacent cells at columns c0 + 4L .. c0 + 4L + 3;
+//   * a CTA is one warp and owns kSW = 128 columns x H rows; lane L owns the cells at
+//     columns c0 + 2L + e (left half of the tile) and c0 + 64 + 2L + e (right half),
+//     e = 0, 1.  The two cells with the same e lie 64 columns apart in the same row and
+//     see the same stencil: they form a float2 pair that the edge and cell code process
+//     together with the f32x2 instructions (add / sub / mul / fma .rn.f32x2: one issue
+//     slot for two float32 operations, each component rounded as the scalar operation);
 //   * rows r0-1 .. r0+H of every field (one halo row above and below, halo columns left
 //     and right) stream into a shared-memory ring of 2-row chunks through TMA tensor
 //     loads (cp.async.bulk.tensor.2d) that complete on mbarriers; lane 0 refills a chunk
@@ -13,7 +17,7 @@
 //     edges of row r are evaluated by the lane that owns their lower cell; a lane also
 //     evaluates the one horizontal and one diagonal edge it shares with each neighbouring
 //     lane (the same canonical edge, so the same bits), which replaces every exchange of
-//     edge terms; every lane reads the cells beside its four (in its own row and the
+//     edge terms; every lane reads the cells beside its own (in its own row and the
 //     next, including the halo columns at the tile ends) from the ring: the same values,
 //     hence the same bits, as the neighbouring lane's own cells;
 //   * contributions to row r+1 stay in registers until that row is finished; no block
@@ -23,8 +27,8 @@
 //     sides (the frame) are processed in the same launch by frame CTAs that gather each
 //     cell's six neighbours (the same per-cell code as the gather kernel).
 // Both cells of an edge accumulate the mass increment of the same canonical edge
-// function, so opposite increments are bit-identical and the water budget closes to
-// float64 rounding.
+// function, bit for bit the increment the scalar code of the frame computes, so opposite
+// increments are identical and the water budget closes to float64 rounding.
 #include <cuda.h>
 
 #include <type_traits>
@@ -126,61 +130,240 @@ __device__ __forceinline__ bool mbar_wait_bounded(unsigned long long *bar, unsig
     return false;
 }
 
-// ----------------------------------------------------------------- cell helpers
+// ----------------------------------------------------------------- packed pairs
 
-struct Acc {
-    float hi, lo, m1, m2;    // compensated mass, momentum sums J + S
+// The packed operations are written as PTX with an explicit rounding mode: like the
+// scalar __fadd_rn / __fmul_rn, they are then never contracted into a fused multiply-add,
+// which the error-free two-sums below depend on.
+__device__ __forceinline__ float2 dup2(float x) { return make_float2(x, x); }
+
+__device__ __forceinline__ float2 add2(float2 a, float2 b)
+{
+    float2 d;
+    asm("{\n\t.reg .b64 ra, rb, rd;\n\tmov.b64 ra, {%2, %3};\n\tmov.b64 rb, {%4, %5};\n\t"
+        "add.rn.f32x2 rd, ra, rb;\n\tmov.b64 {%0, %1}, rd;\n\t}"
+        : "=f"(d.x), "=f"(d.y)
+        : "f"(a.x), "f"(a.y), "f"(b.x), "f"(b.y));
+    return d;
+}
+
+__device__ __forceinline__ float2 sub2(float2 a, float2 b)
+{
+    float2 d;
+    asm("{\n\t.reg .b64 ra, rb, rd;\n\tmov.b64 ra, {%2, %3};\n\tmov.b64 rb, {%4, %5};\n\t"
+        "sub.rn.f32x2 rd, ra, rb;\n\tmov.b64 {%0, %1}, rd;\n\t}"
+        : "=f"(d.x), "=f"(d.y)
+        : "f"(a.x), "f"(a.y), "f"(b.x), "f"(b.y));
+    return d;
+}
+
+__device__ __forceinline__ float2 mul2(float2 a, float2 b)
+{
+    float2 d;
+    asm("{\n\t.reg .b64 ra, rb, rd;\n\tmov.b64 ra, {%2, %3};\n\tmov.b64 rb, {%4, %5};\n\t"
+        "mul.rn.f32x2 rd, ra, rb;\n\tmov.b64 {%0, %1}, rd;\n\t}"
+        : "=f"(d.x), "=f"(d.y)
+        : "f"(a.x), "f"(a.y), "f"(b.x), "f"(b.y));
+    return d;
+}
+
+__device__ __forceinline__ float2 fma2(float2 a, float2 b, float2 c)
+{
+    float2 d;
+    asm("{\n\t.reg .b64 ra, rb, rc, rd;\n\tmov.b64 ra, {%2, %3};\n\tmov.b64 rb, {%4, %5};\n\t"
+        "mov.b64 rc, {%6, %7};\n\tfma.rn.f32x2 rd, ra, rb, rc;\n\tmov.b64 {%0, %1}, rd;\n\t}"
+        : "=f"(d.x), "=f"(d.y)
+        : "f"(a.x), "f"(a.y), "f"(b.x), "f"(b.y), "f"(c.x), "f"(c.y));
+    return d;
+}
+
+// two_sum on both components
+__device__ __forceinline__ void two_sum2(float2 a, float2 b, float2 &s, float2 &e)
+{
+    s = add2(a, b);
+    const float2 bb = sub2(s, a);
+    e = add2(sub2(a, sub2(s, bb)), sub2(b, bb));
+}
+
+// (hi, lo) += x on both components, as acc_add
+__device__ __forceinline__ void acc_add2(float2 &hi, float2 &lo, float2 x)
+{
+    float2 s, e;
+    two_sum2(hi, x, s, e);
+    hi = s;
+    lo = add2(lo, e);
+}
+
+// (hi, lo) += -x with the bits of acc_add(hi, lo, -x): there b - bb = -x - bb rounds
+// to -(x + bb)
+__device__ __forceinline__ void acc_sub2(float2 &hi, float2 &lo, float2 x)
+{
+    const float2 s = sub2(hi, x);
+    const float2 bb = sub2(s, hi);
+    const float2 e = sub2(sub2(hi, sub2(s, bb)), add2(x, bb));
+    hi = s;
+    lo = add2(lo, e);
+}
+
+__device__ __forceinline__ float &comp(float2 &v, int s) { return s ? v.y : v.x; }
+__device__ __forceinline__ float comp(const float2 &v, int s) { return s ? v.y : v.x; }
+
+struct PCell {
+    float2 m, v1, v2, z, h;
 };
 
-// Edge (X lower, Y upper) in direction D; adds its terms to ax if ux and to ay if uy
-// (a side not used belongs to another lane or is not updated by this tile).
-// The pressure term p = c dh enters each momentum sum through one fused multiply-add.
-// EXT: the optional terms are compiled in; with a.visc the artificial viscosity adds
-// t (v_Y - v_X) to X and t (v_X - v_Y) to Y.
-template <int D, bool EXT>
-__device__ __forceinline__ void edge(const StepArgs &a, const Cell &X, const Cell &Y, float kl2,
-                                     Acc &ax, bool ux, Acc &ay, bool uy)
+struct PAcc {
+    float2 hi, lo, m1, m2;
+};
+
+__device__ __forceinline__ Cell half_cell(const PCell &P, int s)
 {
-    float q, f1, f2, dh;
-    edge_core<D>(X, Y, kl2, 0.25f * a.l, q, f1, f2, dh);
-    const float c1 = a.cpe[D][0], c2 = a.cpe[D][1];
+    return Cell{comp(P.m, s), comp(P.v1, s), comp(P.v2, s), comp(P.z, s), comp(P.h, s)};
+}
+
+// Edge (X lower, Y upper) in direction D for both halves of the pairs, the terms of
+// edge_core component by component; adds them to ax if ux and to ay if uy (a side not
+// used belongs to another lane or is not updated by this tile).  The pressure term c dh
+// enters each momentum sum through one fused multiply-add; with EXT and a.visc the
+// artificial viscosity adds t (v_Y - v_X) to X and t (v_X - v_Y) to Y.
+template <int D, bool EXT>
+__device__ __forceinline__ void edge(const StepArgs &a, const PCell &X, const PCell &Y, float2 kl2, float2 l4,
+                                      PAcc &ax, bool ux, PAcc &ay, bool uy)
+{
+    const float2 s1 = add2(X.v1, Y.v1), s2 = add2(X.v2, Y.v2);
+    float2 vn2;
+    if (D == 0) vn2 = s1;
+    else if (D == 1) vn2 = fma2(dup2(kS32), s2, mul2(dup2(0.5f), s1));
+    else vn2 = fma2(dup2(kS32), s2, mul2(dup2(-0.5f), s1));
+    const float2 dw = add2(sub2(Y.z, X.z), sub2(Y.h, X.h));
+    // the upwind side is the sign of v_n, or at v_n = 0 that of -dw
+    const float kx = vn2.x != 0.0f ? vn2.x : -dw.x, ky = vn2.y != 0.0f ? vn2.y : -dw.y;
+    float2 mu;
+    mu.x = kx > 0.0f ? X.m.x : Y.m.x;
+    mu.y = ky > 0.0f ? X.m.y : Y.m.y;
+    const float2 G = mul2(mu, vn2);
+    // q = kl2 G as fma(kl2, G, +0): the same bits as the product (but for the sign of a
+    // zero, which moves no mass), and an instruction the code generator cannot fuse into
+    // the two-sums that consume q, as it was seen to do with a plain packed multiply
+    const float2 q = fma2(kl2, G, dup2(0.0f));
+    const float2 gl = mul2(l4, G);
+    const float2 f1 = mul2(gl, s1), f2 = mul2(gl, s2);
+    const float2 dh = mul2(dw, mu);
+    // an E edge's normal has no second component: its pressure term leaves m2 as it is
+    const float2 c1 = dup2(a.cpe[D][0]), c2 = dup2(a.cpe[D][1]);
     if (ux) {
-        acc_add(ax.hi, ax.lo, -q);
-        ax.m1 = __fsub_rn(__fmaf_rn(c1, dh, ax.m1), f1);
-        ax.m2 = __fsub_rn(__fmaf_rn(c2, dh, ax.m2), f2);
+        acc_sub2(ax.hi, ax.lo, q);
+        ax.m1 = sub2(fma2(c1, dh, ax.m1), f1);
+        ax.m2 = sub2(D == 0 ? ax.m2 : fma2(c2, dh, ax.m2), f2);
     }
     if (uy) {
-        acc_add(ay.hi, ay.lo, q);
-        ay.m1 = __fadd_rn(__fmaf_rn(c1, dh, ay.m1), f1);
-        ay.m2 = __fadd_rn(__fmaf_rn(c2, dh, ay.m2), f2);
+        acc_add2(ay.hi, ay.lo, q);
+        ay.m1 = add2(fma2(c1, dh, ay.m1), f1);
+        ay.m2 = add2(D == 0 ? ay.m2 : fma2(c2, dh, ay.m2), f2);
     }
     if (EXT && a.visc) {
-        const float t = visc_coef(X, Y, a.l, a.g);
-        const float d1 = __fsub_rn(Y.v1, X.v1), d2 = __fsub_rn(Y.v2, X.v2);
-        if (ux) {
-            ax.m1 = __fmaf_rn(t, d1, ax.m1);
-            ax.m2 = __fmaf_rn(t, d2, ax.m2);
-        }
-        if (uy) {
-            ay.m1 = __fmaf_rn(-t, d1, ay.m1);
-            ay.m2 = __fmaf_rn(-t, d2, ay.m2);
+#pragma unroll
+        for (int s = 0; s < 2; s++) {
+            const Cell Xs = half_cell(X, s), Ys = half_cell(Y, s);
+            const float t = visc_coef(Xs, Ys, a.l, a.g);
+            const float d1 = __fsub_rn(Ys.v1, Xs.v1), d2 = __fsub_rn(Ys.v2, Xs.v2);
+            if (ux) {
+                comp(ax.m1, s) = __fmaf_rn(t, d1, comp(ax.m1, s));
+                comp(ax.m2, s) = __fmaf_rn(t, d2, comp(ax.m2, s));
+            }
+            if (uy) {
+                comp(ay.m1, s) = __fmaf_rn(-t, d1, comp(ay.m1, s));
+                comp(ay.m2, s) = __fmaf_rn(-t, d2, comp(ay.m2, s));
+            }
         }
     }
 }
 
-// Per-lane state of one row: four cells, their porosity (theta, or in class mode the
-// class id's bits) and the accumulators of their edge terms.  The halo cells at both ends
-// of the tile row are read from the ring when needed.
-struct Row {
-    Cell X[4];
-    float th[4];
-    Acc A[4];
+// cell_update for both halves of a pair, component by component the same operations
+// (the rare branches, a clamp or a tiny denominator, taken per component).
+struct CellNew2 {
+    float2 hi, lo, v1, v2;
+    unsigned cb0, cb1;
+};
+
+__device__ __forceinline__ void tiny_den(float den, float g1, float g2, float &w1, float &w2)
+{
+    if (den > 0.0f) {
+        // tiny or subnormal denominator: scale it (and the numerators) by 2^64 first
+        const float inv2 = __fmul_rn(2.0f, fast_rcp(__fmul_rn(den, 0x1p64f)));
+        w1 = __fmul_rn(__fmul_rn(g1, 0x1p64f), inv2);
+        w2 = __fmul_rn(__fmul_rn(g2, 0x1p64f), inv2);
+    } else {
+        w1 = 0.0f;
+        w2 = 0.0f;
+    }
+}
+
+template <bool EXT>
+__device__ __forceinline__ CellNew2 cell_update_pair(float2 shi, float2 slo, float2 M1, float2 M2, float2 m_old,
+                                                 float2 v1_old, float2 v2_old, float2 rth, float2 ka, float2 kb,
+                                                 float kappa, float qr, float dtf, float g, float dtau,
+                                                 float h_dry, FF &clx, FF &cly)
+{
+    CellNew2 o;
+    acc_add2(shi, slo, dup2(qr));
+    float2 hi, lo;
+    two_sum2(shi, slo, hi, lo);
+    if (hi.x < 0.0f || (hi.x == 0.0f && lo.x < 0.0f)) {
+        clx.add(-hi.x);
+        clx.add(-lo.x);
+        hi.x = 0.0f;
+        lo.x = 0.0f;
+    }
+    if (hi.y < 0.0f || (hi.y == 0.0f && lo.y < 0.0f)) {
+        cly.add(-hi.y);
+        cly.add(-lo.y);
+        hi.y = 0.0f;
+        lo.y = 0.0f;
+    }
+    const float2 g1 = fma2(dup2(kappa), M1, mul2(m_old, v1_old));
+    const float2 g2 = fma2(dup2(kappa), M2, mul2(m_old, v2_old));
+    const float2 h = mul2(hi, rth);
+    const float2 beta = mul2(dup2(dtf), fma2(ka, h, kb));
+    const float2 nq = fma2(g1, g1, mul2(g2, g2));
+    float2 ng;
+    ng.x = nq.x >= 1.0e-36f ? fast_sqrt(nq.x) : norm2(g1.x, g2.x);
+    ng.y = nq.y >= 1.0e-36f ? fast_sqrt(nq.y) : norm2(g1.y, g2.y);
+    float2 ap = hi;
+    if constexpr (EXT) ap = fma2(dup2(dtau), h, hi);
+    const float2 rad = fma2(ap, ap, mul2(mul2(dup2(4.0f), beta), ng));
+    const float2 den = add2(ap, make_float2(fast_sqrt(rad.x), fast_sqrt(rad.y)));
+    const float2 inv2 = mul2(dup2(2.0f), make_float2(fast_rcp(den.x), fast_rcp(den.y)));
+    float2 w1 = mul2(g1, inv2), w2 = mul2(g2, inv2);
+    if (!(den.x > 1.0e-30f)) tiny_den(den.x, g1.x, g2.x, w1.x, w2.x);
+    if (!(den.y > 1.0e-30f)) tiny_den(den.y, g1.y, g2.y, w1.y, w2.y);
+    if constexpr (EXT) {
+        if (h.x < h_dry) w1.x = w2.x = 0.0f;     // optional dry threshold (0: none)
+        if (h.y < h_dry) w1.y = w2.y = 0.0f;
+    }
+    o.hi = hi;
+    o.lo = lo;
+    o.v1 = w1;
+    o.v2 = w2;
+    const float2 sp = fma2(w1, w1, mul2(w2, w2));
+    const float2 gh = mul2(dup2(g), h);
+    const float2 c = add2(make_float2(fast_sqrt(sp.x), fast_sqrt(sp.y)), make_float2(fast_sqrt(gh.x), fast_sqrt(gh.y)));
+    o.cb0 = speed_bits(c.x);
+    o.cb1 = speed_bits(c.y);
+    return o;
+}
+
+struct PRow {
+    PCell X[2];
+    float2 th[2];     // porosity theta, or in class mode the class ids' bits
+    PAcc A[2];
 };
 
 // ----------------------------------------------------------------- the tile
 
 template <bool CLS, bool EXT>
 struct Tile {
+    static constexpr int kHalf = kSW / 2;
     const StepArgs &a;
     StripSmem<CLS> &S;
     const float (*cls)[kMaxClasses];   // shared copies of the class tables 1/theta, a, b
@@ -192,11 +375,11 @@ struct Tile {
     bool timed_out = false;
     int n_issued = 0;
 
-    int jown;          // first local row this tile writes
-    bool lane_own;     // this lane's four columns are written by this tile
+    int jown;            // first local row this tile writes
+    bool own_l, own_r;   // this lane's left / right columns are written by this tile
 
     __device__ __forceinline__ Tile(const StepArgs &a_, StripSmem<CLS> &S_, const float (*cls_)[kMaxClasses],
-                                    const StripMaps &m_, int c0_, int r0_, int own_c, int own_r)
+                                    const StripMaps &m_, int c0_, int r0_, int own_c, int own_r_)
         : a(a_), S(S_), cls(cls_), maps(m_)
     {
         const DevCtl *ctl = a.ctl;
@@ -210,12 +393,11 @@ struct Tile {
         c0 = c0_;
         r0 = r0_;
         Hn = a.tile_rows;
-        jown = 1 + (own_r - r0);
-        lane_own = c0 + 4 * lane >= own_c;
+        jown = 1 + (own_r_ - r0);
+        own_l = c0 + 2 * lane >= own_c;
+        own_r = c0 + kHalf + 2 * lane >= own_c;
         nchunks = (Hn + 2 + kRB - 1) / kRB;
     }
-
-    __device__ __forceinline__ int col(int e) const { return c0 + 4 * lane + e; }
 
     __device__ __forceinline__ void issue(int k)
     {
@@ -240,25 +422,12 @@ struct Tile {
         tma_load_2d(&ch.mlo.v[0][0], &maps.mlo[par], c0, y, bar);
     }
 
-    // Halo cell of ring row rr at float index x.
-    __device__ __forceinline__ Cell ring_cell(const Chunk<CLS> &ch, int rr, int x) const
+    // Waits for the chunk of local row jr when jr is its first row; returns the chunk.
+    __device__ __forceinline__ const Chunk<CLS> &arrive(int jr)
     {
-        Cell c;
-        c.m = ch.mhi.v[rr][x];
-        c.v1 = ch.v1.v[rr][x];
-        c.v2 = ch.v2.v[rr][x];
-        c.z = ch.z.v[rr][x];
-        float rt;
-        if constexpr (CLS) rt = cls[0][ch.th.v[rr][x - kXO + kXOC]];
-        else rt = fast_rcp(ch.th.v[rr][x]);
-        c.h = __fmul_rn(c.m, rt);
-        return c;
-    }
-
-    // The cell of local row jr at ring x index x (the row's chunk is still resident).
-    __device__ __forceinline__ Cell ring_at(int jr, int x) const
-    {
-        return ring_cell(S.ring[(jr / kRB) % kNC], jr % kRB, x);
+        const int k = jr / kRB;
+        if (jr % kRB == 0 && !mbar_wait_bounded(&S.bar[k % kNC], (unsigned)((k / kNC) & 1))) timed_out = true;
+        return S.ring[k % kNC];
     }
 
     // Local row jr is done (its edges and the ones to the row below are in): once every
@@ -275,130 +444,147 @@ struct Tile {
         }
     }
 
-    // Loads local row jr (global r0 - 1 + jr) into R.
-    __device__ __forceinline__ void load(int jr, Row &R)
+    // The pair of ring cells at float index x and x + 64 of local row jr (the row's
+    // chunk is still resident).
+    __device__ __forceinline__ PCell ring_pair(int jr, int x) const
     {
-        const int k = jr / kRB, rr = jr % kRB;
-        if (rr == 0 && !mbar_wait_bounded(&S.bar[k % kNC], (unsigned)((k / kNC) & 1))) timed_out = true;
-        const Chunk<CLS> &ch = S.ring[k % kNC];
-        const int x = kXO + 4 * lane;
-        const float4 m4 = *reinterpret_cast<const float4 *>(&ch.mhi.v[rr][x]);
-        const float4 u4 = *reinterpret_cast<const float4 *>(&ch.v1.v[rr][x]);
-        const float4 w4 = *reinterpret_cast<const float4 *>(&ch.v2.v[rr][x]);
-        const float4 z4 = *reinterpret_cast<const float4 *>(&ch.z.v[rr][x]);
-        const float4 l4 = *reinterpret_cast<const float4 *>(&ch.mlo.v[rr][4 * lane]);
-        const float mm[4] = {m4.x, m4.y, m4.z, m4.w}, uu[4] = {u4.x, u4.y, u4.z, u4.w};
-        const float ww[4] = {w4.x, w4.y, w4.z, w4.w}, zz[4] = {z4.x, z4.y, z4.z, z4.w};
-        const float ll[4] = {l4.x, l4.y, l4.z, l4.w};
+        const Chunk<CLS> &ch = S.ring[(jr / kRB) % kNC];
+        const int rr = jr % kRB;
+        PCell c;
+        c.m = make_float2(ch.mhi.v[rr][x], ch.mhi.v[rr][x + kHalf]);
+        c.v1 = make_float2(ch.v1.v[rr][x], ch.v1.v[rr][x + kHalf]);
+        c.v2 = make_float2(ch.v2.v[rr][x], ch.v2.v[rr][x + kHalf]);
+        c.z = make_float2(ch.z.v[rr][x], ch.z.v[rr][x + kHalf]);
+        float2 rt;
         if constexpr (CLS) {
-            const uchar4 c4 = *reinterpret_cast<const uchar4 *>(&ch.th.v[rr][kXOC + 4 * lane]);
-            const int cc[4] = {c4.x, c4.y, c4.z, c4.w};
-#pragma unroll
-            for (int e = 0; e < 4; e++) {
-                R.th[e] = __int_as_float(cc[e]);
-                R.X[e].h = __fmul_rn(mm[e], cls[0][cc[e]]);
-            }
+            rt = make_float2(cls[0][ch.th.v[rr][x - kXO + kXOC]], cls[0][ch.th.v[rr][x - kXO + kXOC + kHalf]]);
         } else {
-            const float4 t4 = *reinterpret_cast<const float4 *>(&ch.th.v[rr][x]);
-            const float tt[4] = {t4.x, t4.y, t4.z, t4.w};
-#pragma unroll
-            for (int e = 0; e < 4; e++) {
-                R.th[e] = tt[e];
-                R.X[e].h = __fmul_rn(mm[e], fast_rcp(tt[e]));
-            }
+            rt = make_float2(fast_rcp(ch.th.v[rr][x]), fast_rcp(ch.th.v[rr][x + kHalf]));
         }
+        c.h = mul2(c.m, rt);
+        return c;
+    }
+
+    // Loads local row jr (global r0 - 1 + jr) into R.
+    __device__ __forceinline__ void load(int jr, PRow &R)
+    {
+        const int rr = jr % kRB;
+        const Chunk<CLS> &ch = arrive(jr);
+        const int x = kXO + 2 * lane, xl = 2 * lane;
 #pragma unroll
-        for (int e = 0; e < 4; e++) {
-            R.X[e].m = mm[e];
-            R.X[e].v1 = uu[e];
-            R.X[e].v2 = ww[e];
-            R.X[e].z = zz[e];
-            R.A[e] = Acc{mm[e], ll[e], 0.0f, 0.0f};
+        for (int e = 0; e < 2; e++) {
+            PCell &P = R.X[e];
+            P.m = make_float2(ch.mhi.v[rr][x + e], ch.mhi.v[rr][x + e + kHalf]);
+            P.v1 = make_float2(ch.v1.v[rr][x + e], ch.v1.v[rr][x + e + kHalf]);
+            P.v2 = make_float2(ch.v2.v[rr][x + e], ch.v2.v[rr][x + e + kHalf]);
+            P.z = make_float2(ch.z.v[rr][x + e], ch.z.v[rr][x + e + kHalf]);
+            float2 rt;
+            if constexpr (CLS) {
+                const int il = ch.th.v[rr][kXOC + xl + e], ir = ch.th.v[rr][kXOC + xl + e + kHalf];
+                R.th[e] = make_float2(__int_as_float(il), __int_as_float(ir));
+                rt = make_float2(cls[0][il], cls[0][ir]);
+            } else {
+                const float tl = ch.th.v[rr][x + e], tr = ch.th.v[rr][x + e + kHalf];
+                R.th[e] = make_float2(tl, tr);
+                rt = make_float2(fast_rcp(tl), fast_rcp(tr));
+            }
+            P.h = mul2(P.m, rt);
+            R.A[e] = PAcc{P.m, make_float2(ch.mlo.v[rr][xl + e], ch.mlo.v[rr][xl + e + kHalf]), dup2(0.0f),
+                          dup2(0.0f)};
         }
     }
 
     // Edge terms between row j (C, global row r) and row j+1 (N), and the east edges of
-    // row r; ODD: parity of r.  Both rows always accumulate: a row this tile does not
-    // update (a halo row, or a row above an overlapping last row block) is never
-    // finished, so its sums are simply dropped.
+    // row r; ODD: parity of r.  Pair e = 0, 1 holds the columns c = c0 + 2L + e (and
+    // c + 64).  Both rows always accumulate: a row this tile does not update (a halo
+    // row, or a row above an overlapping last row block) is never finished, so its sums
+    // are simply dropped.
     template <int ODD>
-    __device__ __forceinline__ void edges(int j, Row &C, Row &N)
+    __device__ __forceinline__ void edges(int j, PRow &C, PRow &N)
     {
-        // the cells west and east of this lane's four, read from the ring (the same
-        // values, hence the same h, as the neighbouring lane's own cells)
-        const int xw = kXO + 4 * lane - 1, xe = kXO + 4 * lane + 4;
-        const Cell Wc = ring_at(j, xw);
-        const Cell Ec = ring_at(j, xe);
+        const float2 k2 = dup2(kl2), l4 = dup2(0.25f * a.l);
+        // the cells west and east of this lane's two, read from the ring (the same
+        // values, hence the same h, as the neighbouring lanes' own cells)
+        const int xw = kXO + 2 * lane - 1, xe = kXO + 2 * lane + 2;
+        const PCell Wc = ring_pair(j, xw), Ec = ring_pair(j, xe);
         // ---- east edges of row r (the west edge of c_0 is the west lane's, again)
-        edge<0, EXT>(a, Wc, C.X[0], kl2, C.A[0], false, C.A[0], true);
-#pragma unroll
-        for (int e = 0; e < 3; e++) edge<0, EXT>(a, C.X[e], C.X[e + 1], kl2, C.A[e], true, C.A[e + 1], true);
-        edge<0, EXT>(a, C.X[3], Ec, kl2, C.A[3], true, C.A[3], false);
+        edge<0, EXT>(a, Wc, C.X[0], k2, l4, C.A[0], false, C.A[0], true);
+        edge<0, EXT>(a, C.X[0], C.X[1], k2, l4, C.A[0], true, C.A[1], true);
+        edge<0, EXT>(a, C.X[1], Ec, k2, l4, C.A[1], true, C.A[1], false);
         if (ODD) {
             // odd r: NE(c) = (r+1, c+1), NW(c) = (r+1, c)
-            const Cell On = ring_at(j + 1, xe);                                   // (r+1, c_3 + 1)
-#pragma unroll
-            for (int e = 0; e < 4; e++) {
-                edge<2, EXT>(a, C.X[e], N.X[e], kl2, C.A[e], true, N.A[e], true);        // NW
-                if (e < 3) edge<1, EXT>(a, C.X[e], N.X[e + 1], kl2, C.A[e], true, N.A[e + 1], true);
-                else edge<1, EXT>(a, C.X[3], On, kl2, C.A[3], true, C.A[3], false);
-            }
+            const PCell On = ring_pair(j + 1, xe);                                // (r+1, c_1 + 1)
+            edge<2, EXT>(a, C.X[0], N.X[0], k2, l4, C.A[0], true, N.A[0], true);   // NW
+            edge<1, EXT>(a, C.X[0], N.X[1], k2, l4, C.A[0], true, N.A[1], true);   // NE
+            edge<2, EXT>(a, C.X[1], N.X[1], k2, l4, C.A[1], true, N.A[1], true);   // NW
+            edge<1, EXT>(a, C.X[1], On, k2, l4, C.A[1], true, C.A[1], false);      // NE
             // SW edge of (r+1, c_0): the NE edge of (r, c_0 - 1)
-            edge<1, EXT>(a, Wc, N.X[0], kl2, N.A[0], false, N.A[0], true);
+            edge<1, EXT>(a, Wc, N.X[0], k2, l4, N.A[0], false, N.A[0], true);
         } else {
             // even r: NE(c) = (r+1, c), NW(c) = (r+1, c-1)
-            const Cell On = ring_at(j + 1, xw);                                   // (r+1, c_0 - 1)
-#pragma unroll
-            for (int e = 0; e < 4; e++) {
-                edge<1, EXT>(a, C.X[e], N.X[e], kl2, C.A[e], true, N.A[e], true);        // NE
-                if (e >= 1) edge<2, EXT>(a, C.X[e], N.X[e - 1], kl2, C.A[e], true, N.A[e - 1], true);
-                else edge<2, EXT>(a, C.X[0], On, kl2, C.A[0], true, C.A[0], false);
-            }
-            // SE edge of (r+1, c_3): the NW edge of (r, c_3 + 1)
-            edge<2, EXT>(a, Ec, N.X[3], kl2, N.A[3], false, N.A[3], true);
+            const PCell On = ring_pair(j + 1, xw);                                // (r+1, c_0 - 1)
+            edge<1, EXT>(a, C.X[0], N.X[0], k2, l4, C.A[0], true, N.A[0], true);   // NE
+            edge<2, EXT>(a, C.X[0], On, k2, l4, C.A[0], true, C.A[0], false);      // NW
+            edge<1, EXT>(a, C.X[1], N.X[1], k2, l4, C.A[1], true, N.A[1], true);   // NE
+            edge<2, EXT>(a, C.X[1], N.X[0], k2, l4, C.A[1], true, N.A[0], true);   // NW
+            // SE edge of (r+1, c_1): the NW edge of (r, c_1 + 1)
+            edge<2, EXT>(a, Ec, N.X[1], k2, l4, N.A[1], false, N.A[1], true);
         }
     }
 
-    // Finishes the cells of row r and writes them to the other state buffer.
-    __device__ __forceinline__ void finish(int r, Row &C)
+    // Finishes the cells of row r and writes the ones this tile owns to the other state
+    // buffer.
+    __device__ __forceinline__ void finish(int r, PRow &C)
     {
-        CellNew o[4];
-        FF cl;
+        CellNew2 o[2];
+        FF cll, clr;
 #pragma unroll
-        for (int e = 0; e < 4; e++) {
-            float rt, ka, kb;
+        for (int e = 0; e < 2; e++) {
+            float2 rt, ka, kb;
             if constexpr (CLS) {
-                const int k = __float_as_int(C.th[e]);
-                rt = cls[0][k];
-                ka = cls[1][k];
-                kb = cls[2][k];
+                const int il = __float_as_int(C.th[e].x), ir = __float_as_int(C.th[e].y);
+                rt = make_float2(cls[0][il], cls[0][ir]);
+                ka = make_float2(cls[1][il], cls[1][ir]);
+                kb = make_float2(cls[2][il], cls[2][ir]);
             } else {
-                const float t = C.th[e];
-                rt = fast_rcp(t);
-                ka = a.alpha_p * (1.0f - t);
-                kb = t * a.alpha_s;
+                const float2 t = C.th[e];
+                rt = make_float2(fast_rcp(t.x), fast_rcp(t.y));
+                ka = mul2(dup2(a.alpha_p), sub2(dup2(1.0f), t));
+                kb = mul2(t, dup2(a.alpha_s));
             }
-            o[e] = cell_update<EXT>(C.A[e].hi, C.A[e].lo, C.A[e].m1, C.A[e].m2, C.X[e].m, C.X[e].v1, C.X[e].v2,
-                               rt, ka, kb, kappa, qr, dtf, a.g, __fmul_rn(dtf, a.tau), a.h_dry, cl);
+            o[e] = cell_update_pair<EXT>(C.A[e].hi, C.A[e].lo, C.A[e].m1, C.A[e].m2, C.X[e].m, C.X[e].v1,
+                                         C.X[e].v2, rt, ka, kb, kappa, qr, dtf, a.g, __fmul_rn(dtf, a.tau),
+                                         a.h_dry, cll, clr);
         }
-        if (!lane_own) return;       // columns written by the neighbouring tile
-        if (cl.hi != 0.0f || cl.lo != 0.0f) {
-            clq.add(cl.hi);
-            clq.add(cl.lo);
+        const size_t k0 = (size_t)r * a.pitch + c0 + 2 * lane;
+        if (own_l) {
+            if (cll.hi != 0.0f || cll.lo != 0.0f) {
+                clq.add(cll.hi);
+                clq.add(cll.lo);
+            }
+            *reinterpret_cast<float2 *>(a.mhi[np] + k0) = make_float2(o[0].hi.x, o[1].hi.x);
+            *reinterpret_cast<float2 *>(a.mlo[np] + k0) = make_float2(o[0].lo.x, o[1].lo.x);
+            *reinterpret_cast<float2 *>(a.v1[np] + k0) = make_float2(o[0].v1.x, o[1].v1.x);
+            *reinterpret_cast<float2 *>(a.v2[np] + k0) = make_float2(o[0].v2.x, o[1].v2.x);
+            cwb = max(cwb, max(o[0].cb0, o[1].cb0));
         }
-        const size_t k0 = (size_t)r * a.pitch + col(0);
-        *reinterpret_cast<float4 *>(a.mhi[np] + k0) = make_float4(o[0].hi, o[1].hi, o[2].hi, o[3].hi);
-        *reinterpret_cast<float4 *>(a.mlo[np] + k0) = make_float4(o[0].lo, o[1].lo, o[2].lo, o[3].lo);
-        *reinterpret_cast<float4 *>(a.v1[np] + k0) = make_float4(o[0].v1, o[1].v1, o[2].v1, o[3].v1);
-        *reinterpret_cast<float4 *>(a.v2[np] + k0) = make_float4(o[0].v2, o[1].v2, o[2].v2, o[3].v2);
-#pragma unroll
-        for (int e = 0; e < 4; e++) cwb = max(cwb, o[e].cbits);
+        if (own_r) {
+            if (clr.hi != 0.0f || clr.lo != 0.0f) {
+                clq.add(clr.hi);
+                clq.add(clr.lo);
+            }
+            *reinterpret_cast<float2 *>(a.mhi[np] + k0 + kHalf) = make_float2(o[0].hi.y, o[1].hi.y);
+            *reinterpret_cast<float2 *>(a.mlo[np] + k0 + kHalf) = make_float2(o[0].lo.y, o[1].lo.y);
+            *reinterpret_cast<float2 *>(a.v1[np] + k0 + kHalf) = make_float2(o[0].v1.y, o[1].v1.y);
+            *reinterpret_cast<float2 *>(a.v2[np] + k0 + kHalf) = make_float2(o[0].v2.y, o[1].v2.y);
+            cwb = max(cwb, max(o[0].cb1, o[1].cb1));
+        }
     }
 
     // One row step: load row j+1, evaluate the edges of row j, finish row j, free row j's
     // ring space.
     template <int ODD>
-    __device__ __forceinline__ void step_row(int j, Row &C, Row &N)
+    __device__ __forceinline__ void step_row(int j, PRow &C, PRow &N)
     {
         load(j + 1, N);
         if (j + 1 >= jown) {                // else: rows above the ones this tile writes
@@ -417,7 +603,7 @@ struct Tile {
             n_issued = min(kNC, nchunks);
         }
         __syncwarp();
-        Row R0, R1;
+        PRow R0, R1;
         load(0, R0);
         // local row j is global row r0 - 1 + j; every tile starts on an odd row r0, so
         // even j are even rows and one loop with two row bodies covers every tile

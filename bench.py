@@ -220,6 +220,8 @@ def run_cuda(args):
         out["ensemble"] = run_ensemble(args, stream)
     if args.sur_train > 0:
         out["surrogate"] = run_surrogate(args)
+    if args.cal:
+        out["calibration"] = run_calibration(args)
     return out
 
 
@@ -333,6 +335,42 @@ def run_ensemble(args, stream):
             "speedup": t_one / t_ens}
 
 
+def run_calibration(args):
+    """The flume study of Sec. 4.3 on the batched ensemble: the 21 x 26 sensitivity grid
+    (546 flume runs to a steady state in one ensemble) and the pattern search recovering
+    known friction coefficients from solver-made gauges (six experiments per point)."""
+    import time
+    from paper_2406_14933_gb300 import calibration as C
+    study = C.FlumeStudy()
+    r = C.sensitivity_grid(study, 1, 0.015)
+    sc = study.scenario(0.00709, 73.39, 1, 0.015)
+    grid = {"workload": f"flume 18 m x 1 m, {sc.rows}x{sc.cols} hex (l = {sc.l} m), 15 l/s, vegetation on "
+                        f"x >= 9 m, {study.t_end:.0f} s to a steady state; 21 x 26 (alpha_s, alpha_p) grid",
+            "scenarios": study.runs, "seconds": study.seconds, "scenarios_per_s": study.runs / study.seconds,
+            "delta_s": r["delta_s"], "delta_p": r["delta_p"],
+            "h_bar_range": [float(r["h_bar"].min()), float(r["h_bar"].max())]}
+    cal_study = C.FlumeStudy(l=0.2, t_end=400.0)
+    truth = (0.00709, 73.39)
+    h_exp = C.synthetic_gauges(cal_study, *truth)
+    t_gauges = cal_study.seconds
+    res = C.calibrate(cal_study, h_exp, tol=2e-3)
+    search = {"workload": "six experiments (2 vegetation layouts x 3 discharges), 17 gauges each, l = 0.2 m, "
+                          "400 s per run; gauges made by the solver at alpha = (0.00709, 73.39)",
+              "found": [float(v) for v in res.x], "truth": list(truth), "chi_m": res.f,
+              "points": res.evals, "batches": res.batches, "runs": cal_study.runs,
+              "seconds": cal_study.seconds - t_gauges}
+    out = {"sensitivity": grid, "estimation": search}
+    if not args.no_cpu_baseline:
+        import oracle as orc
+        p = orc.from_scenario(sc)
+        t0 = time.perf_counter()
+        p.run(p.mass(sc.h0), sc.v1_0.ravel().astype(float), sc.v2_0.ravel().astype(float), 0.0, sc.t_end)
+        dt = time.perf_counter() - t0
+        out["cpu_baseline"] = {"kind": "oracle", "cores": 1, "sample": "one flume run of the grid",
+                               "scenarios_per_s": 1.0 / dt, "grid_seconds_estimate": dt * study.runs}
+    return out
+
+
 MLP_FLOP_PER_QUERY = 2 * (36 * 256 + 256 * 256 + 256 * 256 + 256 * 128)   # algorithmic (unpadded)
 
 
@@ -442,6 +480,7 @@ def main():
     ap.add_argument("--sur-epochs", type=int, default=100)
     ap.add_argument("--sur-n", type=int, default=64, help="surrogate members' raster side [cells]")
     ap.add_argument("--sur-l", type=float, default=8.0, help="surrogate members' hexagon edge [m]")
+    ap.add_argument("--cal", type=int, default=1, help="flume sensitivity grid and coefficient estimation (0: skip)")
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)
     out = run_reference(args) if args.impl == "reference" else run_cuda(args)

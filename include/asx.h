@@ -221,8 +221,9 @@ typedef struct asx_ensemble asx_ensemble;
 /* One scenario: geometry, boundaries and parameters as in asx_raster_desc / asx_params
  * (per-cell porosity, scalar alpha_s / alpha_p), a rain table of at most 8 points (host
  * pointers, copied), the end time t_end [s] the scenario runs to, the hydrograph interval
- * sample_dt and capacity max_samples, max_steps (0 = no limit), and the per-side values of
- * ASX_BC_FLUX / ASX_BC_DIRICHLET sides (bc_q, bc_h, bc_u as in asx_params). */
+ * sample_dt and capacity max_samples, max_steps (0 = no limit), the per-side values of
+ * ASX_BC_FLUX / ASX_BC_DIRICHLET sides (bc_q, bc_h, bc_u as in asx_params), and the
+ * optional terms viscosity, tau, h_dry as in asx_params (all 0: the plain scheme). */
 typedef struct {
     int rows, cols;
     double edge_m;
@@ -234,6 +235,8 @@ typedef struct {
     int max_samples;
     long long max_steps;
     double bc_q[4], bc_h[4], bc_u[4];
+    int viscosity;
+    double tau, h_dry;
 } asx_scenario_desc;
 
 /* Launch shape of the ensemble kernel: CTAs per cluster (1, 2, 4, 8) sharing one

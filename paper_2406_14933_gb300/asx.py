@@ -64,7 +64,8 @@ class asx_scenario_desc(C.Structure):
                 ("alpha_p", C.c_double), ("n_rain", C.c_int), ("rain_t", C.POINTER(C.c_double)),
                 ("rain_r", C.POINTER(C.c_double)), ("t_end", C.c_double), ("sample_dt", C.c_double),
                 ("max_samples", C.c_int), ("max_steps", C.c_longlong), ("bc_q", C.c_double * 4),
-                ("bc_h", C.c_double * 4), ("bc_u", C.c_double * 4)]
+                ("bc_h", C.c_double * 4), ("bc_u", C.c_double * 4), ("viscosity", C.c_int),
+                ("tau", C.c_double), ("h_dry", C.c_double)]
 
 
 class asx_ensemble_tuning(C.Structure):

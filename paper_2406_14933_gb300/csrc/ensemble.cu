@@ -143,8 +143,10 @@ __device__ __forceinline__ void block_reduce(unsigned &cb, double &out, double &
 }
 
 // The persistent ensemble kernel.  NT threads per CTA, K cells per thread per round;
-// BND: scenarios with inflow sides (given mass flux, Dirichlet) are present.
-template <int NT, int K, bool BND>
+// MODE 0: the plain scheme; 1: inflow sides (given mass flux, Dirichlet) compiled in;
+// 2: inflow sides and the optional terms (artificial viscosity, linear resistance, dry
+// threshold) compiled in.
+template <int NT, int K, int MODE>
 __global__ void __launch_bounds__(NT) ensemble_kernel(EnsScenario *scen, const int *order, int n_scen,
                                                      unsigned *queue)
 {
@@ -228,7 +230,8 @@ __global__ void __launch_bounds__(NT) ensemble_kernel(EnsScenario *scen, const i
 #pragma unroll
                 for (int u = 0; u < K; u++) {
                     const int i = i0 + u * NT;
-                    if (i < band) gather_cell<false, BND>(sa, sc, rb0 + i / cols, i % cols, cb, outd, clq);
+                    if (i < band)
+                        gather_cell<(MODE >= 2), (MODE >= 1)>(sa, sc, rb0 + i / cols, i % cols, cb, outd, clq);
                 }
             }
             double out = outd.value(), cl = clq.value(), sto = 0.0;
@@ -297,23 +300,26 @@ __global__ void __launch_bounds__(NT) ensemble_kernel(EnsScenario *scen, const i
 
 using EnsKernel = void (*)(EnsScenario *, const int *, int, unsigned *);
 
-template <int NT, int K, bool BND>
+template <int NT, int K, int MODE>
 EnsKernel ens_kernel_ptr()
 {
-    return ensemble_kernel<NT, K, BND>;
+    return ensemble_kernel<NT, K, MODE>;
 }
 
-template <bool BND>
-EnsKernel ens_kernel_b(int nt, int k)
+template <int MODE>
+EnsKernel ens_kernel_m(int nt, int k)
 {
     if (nt == 256)
-        return k == 1 ? ens_kernel_ptr<256, 1, BND>() : k == 2 ? ens_kernel_ptr<256, 2, BND>() : ens_kernel_ptr<256, 4, BND>();
+        return k == 1 ? ens_kernel_ptr<256, 1, MODE>() : k == 2 ? ens_kernel_ptr<256, 2, MODE>() : ens_kernel_ptr<256, 4, MODE>();
     if (nt == 512)
-        return k == 1 ? ens_kernel_ptr<512, 1, BND>() : k == 2 ? ens_kernel_ptr<512, 2, BND>() : ens_kernel_ptr<512, 4, BND>();
-    return k == 1 ? ens_kernel_ptr<128, 1, BND>() : k == 2 ? ens_kernel_ptr<128, 2, BND>() : ens_kernel_ptr<128, 4, BND>();
+        return k == 1 ? ens_kernel_ptr<512, 1, MODE>() : k == 2 ? ens_kernel_ptr<512, 2, MODE>() : ens_kernel_ptr<512, 4, MODE>();
+    return k == 1 ? ens_kernel_ptr<128, 1, MODE>() : k == 2 ? ens_kernel_ptr<128, 2, MODE>() : ens_kernel_ptr<128, 4, MODE>();
 }
 
-EnsKernel ens_kernel(int nt, int k, bool bnd) { return bnd ? ens_kernel_b<true>(nt, k) : ens_kernel_b<false>(nt, k); }
+EnsKernel ens_kernel(int nt, int k, int mode)
+{
+    return mode >= 2 ? ens_kernel_m<2>(nt, k) : mode == 1 ? ens_kernel_m<1>(nt, k) : ens_kernel_m<0>(nt, k);
+}
 
 }  // namespace
 }  // namespace asx
@@ -336,7 +342,7 @@ struct asx_ensemble {
     unsigned *queue = nullptr;
     asx_ensemble_tuning tuning{};
     bool tuned = false, have_fields_all = false;
-    bool bnd = false;                       // some scenario has an inflow side
+    int mode = 0;                           // kernel variant: 1 inflow sides, 2 also optional terms
     std::vector<char> have_fields;
     cudaGraphExec_t graph = nullptr;
     asx_ensemble_tuning graph_tuning{};
@@ -367,9 +373,9 @@ bool tuning_valid(const asx_ensemble_tuning &t)
 }
 
 // Clusters of this shape that fit on the device at once.
-int resident_clusters(const asx_ensemble_tuning &t, bool bnd)
+int resident_clusters(const asx_ensemble_tuning &t, int mode)
 {
-    EnsKernel f = ens_kernel(t.threads, t.cells_per_thread, bnd);
+    EnsKernel f = ens_kernel(t.threads, t.cells_per_thread, mode);
     cudaLaunchConfig_t cfg{};
     cudaLaunchAttribute at[1];
     at[0].id = cudaLaunchAttributeClusterDimension;
@@ -387,8 +393,8 @@ int resident_clusters(const asx_ensemble_tuning &t, bool bnd)
 
 cudaError_t launch_ensemble(asx_ensemble *e, const asx_ensemble_tuning &t, cudaStream_t s)
 {
-    EnsKernel f = ens_kernel(t.threads, t.cells_per_thread, e->bnd);
-    const int nc = std::min(resident_clusters(t, e->bnd), e->n);
+    EnsKernel f = ens_kernel(t.threads, t.cells_per_thread, e->mode);
+    const int nc = std::min(resident_clusters(t, e->mode), e->n);
     cudaLaunchConfig_t cfg{};
     cudaLaunchAttribute at[1];
     at[0].id = cudaLaunchAttributeClusterDimension;
@@ -444,6 +450,9 @@ asx_status asx_create_ensemble(int n, const asx_scenario_desc *descs, void *cuda
             return ASX_EINVAL;
         if (d.n_rain < 0 || d.n_rain > kEnsMaxRain || (d.n_rain > 0 && (!d.rain_t || !d.rain_r))) return ASX_EINVAL;
         if (!(d.t_end >= 0) || !std::isfinite(d.t_end) || !(d.sample_dt >= 0) || d.max_samples < 0) return ASX_EINVAL;
+        if ((d.viscosity != 0 && d.viscosity != 1) || !(d.tau >= 0) || !std::isfinite(d.tau) || !(d.h_dry >= 0) ||
+            !std::isfinite(d.h_dry))
+            return ASX_EINVAL;
     }
     asx_ensemble *e = new (std::nothrow) asx_ensemble();
     if (!e) return ASX_ENOMEM;
@@ -451,9 +460,11 @@ asx_status asx_create_ensemble(int n, const asx_scenario_desc *descs, void *cuda
     e->device = device;
     e->stream = (cudaStream_t)cuda_stream;
     e->desc.assign(descs, descs + n);
-    for (int i = 0; i < n; i++)
+    for (int i = 0; i < n; i++) {
         for (int sd = 0; sd < 4; sd++)
-            if (descs[i].bc[sd] == ASX_BC_FLUX || descs[i].bc[sd] == ASX_BC_DIRICHLET) e->bnd = true;
+            if (descs[i].bc[sd] == ASX_BC_FLUX || descs[i].bc[sd] == ASX_BC_DIRICHLET) e->mode = std::max(e->mode, 1);
+        if (descs[i].viscosity || descs[i].tau > 0 || descs[i].h_dry > 0) e->mode = 2;
+    }
     e->have_fields.assign(n, 0);
     if (cudaSetDevice(device) != cudaSuccess) { delete e; return ASX_ECUDA; }
     // planes per scenario: 8 state (2 parities x m_hi, m_lo, v1, v2), z, theta, 4 initial
@@ -517,6 +528,9 @@ asx_status asx_create_ensemble(int n, const asx_scenario_desc *descs, void *cuda
             a.bh[s] = (float)d.bc_h[s];
             a.bu[s] = (float)d.bc_u[s];
         }
+        a.visc = d.viscosity;
+        a.tau = (float)d.tau;
+        a.h_dry = (float)d.h_dry;
         h.t_end = d.t_end;
         h.cfl = d.cfl;
         h.dt_max = d.dt_max;

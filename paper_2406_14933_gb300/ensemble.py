@@ -53,6 +53,8 @@ class Ensemble:
             d.max_steps = int(max_steps)
             for s in range(4):
                 d.bc_q[s], d.bc_h[s], d.bc_u[s] = float(sc.bc_q[s]), float(sc.bc_h[s]), float(sc.bc_u[s])
+            d.viscosity = int(bool(sc.viscosity))
+            d.tau, d.h_dry = float(sc.tau), float(sc.h_dry)
             descs.append(d)
         self.handle = _a.asx_create_ensemble(descs, stream, device)
         for i, sc in enumerate(scenarios):

@@ -392,3 +392,61 @@ def thacker(l=1.0, x_range=(250.0, 750.0), y_range=(350.0, 650.0), t_end=10.0) -
     sc.tau = T["tau"]
     sc.h_dry = 1.0e-3
     return sc
+
+
+# ----------------------------------------------------------------------------- flume
+
+# The vegetated flume of Sec. 4.2.2: 18 m x 1 m, bed slope 1.05 mm/m, emergent cylinders of
+# radius 5 mm at 81 per m^2 over one half (theta_v = 1 - N pi R_c^2), upstream discharges of
+# the six experiments in m^3/s (layout theta_1: vegetation on x >= 9 m; theta_2: on x < 9 m).
+FLUME = dict(length=18.0, width=1.0, slope=1.05e-3, theta_v=1.0 - 81.0 * math.pi * 0.005 ** 2,
+             q=((1, 0.007), (1, 0.015), (1, 0.021), (2, 0.007), (2, 0.015), (2, 0.050)))
+
+
+def flume(q_l: float, layout: int, alpha_s: float = ALPHA_S_DEFAULT, alpha_p: float = ALPHA_P_DEFAULT,
+          l: float = 0.1, tailwater: float = 0.1, t_end: float = 600.0) -> Scenario:
+    """The flume of Sec. 4.2.2 on a hexagonal raster of edge l: bed z = m (18 - x), porosity
+    theta_1 (layout 1) or theta_2 (layout 2), uniform soil friction alpha_s and plant drag
+    alpha_p.  The upstream (west) side admits the discharge q_l [m^3/s] as a given mass flux
+    spread over the side's width (west_width); the downstream (east) side is a Dirichlet side
+    at the tailwater depth, its ghost carrying the same discharge out (a tailgate: the
+    zero-gradient outlet of the paper leaves a subcritical flow without control, and the
+    depths do not settle); north and south are walls.  Initially at rest at the tailwater
+    level over the bed."""
+    F = FLUME
+    cols = int(round(F["length"] / (math.sqrt(3.0) * l)))
+    rows = max(2, int(round(F["width"] / (1.5 * l))))
+    x, _ = cell_centres(rows, cols, l)
+    sh = (rows, cols)
+    z = (F["slope"] * (F["length"] - x)).astype(np.float32)
+    veg = (x >= 9.0) if layout == 1 else (x < 9.0)
+    theta = np.where(veg, F["theta_v"], 1.0).astype(np.float32)
+    level = tailwater + float(z.min())
+    h0 = np.maximum(level - z.astype(np.float64), 0.0).astype(np.float32)
+    q_side = q_l / west_width(rows, l)              # per unit width of the inflow side
+    sc = Scenario(f"flume_q{q_l * 1e3:g}_t{layout}", rows, cols, l, z, theta, _fill(sh, alpha_s),
+                  _fill(sh, alpha_p), h0, _fill(sh, 0.0), _fill(sh, 0.0), bc=(FLUX, DIRICHLET, WALL, WALL),
+                  t_end=t_end, meta=dict(q_l=q_l, layout=layout, tailwater=tailwater))
+    sc.bc_q = (q_side, 0.0, 0.0, 0.0)
+    sc.bc_h = (0.0, tailwater, 0.0, 0.0)
+    sc.bc_u = (0.0, -q_side / tailwater, 0.0, 0.0)
+    return sc
+
+
+def west_width(rows: int, l: float) -> float:
+    """Width of a raster's west side seen by a flux along its normal: the sum over its
+    boundary edges of l (n_W . n_edge).  Every row has its W edge (1); an even row, not
+    shifted, also has its NW and SW edges on the side (1/2 each) when the neighbour row
+    exists (else the edge belongs to the N or S side)."""
+    even = [r for r in range(rows) if r % 2 == 0]
+    return l * (rows + 0.5 * sum(1 for r in even if r + 1 < rows) + 0.5 * sum(1 for r in even if r >= 1))
+
+
+def flume_gauges(sc: Scenario, n: int = 17) -> np.ndarray:
+    """Flat indices of n gauges on the flume's centre row, evenly spaced from x = 0.5 m to
+    x = 17.5 m (nearest cell centre)."""
+    x, _ = cell_centres(sc.rows, sc.cols, sc.l)
+    r = sc.rows // 2
+    xs = np.linspace(0.5, FLUME["length"] - 0.5, n)
+    cols = np.abs(x[r][None, :] - xs[:, None]).argmin(axis=1)
+    return r * sc.cols + cols

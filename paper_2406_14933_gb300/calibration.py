@@ -47,7 +47,10 @@ class FlumeStudy:
     experiments: tuple = inputs.FLUME["q"]        # (layout, q_l [m^3/s]) pairs
     tuning: tuple | None = None                   # ensemble launch shape (None: autotune)
     runs: int = 0                                 # scenarios run so far
-    seconds: float = 0.0                          # wall time in ensemble runs
+    cell_updates: int = 0                         # cells x time steps of those runs
+    seconds: float = 0.0                          # wall time, end to end (build, tune, solve, read back)
+    solve_seconds: float = 0.0                    # wall time of the ensemble launches alone
+    tune_seconds: float = 0.0                     # wall time of the launch-shape search
 
     def scenario(self, alpha_s: float, alpha_p: float, layout: int, q_l: float):
         sc = inputs.flume(q_l, layout, alpha_s, alpha_p, l=self.l, tailwater=self.tailwater, t_end=self.t_end)
@@ -62,18 +65,24 @@ def steady_depths(study: FlumeStudy, scenarios: list) -> list[np.ndarray]:
     E = Ensemble(scenarios)
     try:
         tuning = study.tuning
+        t1 = time.perf_counter()
         if tuning is None:
             study.tuning = tuning = E.autotune(max_steps=200).as_tuple()
-        E.run(tuning)
+        t2 = time.perf_counter()
+        E.run(tuning)                     # returns once the launch has finished
+        t3 = time.perf_counter()
         out = []
         for s, sc in enumerate(scenarios):
-            t, _ = E.clock(s)
+            t, steps = E.clock(s)
             if t < sc.t_end * (1.0 - 1e-12):
                 raise RuntimeError(f"scenario {s} stopped at t = {t} before {sc.t_end}")
+            study.cell_updates += steps * sc.n
             out.append(E.fields(s)[0])
     finally:
         E.close()
     study.runs += len(scenarios)
+    study.tune_seconds += t2 - t1
+    study.solve_seconds += t3 - t2
     study.seconds += time.perf_counter() - t0
     return out
 

@@ -341,6 +341,7 @@ def run_calibration(args):
     known friction coefficients from solver-made gauges (six experiments per point)."""
     import time
     from paper_2406_14933_gb300 import calibration as C
+    from paper_2406_14933_gb300 import inputs
     study = C.FlumeStudy()
     r = C.sensitivity_grid(study, 1, 0.015)
     sc = study.scenario(0.00709, 73.39, 1, 0.015)
@@ -352,6 +353,17 @@ def run_calibration(args):
             "end_to_end_seconds": study.seconds, "tune_seconds": study.tune_seconds,
             "tuning": list(study.tuning), "delta_s": r["delta_s"], "delta_p": r["delta_p"],
             "h_bar_range": [float(r["h_bar"].min()), float(r["h_bar"].max())]}
+    sweep_study = C.FlumeStudy(tuning=study.tuning)
+    envs = [dict(q=0.007), dict(q=0.015), dict(q=0.021), dict(q=0.015, theta_v=0.98),
+            dict(q=0.015, slope=0.5e-3), dict(q=0.015, slope=3.0e-3)]
+    sw = C.sensitivity_sweep(sweep_study, envs)
+    grid["environments"] = {
+        "runs": sweep_study.runs, "solve_seconds": sweep_study.solve_seconds,
+        "scenarios_per_s": sweep_study.runs / sweep_study.solve_seconds,
+        "end_to_end_seconds": sweep_study.seconds,
+        "delta": [{"q": e["env"]["q"], "theta_v": e["env"].get("theta_v", inputs.FLUME["theta_v"]),
+                   "slope": e["env"].get("slope", inputs.FLUME["slope"]), "delta_s": e["delta_s"],
+                   "delta_p": e["delta_p"]} for e in sw]}
     cal_study = C.FlumeStudy(l=0.2, t_end=400.0)
     truth = (0.00709, 73.39)
     h_exp = C.synthetic_gauges(cal_study, *truth)

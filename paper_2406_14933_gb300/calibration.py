@@ -8,7 +8,8 @@ flume keeps sloshing; with it the depths settle geometrically), run to a steady 
 
 * ``h_bar``: the mean depth over the cells with x >= 9 m (Eq. eq_h_bar);
 * ``sensitivity``: delta_s and delta_p, the averaged forward differences of h_bar over a
-  regular (alpha_s, alpha_p) grid (Sec. 4.3);
+  regular (alpha_s, alpha_p) grid (Sec. 4.3); ``sensitivity_sweep`` repeats them over
+  environments p = (q, theta_v, m), all grids in one ensemble;
 * ``chi``: the root-mean-square gauge-depth misfit over experiments and gauges
   (Eq. eq_chi_6experim);
 * ``hooke_jeeves``: Hooke and Jeeves' pattern search (exploratory moves coordinate by
@@ -52,8 +53,10 @@ class FlumeStudy:
     solve_seconds: float = 0.0                    # wall time of the ensemble launches alone
     tune_seconds: float = 0.0                     # wall time of the launch-shape search
 
-    def scenario(self, alpha_s: float, alpha_p: float, layout: int, q_l: float):
-        sc = inputs.flume(q_l, layout, alpha_s, alpha_p, l=self.l, tailwater=self.tailwater, t_end=self.t_end)
+    def scenario(self, alpha_s: float, alpha_p: float, layout: int, q_l: float, theta_v: float | None = None,
+                 slope: float | None = None):
+        sc = inputs.flume(q_l, layout, alpha_s, alpha_p, l=self.l, tailwater=self.tailwater, t_end=self.t_end,
+                          theta_v=theta_v, slope=slope)
         sc.viscosity = True
         return sc
 
@@ -121,6 +124,23 @@ def sensitivity_grid(study: FlumeStudy, layout: int = 1, q_l: float = 0.015, ns:
     H = np.array([h_bar(h, sc) for h, sc in zip(hs, scs)]).reshape(ns, np_)
     ds, dp = sensitivity(H, a_s[1] - a_s[0], a_p[1] - a_p[0])
     return dict(alpha_s=a_s, alpha_p=a_p, h_bar=H, delta_s=ds, delta_p=dp)
+
+
+def sensitivity_sweep(study: FlumeStudy, envs: list, layout: int = 1, ns: int = GRID[0], np_: int = GRID[1],
+                      box=LAMBDA) -> list[dict]:
+    """delta_s and delta_p as functions of the environment p = (q, theta_v, m) (Sec. 4.3):
+    one (alpha_s, alpha_p) grid per environment dict(q=..., theta_v=..., slope=...), every
+    grid of every environment in one ensemble."""
+    a_s, a_p = grid_points(ns, np_, box)
+    scs = [study.scenario(s, p, layout, e["q"], e.get("theta_v"), e.get("slope")) for e in envs for s in a_s
+           for p in a_p]
+    hs = steady_depths(study, scs)
+    Hb = np.array([h_bar(h, sc) for h, sc in zip(hs, scs)]).reshape(len(envs), ns, np_)
+    out = []
+    for e, H in zip(envs, Hb):
+        ds, dp = sensitivity(H, a_s[1] - a_s[0], a_p[1] - a_p[0])
+        out.append(dict(env=dict(e), h_bar=H, delta_s=ds, delta_p=dp))
+    return out
 
 
 def chi(h_exp: np.ndarray, h_sim: np.ndarray) -> float:

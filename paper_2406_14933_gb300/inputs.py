@@ -404,29 +404,35 @@ FLUME = dict(length=18.0, width=1.0, slope=1.05e-3, theta_v=1.0 - 81.0 * math.pi
 
 
 def flume(q_l: float, layout: int, alpha_s: float = ALPHA_S_DEFAULT, alpha_p: float = ALPHA_P_DEFAULT,
-          l: float = 0.1, tailwater: float = 0.1, t_end: float = 600.0) -> Scenario:
+          l: float = 0.1, tailwater: float = 0.1, t_end: float = 600.0, theta_v: float | None = None,
+          slope: float | None = None) -> Scenario:
     """The flume of Sec. 4.2.2 on a hexagonal raster of edge l: bed z = m (18 - x), porosity
     theta_1 (layout 1) or theta_2 (layout 2), uniform soil friction alpha_s and plant drag
-    alpha_p.  The upstream (west) side admits the discharge q_l [m^3/s] as a given mass flux
+    alpha_p; theta_v and slope override the flume's vegetation porosity and bed slope (the
+    environment of the sensitivity study).  The upstream (west) side admits the discharge
+    q_l [m^3/s] as a given mass flux
     spread over the side's width (west_width); the downstream (east) side is a Dirichlet side
     at the tailwater depth, its ghost carrying the same discharge out (a tailgate: the
     zero-gradient outlet of the paper leaves a subcritical flow without control, and the
     depths do not settle); north and south are walls.  Initially at rest at the tailwater
     level over the bed."""
     F = FLUME
+    theta_v = F["theta_v"] if theta_v is None else theta_v
+    slope = F["slope"] if slope is None else slope
     cols = int(round(F["length"] / (math.sqrt(3.0) * l)))
     rows = max(2, int(round(F["width"] / (1.5 * l))))
     x, _ = cell_centres(rows, cols, l)
     sh = (rows, cols)
-    z = (F["slope"] * (F["length"] - x)).astype(np.float32)
+    z = (slope * (F["length"] - x)).astype(np.float32)
     veg = (x >= 9.0) if layout == 1 else (x < 9.0)
-    theta = np.where(veg, F["theta_v"], 1.0).astype(np.float32)
+    theta = np.where(veg, theta_v, 1.0).astype(np.float32)
     level = tailwater + float(z.min())
     h0 = np.maximum(level - z.astype(np.float64), 0.0).astype(np.float32)
     q_side = q_l / west_width(rows, l)              # per unit width of the inflow side
     sc = Scenario(f"flume_q{q_l * 1e3:g}_t{layout}", rows, cols, l, z, theta, _fill(sh, alpha_s),
                   _fill(sh, alpha_p), h0, _fill(sh, 0.0), _fill(sh, 0.0), bc=(FLUX, DIRICHLET, WALL, WALL),
-                  t_end=t_end, meta=dict(q_l=q_l, layout=layout, tailwater=tailwater))
+                  t_end=t_end, meta=dict(q_l=q_l, layout=layout, tailwater=tailwater, theta_v=theta_v,
+                                         slope=slope))
     sc.bc_q = (q_side, 0.0, 0.0, 0.0)
     sc.bc_h = (0.0, tailwater, 0.0, 0.0)
     sc.bc_u = (0.0, -q_side / tailwater, 0.0, 0.0)

@@ -200,3 +200,12 @@ def test_flume_settles_with_viscosity(orc):
     r2 = p.run(r1["m"], r1["v1"], r1["v2"], r1["t"], 600.0)
     th = sc.theta.ravel().astype(float)
     assert np.max(np.abs(r2["m"] / th - r1["m"] / th)) < 1e-5
+
+
+def test_flume_environment_overrides():
+    sc = inputs.flume(0.015, 1, theta_v=0.98, slope=3.0e-3)
+    x, _ = inputs.cell_centres(sc.rows, sc.cols, sc.l)
+    assert np.all(sc.theta[x >= 9.0] == np.float32(0.98)) and np.all(sc.theta[x < 9.0] == 1.0)
+    assert np.allclose(sc.z, (3.0e-3 * (18.0 - x)).astype(np.float32))
+    d = inputs.flume(0.015, 2)
+    assert np.all(d.theta[x < 9.0] == np.float32(inputs.FLUME["theta_v"])) and np.all(d.theta[x >= 9.0] == 1.0)

@@ -118,3 +118,20 @@ def test_calibration_recovers_known_coefficients(asx):
     assert abs(r.x[0] - truth[0]) <= 0.02 * (C.LAMBDA[0][1] - C.LAMBDA[0][0])
     assert abs(r.x[1] - truth[1]) <= 0.02 * (C.LAMBDA[1][1] - C.LAMBDA[1][0])
     assert r.f < 1e-4
+
+
+def test_sensitivity_sweep_over_environments(asx):
+    """delta_s, delta_p over environments p = (q, theta_v, m), every grid in one ensemble:
+    without vegetation (theta_v = 1) the plant drag alpha_p (1 - theta) vanishes, every
+    alpha_p gives the same run bit for bit and delta_p is exactly 0; with vegetation it is
+    positive; and an environment's grid inside the sweep is, bit for bit, the grid run on
+    its own."""
+    study = C.FlumeStudy(l=0.2, t_end=300.0)
+    envs = [dict(q=0.015), dict(q=0.015, theta_v=1.0), dict(q=0.007, slope=3.0e-3)]
+    res = C.sensitivity_sweep(study, envs, ns=5, np_=5)
+    assert res[1]["delta_p"] == 0.0
+    assert res[0]["delta_p"] > 0.0 and res[2]["delta_p"] > 0.0
+    alone = C.sensitivity_grid(C.FlumeStudy(l=0.2, t_end=300.0), 1, 0.015, ns=5, np_=5)
+    assert np.array_equal(alone["h_bar"], res[0]["h_bar"])
+    for r in res:
+        print(f"[sweep] {r['env']}: delta_s {r['delta_s']:.4g} m, delta_p {r['delta_p']:.4g} m")

@@ -357,6 +357,14 @@ asx_status asx_state_scan_noalloc(int rows, int cols, int pitch, double edge_m, 
                                   const float *v2, const float *theta, double *storage_out,
                                   float *cmax_out, void *cuda_stream);
 
+/* Failure-detection self-test (no counterpart in the paper): one warp on `device` waits,
+ * with the bounded mbarrier wait of the step kernels (which gives up after 2 s), on an
+ * mbarrier that nothing arrives at; the wait runs out, the kernel flags it, and the
+ * host reads the flag.  Returns ASX_ETIMEOUT when the timeout was detected and reported
+ * (the expected outcome; the CUDA context stays usable), ASX_OK if the wait completed,
+ * ASX_ECUDA / ASX_ENOMEM on a CUDA error. */
+asx_status asx_selftest_wait(int device);
+
 #ifdef __cplusplus
 }
 #endif

@@ -96,6 +96,7 @@ _PROTOS = {
     "asx_get_clock": (C.c_int, [_RASTER, C.c_int, C.POINTER(C.c_double), C.POINTER(C.c_double),
                                 C.POINTER(C.c_longlong)]),
     "asx_last_error": (C.c_char_p, [_RASTER]),
+    "asx_selftest_wait": (C.c_int, [C.c_int]),
     "asx_state_scan_noalloc": (C.c_int, [C.c_int, C.c_int, C.c_int, C.c_double, C.c_double, _vp, _vp,
                                          _vp, _vp, _vp, _vp, _vp, _vp]),
     "asx_create_ensemble": (C.c_int, [C.c_int, C.POINTER(asx_scenario_desc), _vp, C.c_int, C.POINTER(_ENS)]),
@@ -247,6 +248,12 @@ def asx_state_scan_noalloc(rows, cols, pitch, edge_m, g, m_hi, m_lo, v1, v2, the
     _check(load().asx_state_scan_noalloc(int(rows), int(cols), int(pitch), float(edge_m), float(g),
                                          _ptr(m_hi), _ptr(m_lo), _ptr(v1), _ptr(v2), _ptr(theta),
                                          _ptr(storage_out), _ptr(cmax_out), cuda_stream))
+
+
+def asx_selftest_wait(device=0):
+    """Runs the bounded-wait self-test (see asx.h) and returns its status code: ASX_ETIMEOUT
+    when the timeout was detected and reported."""
+    return load().asx_selftest_wait(int(device))
 
 
 # ----------------------------------------------------------------- ensembles

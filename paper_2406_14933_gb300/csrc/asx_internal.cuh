@@ -63,6 +63,20 @@ struct DevCtl {
 constexpr int kErrNumeric = 1;
 constexpr int kErrTimeout = 2;
 
+// Every spin-wait of the kernels (on an mbarrier phase) gives up after this long and
+// reports kErrTimeout: copies and products complete in microseconds.
+constexpr unsigned long long kWaitLimitNs = 2000000000ull;
+
+#ifdef __CUDACC__
+// Nanoseconds of the GPU's global timer.
+__device__ __forceinline__ unsigned long long global_ns()
+{
+    unsigned long long t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
+#endif
+
 // Arguments of the step kernels (passed by value; fixed for a raster so that a
 // captured CUDA graph can replay them).
 struct StepArgs {

@@ -57,13 +57,16 @@ __device__ __forceinline__ bool mbar_try(unsigned long long *bar, unsigned parit
     return ok != 0;
 }
 
+// Bounded wait on an mbarrier phase (try_wait suspends the warp for a short interval
+// each time); gives up after kWaitLimitNs.
 __device__ __forceinline__ bool mbar_wait_bounded1(unsigned long long *bar, unsigned parity)
 {
-    for (unsigned it = 0; it < (1u << 26); it++) {
+    if (mbar_try(bar, parity)) return true;
+    const unsigned long long t0 = global_ns();
+    for (;;) {
         if (mbar_try(bar, parity)) return true;
-        if (it > 64) __nanosleep(32);
+        if (global_ns() - t0 > kWaitLimitNs) return false;
     }
-    return false;
 }
 
 // Shared-memory matrix descriptor of a K-major, non-swizzled operand: core matrices of

@@ -120,14 +120,16 @@ __device__ __forceinline__ void tma_load_2d(void *dst, const CUtensorMap *map, i
         : "memory");
 }
 
-// Bounded wait on an mbarrier phase: gives up after ~2^26 polls (well over a second).
+// Bounded wait on an mbarrier phase: each try_wait suspends the warp until the phase
+// completes or a short hardware-defined interval passes; gives up after kWaitLimitNs.
 __device__ __forceinline__ bool mbar_wait_bounded(unsigned long long *bar, unsigned parity)
 {
-    for (unsigned it = 0; it < (1u << 26); it++) {
+    if (mbar_try_wait(bar, parity)) return true;
+    const unsigned long long t0 = global_ns();
+    for (;;) {
         if (mbar_try_wait(bar, parity)) return true;
-        if (it > 64) __nanosleep(32);
+        if (global_ns() - t0 > kWaitLimitNs) return false;
     }
-    return false;
 }
 
 // ----------------------------------------------------------------- packed pairs
@@ -775,4 +777,39 @@ cudaError_t launch_step_strip(const StepArgs &a, const StripMaps &maps, cudaStre
     return cudaGetLastError();
 }
 
+namespace {
+
+// One warp waits, with the step kernels' bounded wait, on an mbarrier nothing arrives at,
+// and flags the timeout.
+__global__ void wait_selftest_kernel(int *err)
+{
+    __shared__ __align__(8) unsigned long long bar;
+    if (threadIdx.x == 0) {
+        mbar_init(&bar, 1);
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    __syncwarp();
+    if (threadIdx.x == 0 && !mbar_wait_bounded(&bar, 0u)) atomicOr(err, kErrTimeout);
+}
+
+}  // namespace
+
 }  // namespace asx
+
+extern "C" asx_status asx_selftest_wait(int device)
+{
+    if (cudaSetDevice(device) != cudaSuccess) return ASX_ECUDA;
+    int *err = nullptr;
+    if (cudaMalloc(&err, sizeof(int)) != cudaSuccess) return ASX_ENOMEM;
+    cudaError_t e = cudaMemset(err, 0, sizeof(int));
+    if (e == cudaSuccess) {
+        asx::wait_selftest_kernel<<<1, 32>>>(err);
+        e = cudaGetLastError();
+    }
+    if (e == cudaSuccess) e = cudaDeviceSynchronize();
+    int h = 0;
+    if (e == cudaSuccess) e = cudaMemcpy(&h, err, sizeof(int), cudaMemcpyDeviceToHost);
+    cudaFree(err);
+    if (e != cudaSuccess) return ASX_ECUDA;
+    return (h & asx::kErrTimeout) ? ASX_ETIMEOUT : ASX_OK;
+}

@@ -46,7 +46,9 @@ typedef enum {
     ASX_ECUDA = 3,     /* a CUDA runtime call failed (asx_last_error has the text) */
     ASX_ESTATE = 4,    /* the call needs fields / params that were not set */
     ASX_ENUMERIC = 5,  /* the state became non-finite; the clock stops at that step */
-    ASX_ETIMEOUT = 6   /* a bounded wait inside a kernel ran out */
+    ASX_ETIMEOUT = 6,  /* a bounded wait inside a kernel ran out */
+    ASX_EBOUNDS = 7    /* an index outside its buffer (only the bounds-checked debug build
+                        * of the library checks; the access was skipped) */
 } asx_status;
 
 enum { ASX_BC_WALL = 0, ASX_BC_FREE = 1, ASX_BC_FLUX = 2, ASX_BC_DIRICHLET = 3 };

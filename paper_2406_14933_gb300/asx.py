@@ -13,11 +13,13 @@ import os
 import numpy as np
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
-LIB_PATH = os.path.join(_HERE, "_build", "libasx.so")
+# the library this process loads: the in-tree build, or the file ASX_LIB names (e.g. the
+# bounds-checked debug build, build.build_checked())
+LIB_PATH = os.environ.get("ASX_LIB") or os.path.join(_HERE, "_build", "libasx.so")
 
-ASX_OK, ASX_EINVAL, ASX_ENOMEM, ASX_ECUDA, ASX_ESTATE, ASX_ENUMERIC, ASX_ETIMEOUT = range(7)
+ASX_OK, ASX_EINVAL, ASX_ENOMEM, ASX_ECUDA, ASX_ESTATE, ASX_ENUMERIC, ASX_ETIMEOUT, ASX_EBOUNDS = range(8)
 STATUS_NAMES = {0: "ASX_OK", 1: "ASX_EINVAL", 2: "ASX_ENOMEM", 3: "ASX_ECUDA", 4: "ASX_ESTATE",
-                5: "ASX_ENUMERIC", 6: "ASX_ETIMEOUT"}
+                5: "ASX_ENUMERIC", 6: "ASX_ETIMEOUT", 7: "ASX_EBOUNDS"}
 ASX_BC_WALL, ASX_BC_FREE = 0, 1
 ASX_SIDE_W, ASX_SIDE_E, ASX_SIDE_S, ASX_SIDE_N = 0, 1, 2, 3
 ASX_PTR_HOST, ASX_PTR_DEVICE = 0, 1

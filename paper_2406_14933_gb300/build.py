@@ -77,5 +77,31 @@ def build(force: bool = False, verbose: bool = False) -> str:
     return LIB
 
 
+LIB_CHECKED = os.path.join(BUILD, "libasx_bounds.so")
+
+
+def build_checked() -> str:
+    """The bounds-checked debug build ``libasx_bounds.so``: the step kernel compiled with
+    ``-DASX_BOUNDS_CHECK`` (every shared-memory ring index and global store of its tiles
+    checked; a violation is reported as ASX_EBOUNDS and the access skipped), linked with
+    the ordinary objects.  Builds the ordinary library first; returns the path."""
+    build()
+    src = os.path.join(CSRC, "step_strip.cu")
+    obj = os.path.join(BUILD, "step_strip_bounds.cu.o")
+    r = subprocess.run([_nvcc(), *ARCH, *NVFLAGS, "-DASX_BOUNDS_CHECK", "-c", src, "-o", obj],
+                       capture_output=True, text=True)
+    if r.returncode != 0:
+        raise RuntimeError(f"nvcc failed on {src} (bounds-checked):\n{r.stderr}")
+    objs = [obj] + [os.path.join(BUILD, os.path.basename(s) + ".o") for s in _sources()
+                    if os.path.basename(s) != "step_strip.cu"]
+    tmp = LIB_CHECKED + f".tmp{os.getpid()}"
+    r = subprocess.run([_nvcc(), *ARCH, "-shared", "-o", tmp, *objs, "-cudart", "static"], capture_output=True,
+                       text=True)
+    if r.returncode != 0:
+        raise RuntimeError(f"link failed (bounds-checked):\n{r.stderr}")
+    os.replace(tmp, LIB_CHECKED)
+    return LIB_CHECKED
+
+
 if __name__ == "__main__":
     print(build(force=True, verbose=True))

@@ -62,6 +62,7 @@ struct DevCtl {
 
 constexpr int kErrNumeric = 1;
 constexpr int kErrTimeout = 2;
+constexpr int kErrBounds = 4;     // bounds-checked build (ASX_BOUNDS_CHECK): an index left its buffer
 
 // Every spin-wait of the kernels (on an mbarrier phase) gives up after this long and
 // reports kErrTimeout: copies and products complete in microseconds.

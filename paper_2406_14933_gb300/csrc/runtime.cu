@@ -205,6 +205,7 @@ asx_status check_numeric(asx_raster *r, const DevCtl *h)
     if (h->err & kErrNumeric)
         return fail(r, ASX_ENUMERIC, "the state became non-finite at step " + std::to_string(h->step));
     if (h->err & kErrTimeout) return fail(r, ASX_ETIMEOUT, "a bounded wait in a kernel ran out");
+    if (h->err & kErrBounds) return fail(r, ASX_EBOUNDS, "an index outside its buffer (bounds-checked build)");
     return ASX_OK;
 }
 

@@ -79,6 +79,26 @@ struct StripSmem {
     unsigned long long bar[kNC];
 };
 
+// ----------------------------------------------------------------- bounds checks
+//
+// The bounds-checked debug build (-DASX_BOUNDS_CHECK, `build.build_checked`) tests every
+// shared-memory ring index and global store of the tile code: an index outside its buffer
+// sets kErrBounds in the step's error word (reported as ASX_EBOUNDS) and the access is
+// skipped or redirected to element 0.  The ordinary build compiles no check.
+#ifdef ASX_BOUNDS_CHECK
+__device__ __forceinline__ bool in_bounds(const StepArgs &a, long long i, long long n)
+{
+    if (i >= 0 && i < n) return true;
+    atomicOr(&a.ctl->err, kErrBounds);
+    return false;
+}
+#define ASX_RING(a, i, n) (in_bounds((a), (i), (n)) ? (i) : 0)
+#define ASX_STORE_OK(a, i, n) in_bounds((a), (i), (n))
+#else
+#define ASX_RING(a, i, n) (i)
+#define ASX_STORE_OK(a, i, n) true
+#endif
+
 // ----------------------------------------------------------------- PTX wrappers
 
 __device__ __forceinline__ unsigned smem_u32(const void *p)
@@ -452,6 +472,7 @@ struct Tile {
     {
         const Chunk<CLS> &ch = S.ring[(jr / kRB) % kNC];
         const int rr = jr % kRB;
+        x = ASX_RING(a, x, kBXF - kHalf);
         PCell c;
         c.m = make_float2(ch.mhi.v[rr][x], ch.mhi.v[rr][x + kHalf]);
         c.v1 = make_float2(ch.v1.v[rr][x], ch.v1.v[rr][x + kHalf]);
@@ -472,7 +493,7 @@ struct Tile {
     {
         const int rr = jr % kRB;
         const Chunk<CLS> &ch = arrive(jr);
-        const int x = kXO + 2 * lane, xl = 2 * lane;
+        const int x = ASX_RING(a, kXO + 2 * lane, kBXF - kHalf - 1), xl = ASX_RING(a, 2 * lane, kSW - kHalf - 1);
 #pragma unroll
         for (int e = 0; e < 2; e++) {
             PCell &P = R.X[e];
@@ -559,6 +580,9 @@ struct Tile {
                                          a.h_dry, cll, clr);
         }
         const size_t k0 = (size_t)r * a.pitch + c0 + 2 * lane;
+        const long long nplane = (long long)a.rows * a.pitch;
+        if (!ASX_STORE_OK(a, (long long)k0 + kHalf + 1, nplane) || !ASX_STORE_OK(a, c0 + 2 * lane + kHalf + 1, a.cols))
+            return;
         if (own_l) {
             if (cll.hi != 0.0f || cll.lo != 0.0f) {
                 clq.add(cll.hi);

@@ -3,7 +3,7 @@
 A small MLP stands in for whole hillslope runs: from a scenario's slope, vegetation cover,
 porosity, plant drag and its hyetograph it predicts the outlet hydrograph.  It is trained
 on hydrographs the solver itself produces (the hillslope ensemble of Sec. 2 scenarios run
-to 6400 s), and the solver remains its judge: at serving time a sample of the queries is
+to 6400 s), and the solver remains the reference: at serving time a sample of the queries is
 re-solved, their error measured, and the solver's hydrograph replaces the surrogate's
 wherever the relative L2 error exceeds the tolerance.
 

@@ -12,6 +12,7 @@ flume keeps sloshing; with it the depths settle geometrically), run to a steady 
   environments p = (q, theta_v, m), all grids in one ensemble;
 * ``chi``: the root-mean-square gauge-depth misfit over experiments and gauges
   (Eq. eq_chi_6experim);
+* ``chi_surfaces``: chi over the grid for the experiment subsets (cases I-IV) of Sec. 4.3;
 * ``hooke_jeeves``: Hooke and Jeeves' pattern search (exploratory moves coordinate by
   coordinate, pattern moves, step halving).  Each exploratory move evaluates the 3 x 3
   stencil around its base point in one batch, which holds every point the sequential
@@ -162,6 +163,27 @@ def synthetic_gauges(study: FlumeStudy, alpha_s: float, alpha_p: float) -> np.nd
     """Stand-in for the flume measurements: the solver's own gauge depths at known
     coefficients, [experiments, gauges]."""
     return simulate_gauges(study, [(alpha_s, alpha_p)])[0]
+
+
+# The experiment subsets of Sec. 4.3, as indices into inputs.FLUME["q"]: one experiment
+# (layout 1, 15 l/s), the three of layout 1, the three of layout 2, all six.
+CASES = {"I": (1,), "II": (0, 1, 2), "III": (3, 4, 5), "IV": (0, 1, 2, 3, 4, 5)}
+
+
+def chi_surfaces(study: FlumeStudy, h_exp: np.ndarray, ns: int = GRID[0], np_: int = GRID[1], box=LAMBDA,
+                 cases=CASES) -> dict:
+    """chi over the (alpha_s, alpha_p) grid for each case of Sec. 4.3: every grid point and
+    experiment in one ensemble, each case's surface from its subset of experiments.
+    h_exp: [experiments, gauges] for study.experiments."""
+    a_s, a_p = grid_points(ns, np_, box)
+    g = simulate_gauges(study, [(s, p) for s in a_s for p in a_p])          # [points, experiments, gauges]
+    out = {}
+    for name, idx in cases.items():
+        idx = list(idx)
+        chi_grid = np.array([chi(h_exp[idx], gi[idx]) for gi in g]).reshape(ns, np_)
+        i, j = np.unravel_index(np.argmin(chi_grid), chi_grid.shape)
+        out[name] = dict(chi=chi_grid, argmin=(float(a_s[i]), float(a_p[j])), min=float(chi_grid[i, j]))
+    return dict(alpha_s=a_s, alpha_p=a_p, cases=out)
 
 
 @dataclass

@@ -135,3 +135,22 @@ def test_sensitivity_sweep_over_environments(asx):
     assert np.array_equal(alone["h_bar"], res[0]["h_bar"])
     for r in res:
         print(f"[sweep] {r['env']}: delta_s {r['delta_s']:.4g} m, delta_p {r['delta_p']:.4g} m")
+
+
+def test_chi_surfaces_of_the_four_cases(asx):
+    """chi over the 21 x 26 grid for the experiment subsets of Sec. 4.3 (I: one experiment,
+    II / III: the three of one vegetation layout, IV: all six), gauges made by the solver at
+    (0.00709, 73.39): the grid minimum of case IV lies within one grid step of that pair.
+    The size of each case's low-misfit region (chi below twice the grid's lowest value plus
+    0.1 mm) is printed: the paper finds one experiment locates the minimum poorly and all
+    six best."""
+    study = C.FlumeStudy(l=0.2, t_end=400.0)
+    truth = (0.00709, 73.39)
+    h_exp = C.synthetic_gauges(study, *truth)
+    r = C.chi_surfaces(study, h_exp)
+    ds, dp = r["alpha_s"][1] - r["alpha_s"][0], r["alpha_p"][1] - r["alpha_p"][0]
+    am = r["cases"]["IV"]["argmin"]
+    assert abs(am[0] - truth[0]) <= ds * 1.0001 and abs(am[1] - truth[1]) <= dp * 1.0001
+    for name, c in r["cases"].items():
+        low = int((c["chi"] <= 2.0 * c["min"] + 1e-4).sum())
+        print(f"[cases] {name}: grid minimum {c['min'] * 1e3:.3f} mm at {c['argmin']}, {low} of 546 points low")

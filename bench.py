@@ -18,6 +18,7 @@ import argparse
 import json
 import math
 import os
+import platform
 import subprocess
 import sys
 import threading
@@ -288,7 +289,28 @@ def cpu_baseline(sc, budget_s=15.0, crop=REF_CROP):
     el = time.perf_counter() - w0
     return {"value": crop * crop * steps / el, "unit": UNIT, "cores": 1, "kind": "oracle",
             "sample": f"{steps} oracle steps of a {crop}x{crop} crop of the catchment "
-                      f"(5 mm film from t={T_WARM:.0f} s), {el:.1f} s, single thread"}
+                      f"(5 mm film from t={T_WARM:.0f} s), {el:.1f} s, single thread",
+            "host": host_info()}
+
+
+def host_info():
+    """CPU model and the cores this process may run on."""
+    model = platform.processor() or platform.machine()
+    try:
+        with open("/proc/cpuinfo") as f:
+            for line in f:
+                key = line.split(":")[0].strip().lower()
+                if key in ("model name", "cpu part", "hardware") and ":" in line:
+                    model = line.split(":", 1)[1].strip()
+                    if key == "model name":
+                        break
+    except OSError:
+        pass
+    try:
+        n = len(os.sched_getaffinity(0))
+    except AttributeError:
+        n = os.cpu_count() or 1
+    return {"cpu": model, "machine": platform.machine(), "cores_available": n}
 
 
 def run_ensemble(args, stream):
@@ -475,7 +497,8 @@ def run_reference(args):
             "data": "synthetic", "config": cfg,
             "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
                              "sample": f"{args.steps} oracle steps of a {crop}x{crop} crop "
-                                       f"(5 mm film from t={T_WARM:.0f} s), single thread"},
+                                       f"(5 mm film from t={T_WARM:.0f} s), single thread",
+                             "host": host_info()},
             "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
 
 

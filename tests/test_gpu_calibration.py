@@ -101,7 +101,7 @@ def test_sensitivity_full_grid(asx):
     hs = C.steady_depths(longer, scs)
     for (i, j), h, sc in zip([(0, 0), (0, -1), (-1, 0), (-1, -1)], hs, scs):
         assert abs(C.h_bar(h, sc) - r["h_bar"][i, j]) < 1e-5
-    print(f"[sensitivity] 21x26 grid: delta_s {r['delta_s']:.4g} m, delta_p {r['delta_p']:.4g} m s, "
+    print(f"[sensitivity] 21x26 grid: delta_s {r['delta_s']:.4g} m, delta_p {r['delta_p']:.4g} m^2, "
           f"{study.runs} runs in {study.seconds:.2f} s")
 
 
@@ -134,7 +134,7 @@ def test_sensitivity_sweep_over_environments(asx):
     alone = C.sensitivity_grid(C.FlumeStudy(l=0.2, t_end=300.0), 1, 0.015, ns=5, np_=5)
     assert np.array_equal(alone["h_bar"], res[0]["h_bar"])
     for r in res:
-        print(f"[sweep] {r['env']}: delta_s {r['delta_s']:.4g} m, delta_p {r['delta_p']:.4g} m")
+        print(f"[sweep] {r['env']}: delta_s {r['delta_s']:.4g} m, delta_p {r['delta_p']:.4g} m^2")
 
 
 def test_chi_surfaces_of_the_four_cases(asx):

@@ -127,7 +127,8 @@ def _workload_config(sc, k, t_warm=T_WARM):
     return {"workload": f"carved catchment {sc.rows}x{sc.cols} hex, edge {sc.l:g} m, "
                         f"3 land-cover classes, double-peak storm, window from t={t_warm:.0f} s",
             "cells": sc.n, "rows": sc.rows, "cols": sc.cols, "steps_timed": k,
-            "l2": "state 0.74 GB > 129 MB L2 (no flush needed)", "parallelism": "replicas"}
+            "l2": f"device state {sc.n * 37 / 1e9:.2f} GB (8 state planes, bed, classes) > 129 MB L2 "
+                  "(no flush needed)", "parallelism": "replicas"}
 
 
 def run_cuda(args):

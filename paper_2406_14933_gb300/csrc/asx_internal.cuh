@@ -107,6 +107,7 @@ struct StepArgs {
     float l;                           // edge length
     float g;                           // gravity
     float cpe[3][2];                   // -1/2 l g n for owned directions E, NE, NW
+    float cpm[3][2];                   // -4 g n: cpe in the strip kernel's momentum unit l/8
     // boundaries
     int bc[4], fb[4], fe[4];
     int visc;                          // 1: artificial viscosity on interior edges

@@ -426,6 +426,8 @@ asx_status asx_set_params(asx_raster *r, const asx_params *p)
     for (int d = 0; d < 3; d++) {
         a.cpe[d][0] = (float)(-0.5 * l * p->g * n1[d]);
         a.cpe[d][1] = (float)(-0.5 * l * p->g * n2[d]);
+        a.cpm[d][0] = (float)(-4.0 * p->g * n1[d]);
+        a.cpm[d][1] = (float)(-4.0 * p->g * n2[d]);
     }
     asx_status st = set_device(r);
     if (st) return st;

@@ -28,7 +28,9 @@
 //     cell's six neighbours (the same per-cell code as the gather kernel).
 // Both cells of an edge accumulate the mass increment of the same canonical edge
 // function, bit for bit the increment the scalar code of the frame computes, so opposite
-// increments are identical and the water budget closes to float64 rounding.
+// increments are identical and the water budget closes to float64 rounding.  The edge
+// code works with the normal component scaled by +-2 (exact) and keeps the momentum sums
+// in units of l/8, which saves a multiply and two constants per diagonal edge.
 #include <cuda.h>
 
 #include <type_traits>
@@ -245,49 +247,75 @@ __device__ __forceinline__ Cell half_cell(const PCell &P, int s)
 
 // Edge (X lower, Y upper) in direction D for both halves of the pairs, the terms of
 // edge_core component by component; adds them to ax if ux and to ay if uy (a side not
-// used belongs to another lane or is not updated by this tile).  The pressure term c dh
-// enters each momentum sum through one fused multiply-add; with EXT and a.visc the
-// artificial viscosity adds t (v_Y - v_X) to X and t (v_X - v_Y) to Y.
+// used belongs to another lane or is not updated by this tile).
+//
+// Scaled form.  u = 2 v_n for E and NE, u = -2 v_n for NW, where v_n is edge_core's
+// normal component (itself twice the interface velocity's): scaling by a power of two is
+// exact, so G = mu u is exactly +-2 edge_core's G and q = (kl2 / 2) G is exactly +-q of
+// edge_core, the same bits in every normal-range case (a normal component or flux below
+// 2^-126 may differ in its last subnormal bit, a mass of order 1e-45 of the cell's).  A
+// NW edge's negative q enters the sums with the opposite operation (acc_add2(x) has the
+// bits of acc_sub2(-x)).  The momentum sums are kept in units of l/8, so the flux terms
+// are G s without a factor and the pressure coefficients are a.cpm = -4 g n; the cell
+// update multiplies them by dt/sigma * l/8.  With EXT and a.visc the artificial viscosity
+// adds t (v_Y - v_X) to X and t (v_X - v_Y) to Y, t scaled by vs = 8/l.
 template <int D, bool EXT>
-__device__ __forceinline__ void edge(const StepArgs &a, const PCell &X, const PCell &Y, float2 kl2, float2 l4,
+__device__ __forceinline__ void edge(const StepArgs &a, const PCell &X, const PCell &Y, float2 kh, float vs,
                                       PAcc &ax, bool ux, PAcc &ay, bool uy)
 {
+    constexpr float kSgn = D == 2 ? -1.0f : 1.0f;
     const float2 s1 = add2(X.v1, Y.v1), s2 = add2(X.v2, Y.v2);
-    float2 vn2;
-    if (D == 0) vn2 = s1;
-    else if (D == 1) vn2 = fma2(dup2(kS32), s2, mul2(dup2(0.5f), s1));
-    else vn2 = fma2(dup2(kS32), s2, mul2(dup2(-0.5f), s1));
+    float2 u;
+    if (D == 0) u = add2(s1, s1);
+    else u = fma2(dup2(kSgn * 2.0f * kS32), s2, s1);
     const float2 dw = add2(sub2(Y.z, X.z), sub2(Y.h, X.h));
     // the upwind side is the sign of v_n, or at v_n = 0 that of -dw
-    const float kx = vn2.x != 0.0f ? vn2.x : -dw.x, ky = vn2.y != 0.0f ? vn2.y : -dw.y;
     float2 mu;
-    mu.x = kx > 0.0f ? X.m.x : Y.m.x;
-    mu.y = ky > 0.0f ? X.m.y : Y.m.y;
-    const float2 G = mul2(mu, vn2);
-    // q = kl2 G as fma(kl2, G, +0): the same bits as the product (but for the sign of a
+    if (D != 2) {
+        const float kx = u.x != 0.0f ? u.x : -dw.x, ky = u.y != 0.0f ? u.y : -dw.y;
+        mu.x = kx > 0.0f ? X.m.x : Y.m.x;
+        mu.y = ky > 0.0f ? X.m.y : Y.m.y;
+    } else {
+        const float kx = u.x != 0.0f ? u.x : dw.x, ky = u.y != 0.0f ? u.y : dw.y;
+        mu.x = kx < 0.0f ? X.m.x : Y.m.x;
+        mu.y = ky < 0.0f ? X.m.y : Y.m.y;
+    }
+    const float2 G = mul2(mu, u);
+    // q = kh G as fma(kh, G, +0): the same bits as the product (but for the sign of a
     // zero, which moves no mass), and an instruction the code generator cannot fuse into
     // the two-sums that consume q, as it was seen to do with a plain packed multiply
-    const float2 q = fma2(kl2, G, dup2(0.0f));
-    const float2 gl = mul2(l4, G);
-    const float2 f1 = mul2(gl, s1), f2 = mul2(gl, s2);
+    const float2 q = fma2(kh, G, dup2(0.0f));
+    const float2 f1 = mul2(G, s1), f2 = mul2(G, s2);
     const float2 dh = mul2(dw, mu);
     // an E edge's normal has no second component: its pressure term leaves m2 as it is
-    const float2 c1 = dup2(a.cpe[D][0]), c2 = dup2(a.cpe[D][1]);
+    const float2 c1 = dup2(a.cpm[D][0]), c2 = dup2(a.cpm[D][1]);
     if (ux) {
-        acc_sub2(ax.hi, ax.lo, q);
-        ax.m1 = sub2(fma2(c1, dh, ax.m1), f1);
-        ax.m2 = sub2(D == 0 ? ax.m2 : fma2(c2, dh, ax.m2), f2);
+        if (D != 2) {
+            acc_sub2(ax.hi, ax.lo, q);
+            ax.m1 = sub2(fma2(c1, dh, ax.m1), f1);
+            ax.m2 = sub2(D == 0 ? ax.m2 : fma2(c2, dh, ax.m2), f2);
+        } else {
+            acc_add2(ax.hi, ax.lo, q);
+            ax.m1 = add2(fma2(c1, dh, ax.m1), f1);
+            ax.m2 = add2(fma2(c2, dh, ax.m2), f2);
+        }
     }
     if (uy) {
-        acc_add2(ay.hi, ay.lo, q);
-        ay.m1 = add2(fma2(c1, dh, ay.m1), f1);
-        ay.m2 = add2(D == 0 ? ay.m2 : fma2(c2, dh, ay.m2), f2);
+        if (D != 2) {
+            acc_add2(ay.hi, ay.lo, q);
+            ay.m1 = add2(fma2(c1, dh, ay.m1), f1);
+            ay.m2 = add2(D == 0 ? ay.m2 : fma2(c2, dh, ay.m2), f2);
+        } else {
+            acc_sub2(ay.hi, ay.lo, q);
+            ay.m1 = sub2(fma2(c1, dh, ay.m1), f1);
+            ay.m2 = sub2(fma2(c2, dh, ay.m2), f2);
+        }
     }
     if (EXT && a.visc) {
 #pragma unroll
         for (int s = 0; s < 2; s++) {
             const Cell Xs = half_cell(X, s), Ys = half_cell(Y, s);
-            const float t = visc_coef(Xs, Ys, a.l, a.g);
+            const float t = __fmul_rn(visc_coef(Xs, Ys, a.l, a.g), vs);
             const float d1 = __fsub_rn(Ys.v1, Xs.v1), d2 = __fsub_rn(Ys.v2, Xs.v2);
             if (ux) {
                 comp(ax.m1, s) = __fmaf_rn(t, d1, comp(ax.m1, s));
@@ -321,6 +349,7 @@ __device__ __forceinline__ void tiny_den(float den, float g1, float g2, float &w
     }
 }
 
+// kappa: dt / sigma times the momentum sums' unit l/8 (see edge)
 template <bool EXT>
 __device__ __forceinline__ CellNew2 cell_update_pair(float2 shi, float2 slo, float2 M1, float2 M2, float2 m_old,
                                                  float2 v1_old, float2 v2_old, float2 rth, float2 ka, float2 kb,
@@ -525,33 +554,34 @@ struct Tile {
     template <int ODD>
     __device__ __forceinline__ void edges(int j, PRow &C, PRow &N)
     {
-        const float2 k2 = dup2(kl2), l4 = dup2(0.25f * a.l);
+        const float2 kh = dup2(0.5f * kl2);     // the scaled form's kl2 / 2
+        const float vs = 8.0f / a.l;            // the momentum unit's inverse
         // the cells west and east of this lane's two, read from the ring (the same
         // values, hence the same h, as the neighbouring lanes' own cells)
         const int xw = kXO + 2 * lane - 1, xe = kXO + 2 * lane + 2;
         const PCell Wc = ring_pair(j, xw), Ec = ring_pair(j, xe);
         // ---- east edges of row r (the west edge of c_0 is the west lane's, again)
-        edge<0, EXT>(a, Wc, C.X[0], k2, l4, C.A[0], false, C.A[0], true);
-        edge<0, EXT>(a, C.X[0], C.X[1], k2, l4, C.A[0], true, C.A[1], true);
-        edge<0, EXT>(a, C.X[1], Ec, k2, l4, C.A[1], true, C.A[1], false);
+        edge<0, EXT>(a, Wc, C.X[0], kh, vs, C.A[0], false, C.A[0], true);
+        edge<0, EXT>(a, C.X[0], C.X[1], kh, vs, C.A[0], true, C.A[1], true);
+        edge<0, EXT>(a, C.X[1], Ec, kh, vs, C.A[1], true, C.A[1], false);
         if (ODD) {
             // odd r: NE(c) = (r+1, c+1), NW(c) = (r+1, c)
             const PCell On = ring_pair(j + 1, xe);                                // (r+1, c_1 + 1)
-            edge<2, EXT>(a, C.X[0], N.X[0], k2, l4, C.A[0], true, N.A[0], true);   // NW
-            edge<1, EXT>(a, C.X[0], N.X[1], k2, l4, C.A[0], true, N.A[1], true);   // NE
-            edge<2, EXT>(a, C.X[1], N.X[1], k2, l4, C.A[1], true, N.A[1], true);   // NW
-            edge<1, EXT>(a, C.X[1], On, k2, l4, C.A[1], true, C.A[1], false);      // NE
+            edge<2, EXT>(a, C.X[0], N.X[0], kh, vs, C.A[0], true, N.A[0], true);   // NW
+            edge<1, EXT>(a, C.X[0], N.X[1], kh, vs, C.A[0], true, N.A[1], true);   // NE
+            edge<2, EXT>(a, C.X[1], N.X[1], kh, vs, C.A[1], true, N.A[1], true);   // NW
+            edge<1, EXT>(a, C.X[1], On, kh, vs, C.A[1], true, C.A[1], false);      // NE
             // SW edge of (r+1, c_0): the NE edge of (r, c_0 - 1)
-            edge<1, EXT>(a, Wc, N.X[0], k2, l4, N.A[0], false, N.A[0], true);
+            edge<1, EXT>(a, Wc, N.X[0], kh, vs, N.A[0], false, N.A[0], true);
         } else {
             // even r: NE(c) = (r+1, c), NW(c) = (r+1, c-1)
             const PCell On = ring_pair(j + 1, xw);                                // (r+1, c_0 - 1)
-            edge<1, EXT>(a, C.X[0], N.X[0], k2, l4, C.A[0], true, N.A[0], true);   // NE
-            edge<2, EXT>(a, C.X[0], On, k2, l4, C.A[0], true, C.A[0], false);      // NW
-            edge<1, EXT>(a, C.X[1], N.X[1], k2, l4, C.A[1], true, N.A[1], true);   // NE
-            edge<2, EXT>(a, C.X[1], N.X[0], k2, l4, C.A[1], true, N.A[0], true);   // NW
+            edge<1, EXT>(a, C.X[0], N.X[0], kh, vs, C.A[0], true, N.A[0], true);   // NE
+            edge<2, EXT>(a, C.X[0], On, kh, vs, C.A[0], true, C.A[0], false);      // NW
+            edge<1, EXT>(a, C.X[1], N.X[1], kh, vs, C.A[1], true, N.A[1], true);   // NE
+            edge<2, EXT>(a, C.X[1], N.X[0], kh, vs, C.A[1], true, N.A[0], true);   // NW
             // SE edge of (r+1, c_1): the NW edge of (r, c_1 + 1)
-            edge<2, EXT>(a, Ec, N.X[1], k2, l4, N.A[1], false, N.A[1], true);
+            edge<2, EXT>(a, Ec, N.X[1], kh, vs, N.A[1], false, N.A[1], true);
         }
     }
 
@@ -576,7 +606,7 @@ struct Tile {
                 kb = mul2(t, dup2(a.alpha_s));
             }
             o[e] = cell_update_pair<EXT>(C.A[e].hi, C.A[e].lo, C.A[e].m1, C.A[e].m2, C.X[e].m, C.X[e].v1,
-                                         C.X[e].v2, rt, ka, kb, kappa, qr, dtf, a.g, __fmul_rn(dtf, a.tau),
+                                         C.X[e].v2, rt, ka, kb, kappa * (0.125f * a.l), qr, dtf, a.g, __fmul_rn(dtf, a.tau),
                                          a.h_dry, cll, clr);
         }
         const size_t k0 = (size_t)r * a.pitch + c0 + 2 * lane;

@@ -30,7 +30,11 @@
 // function, bit for bit the increment the scalar code of the frame computes, so opposite
 // increments are identical and the water budget closes to float64 rounding.  The edge
 // code works with the normal component scaled by +-2 (exact) and keeps the momentum sums
-// in units of l/8, which saves a multiply and two constants per diagonal edge.
+// in units of l/8, which saves a multiply and two constants per diagonal edge.  The cell
+// update of a row runs without branches (cell_update_fast) for both pairs, so the code
+// generator can interleave their long dependency chains; a clamp, a vanishing momentum or
+// friction denominator, or a NaN sends the pair through the full update with its
+// branches, which gives the same bits in every other case.
 #include <cuda.h>
 
 #include <type_traits>
@@ -404,6 +408,52 @@ __device__ __forceinline__ CellNew2 cell_update_pair(float2 shi, float2 slo, flo
     return o;
 }
 
+// The common case of cell_update_pair without its branches: the same operations, hence
+// the same bits, whenever no component is clamped (m < 0), has a momentum norm below
+// 1e-18 or a friction denominator at or below 1e-30; rare is set when one of those (or a
+// NaN) occurs, and the caller then recomputes the pair with cell_update_pair.
+template <bool EXT>
+__device__ __forceinline__ CellNew2 cell_update_fast(float2 shi, float2 slo, float2 M1, float2 M2, float2 m_old,
+                                                 float2 v1_old, float2 v2_old, float2 rth, float2 ka, float2 kb,
+                                                 float kappa, float qr, float dtf, float g, float dtau,
+                                                 float h_dry, bool &rare)
+{
+    CellNew2 o;
+    acc_add2(shi, slo, dup2(qr));
+    float2 hi, lo;
+    two_sum2(shi, slo, hi, lo);
+    const bool clx = hi.x < 0.0f || (hi.x == 0.0f && lo.x < 0.0f);
+    const bool cly = hi.y < 0.0f || (hi.y == 0.0f && lo.y < 0.0f);
+    const float2 g1 = fma2(dup2(kappa), M1, mul2(m_old, v1_old));
+    const float2 g2 = fma2(dup2(kappa), M2, mul2(m_old, v2_old));
+    const float2 h = mul2(hi, rth);
+    const float2 beta = mul2(dup2(dtf), fma2(ka, h, kb));
+    const float2 nq = fma2(g1, g1, mul2(g2, g2));
+    const float2 ng = make_float2(fast_sqrt(nq.x), fast_sqrt(nq.y));
+    float2 ap = hi;
+    if constexpr (EXT) ap = fma2(dup2(dtau), h, hi);
+    const float2 rad = fma2(ap, ap, mul2(mul2(dup2(4.0f), beta), ng));
+    const float2 den = add2(ap, make_float2(fast_sqrt(rad.x), fast_sqrt(rad.y)));
+    const float2 inv2 = mul2(dup2(2.0f), make_float2(fast_rcp(den.x), fast_rcp(den.y)));
+    float2 w1 = mul2(g1, inv2), w2 = mul2(g2, inv2);
+    if constexpr (EXT) {
+        if (h.x < h_dry) w1.x = w2.x = 0.0f;
+        if (h.y < h_dry) w1.y = w2.y = 0.0f;
+    }
+    rare = clx || cly || !(nq.x >= 1.0e-36f) || !(nq.y >= 1.0e-36f) || !(den.x > 1.0e-30f) ||
+           !(den.y > 1.0e-30f);
+    o.hi = hi;
+    o.lo = lo;
+    o.v1 = w1;
+    o.v2 = w2;
+    const float2 sp = fma2(w1, w1, mul2(w2, w2));
+    const float2 gh = mul2(dup2(g), h);
+    const float2 c = add2(make_float2(fast_sqrt(sp.x), fast_sqrt(sp.y)), make_float2(fast_sqrt(gh.x), fast_sqrt(gh.y)));
+    o.cb0 = speed_bits(c.x);
+    o.cb1 = speed_bits(c.y);
+    return o;
+}
+
 struct PRow {
     PCell X[2];
     float2 th[2];     // porosity theta, or in class mode the class ids' bits
@@ -590,24 +640,27 @@ struct Tile {
     __device__ __forceinline__ void finish(int r, PRow &C)
     {
         CellNew2 o[2];
-        FF cll, clr;
+        bool rare[2];
+        const float km = kappa * (0.125f * a.l), dtau = __fmul_rn(dtf, a.tau);
 #pragma unroll
         for (int e = 0; e < 2; e++) {
             float2 rt, ka, kb;
-            if constexpr (CLS) {
-                const int il = __float_as_int(C.th[e].x), ir = __float_as_int(C.th[e].y);
-                rt = make_float2(cls[0][il], cls[0][ir]);
-                ka = make_float2(cls[1][il], cls[1][ir]);
-                kb = make_float2(cls[2][il], cls[2][ir]);
-            } else {
-                const float2 t = C.th[e];
-                rt = make_float2(fast_rcp(t.x), fast_rcp(t.y));
-                ka = mul2(dup2(a.alpha_p), sub2(dup2(1.0f), t));
-                kb = mul2(t, dup2(a.alpha_s));
+            coeffs(C, e, rt, ka, kb);
+            o[e] = cell_update_fast<EXT>(C.A[e].hi, C.A[e].lo, C.A[e].m1, C.A[e].m2, C.X[e].m, C.X[e].v1,
+                                         C.X[e].v2, rt, ka, kb, km, qr, dtf, a.g, dtau, a.h_dry, rare[e]);
+        }
+        FF cll, clr;
+        if (rare[0] || rare[1]) {
+            // a clamp, a vanishing momentum or friction denominator, or a NaN: the full
+            // update with its branches, for the pair(s) concerned
+#pragma unroll
+            for (int e = 0; e < 2; e++) {
+                if (!rare[e]) continue;
+                float2 rt, ka, kb;
+                coeffs(C, e, rt, ka, kb);
+                o[e] = cell_update_pair<EXT>(C.A[e].hi, C.A[e].lo, C.A[e].m1, C.A[e].m2, C.X[e].m, C.X[e].v1,
+                                             C.X[e].v2, rt, ka, kb, km, qr, dtf, a.g, dtau, a.h_dry, cll, clr);
             }
-            o[e] = cell_update_pair<EXT>(C.A[e].hi, C.A[e].lo, C.A[e].m1, C.A[e].m2, C.X[e].m, C.X[e].v1,
-                                         C.X[e].v2, rt, ka, kb, kappa * (0.125f * a.l), qr, dtf, a.g, __fmul_rn(dtf, a.tau),
-                                         a.h_dry, cll, clr);
         }
         const size_t k0 = (size_t)r * a.pitch + c0 + 2 * lane;
         const long long nplane = (long long)a.rows * a.pitch;
@@ -634,6 +687,22 @@ struct Tile {
             *reinterpret_cast<float2 *>(a.v1[np] + k0 + kHalf) = make_float2(o[0].v1.y, o[1].v1.y);
             *reinterpret_cast<float2 *>(a.v2[np] + k0 + kHalf) = make_float2(o[0].v2.y, o[1].v2.y);
             cwb = max(cwb, max(o[0].cb1, o[1].cb1));
+        }
+    }
+
+    // Porosity terms of pair e of row C: 1/theta, alpha_p (1 - theta), theta alpha_s.
+    __device__ __forceinline__ void coeffs(const PRow &C, int e, float2 &rt, float2 &ka, float2 &kb) const
+    {
+        if constexpr (CLS) {
+            const int il = __float_as_int(C.th[e].x), ir = __float_as_int(C.th[e].y);
+            rt = make_float2(cls[0][il], cls[0][ir]);
+            ka = make_float2(cls[1][il], cls[1][ir]);
+            kb = make_float2(cls[2][il], cls[2][ir]);
+        } else {
+            const float2 t = C.th[e];
+            rt = make_float2(fast_rcp(t.x), fast_rcp(t.y));
+            ka = mul2(dup2(a.alpha_p), sub2(dup2(1.0f), t));
+            kb = mul2(t, dup2(a.alpha_s));
         }
     }
 

@@ -366,7 +366,7 @@ asx_status efail(asx_ensemble *e, asx_status st, const std::string &m)
 
 bool tuning_valid(const asx_ensemble_tuning &t)
 {
-    const bool c = t.cluster == 1 || t.cluster == 2 || t.cluster == 4 || t.cluster == 8;
+    const bool c = t.cluster == 1 || t.cluster == 2 || t.cluster == 4 || t.cluster == kEnsMaxCluster;
     const bool n = t.threads == 128 || t.threads == 256 || t.threads == 512;
     const bool k = t.cells_per_thread == 1 || t.cells_per_thread == 2 || t.cells_per_thread == 4;
     return c && n && k;

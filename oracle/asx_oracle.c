@@ -48,13 +48,20 @@
  *   - dt_n = min(dt_max, CFL phi / c_max^n) (dt_max if c_max = 0), cut so that a
  *     step never passes t_end or the next hydrograph sample time.
  *
- * Everything is double precision, single-threaded, one cell at a time, each
- * operator summed over the neighbours of the cell exactly as written.
+ * Everything is double precision, one cell at a time, each operator summed over the
+ * neighbours of the cell exactly as written.  Built plainly the file is single-threaded;
+ * built with OpenMP (-fopenmp) the rows of a step are shared among threads.  A cell's
+ * update reads only the state at t^n and writes only its own outputs, and the step's
+ * outflow and clamp sums are formed after the cell loop, cell by cell in row-major
+ * order as the single-threaded loop adds them, so both builds give the same bits.
  */
 #include <math.h>
 #include <stddef.h>
 #include <stdlib.h>
 #include <string.h>
+#ifdef _OPENMP
+#include <omp.h>
+#endif
 
 #define ORC_W 0
 #define ORC_E 1
@@ -146,6 +153,19 @@ double orc_sigma(double l) { return 1.5 * sqrt(3.0) * l * l; }
 /* phi = sigma_i / sum_j l_(i,j) with all six sides of the cell (Eq. fvm_2D_eq_frac.13). */
 double orc_phi(double l) { return orc_sigma(l) / (6.0 * l); }
 
+/* Threads the cell loops use: sets the count when n > 0, returns the count in force
+ * (always 1 in the single-threaded build). */
+int orc_threads(int n)
+{
+#ifdef _OPENMP
+    if (n > 0) omp_set_num_threads(n);
+    return omp_get_max_threads();
+#else
+    (void)n;
+    return 1;
+#endif
+}
+
 /* ---------------- forcing ---------------- */
 
 /* Piecewise-linear hyetograph r(t), zero outside [t_0, t_last] (Appendix C gives the
@@ -198,6 +218,9 @@ double orc_cmax(const orc_problem *p, const double *m, const double *v1, const d
 {
     int n = p->rows * p->cols, i;
     double cmax = 0.0;
+#ifdef _OPENMP
+#pragma omp parallel for schedule(static) reduction(max : cmax)
+#endif
     for (i = 0; i < n; i++) {
         double h = m[i] / p->theta[i];
         double c = sqrt(v1[i] * v1[i] + v2[i] * v2[i]) + sqrt(p->g * h);
@@ -221,7 +244,8 @@ double orc_cfl_dt(const orc_problem *p, const double *m, const double *v1, const
 /* ---------------- one time step ---------------- */
 
 /* Advance (m, v1, v2) at t^n by dt to t_next = t^{n+1}.  Outputs may not alias inputs.
- * Returns 0, or -1 on a non-finite result. */
+ * Returns 0, or -1 on a non-finite result (or when the step's scratch cannot be
+ * allocated). */
 int orc_step(const orc_problem *p, const double *m, const double *v1, const double *v2,
              double dt, double t_next,
              double *m_out, double *v1_out, double *v2_out, orc_ledger *led)
@@ -231,9 +255,17 @@ int orc_step(const orc_problem *p, const double *m, const double *v1, const doub
     const double sigma = orc_sigma(l);
     const double rain = orc_rain_rate(p, t_next);   /* M_i(t^{n+1}) = r(t^{n+1}) */
     double out_rate_total = 0.0, clamp_total = 0.0;
-    int r, c, d, bad = 0;
+    /* per-cell outflow rate and clamped volume, summed after the cell loop */
+    double *cell_out = (double *)malloc(sizeof(double) * (size_t)n);
+    double *cell_clamp = (double *)malloc(sizeof(double) * (size_t)n);
+    int r, i, bad = 0;
+    if (!cell_out || !cell_clamp) { free(cell_out); free(cell_clamp); return -1; }
 
+#ifdef _OPENMP
+#pragma omp parallel for schedule(static) reduction(| : bad)
+#endif
     for (r = 0; r < rows; r++) {
+        int c, d;
         for (c = 0; c < cols; c++) {
             const int i = r * cols + c;
             const double hi = m[i] / p->theta[i];
@@ -338,8 +370,9 @@ int orc_step(const orc_problem *p, const double *m, const double *v1, const doub
                 const double g1 = m[i] * v1[i] + dt / sigma * (J1 + S1);
                 const double g2 = m[i] * v2[i] + dt / sigma * (J2 + S2);
                 double h_new, beta;
+                cell_clamp[i] = 0.0;
                 if (m_new < 0.0) {
-                    clamp_total += -m_new * sigma;
+                    cell_clamp[i] = -m_new * sigma;
                     m_new = 0.0;
                 }
                 /* Eq. fvm_2D_eq_frac.06-2 via Eq. miu-formula; a linear resistance
@@ -355,9 +388,16 @@ int orc_step(const orc_problem *p, const double *m, const double *v1, const doub
                 }
                 if (!isfinite(m_new) || !isfinite(v1_out[i]) || !isfinite(v2_out[i])) bad = 1;
             }
-            out_rate_total += out_rate;
+            cell_out[i] = out_rate;
         }
     }
+    /* the step's sums, in row-major order (adding a cell's 0 leaves a sum unchanged) */
+    for (i = 0; i < n; i++) {
+        out_rate_total += cell_out[i];
+        clamp_total += cell_clamp[i];
+    }
+    free(cell_out);
+    free(cell_clamp);
     if (led) {
         led->rain_in += sigma * dt * rain * (double)n;
         led->outflow += dt * out_rate_total;

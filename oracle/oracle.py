@@ -20,27 +20,43 @@ _HERE = os.path.dirname(os.path.abspath(__file__))
 _SRC = os.path.join(_HERE, "asx_oracle.c")
 _BUILD = os.path.join(_HERE, "_build")
 _SO = os.path.join(_BUILD, "liborc.so")
+_SO_OMP = os.path.join(_BUILD, "liborc_omp.so")
 _lock = threading.Lock()
-_lib = None
+_libs = {}
 
 WALL, FREE = 0, 1
 W, E, S, N = 0, 1, 2, 3
+_CFLAGS = ["-O2", "-std=c99", "-fPIC", "-shared", "-ffp-contract=off", "-fno-fast-math"]
+
+
+def _compile(out, extra):
+    tmp = out + f".tmp{os.getpid()}"
+    subprocess.check_call(["gcc", *_CFLAGS, *extra, "-o", tmp, _SRC, "-lm"])
+    os.replace(tmp, out)
 
 
 def build(force: bool = False) -> str:
-    """Compile the oracle into ``oracle/_build/liborc.so`` (gcc, -O2, no FMA contraction).
+    """Compile the oracle into ``oracle/_build/liborc.so`` (gcc, -O2, no FMA contraction)
+    and its OpenMP build ``liborc_omp.so`` (the same source with -fopenmp: the cells of a
+    step shared among threads, the same bits); returns the single-threaded library.
 
     ``ASX_ORACLE_SO`` names a prebuilt library to load instead (the mutation test uses it
     to run the pins against oracles with planted mistakes)."""
     if os.environ.get("ASX_ORACLE_SO"):
         return os.environ["ASX_ORACLE_SO"]
     os.makedirs(_BUILD, exist_ok=True)
-    if force or not os.path.exists(_SO) or os.path.getmtime(_SO) < os.path.getmtime(_SRC):
-        tmp = _SO + f".tmp{os.getpid()}"
-        subprocess.check_call(["gcc", "-O2", "-std=c99", "-fPIC", "-shared", "-ffp-contract=off",
-                               "-fno-fast-math", "-o", tmp, _SRC, "-lm"])
-        os.replace(tmp, _SO)
+    for out, extra in ((_SO, []), (_SO_OMP, ["-fopenmp"])):
+        if force or not os.path.exists(out) or os.path.getmtime(out) < os.path.getmtime(_SRC):
+            _compile(out, extra)
     return _SO
+
+
+def max_threads() -> int:
+    """Cores this process may run on (the thread count the OpenMP build uses by default)."""
+    try:
+        return len(os.sched_getaffinity(0))
+    except AttributeError:
+        return os.cpu_count() or 1
 
 
 class _Problem(C.Structure):
@@ -60,11 +76,15 @@ class Ledger(C.Structure):
                 ("steps", C.c_longlong)]
 
 
-def _load():
-    global _lib
+def _load(threads: int = 1):
+    """The oracle library: the single-threaded build for threads == 1, else the OpenMP
+    build set to that many threads."""
+    omp = threads > 1 and not os.environ.get("ASX_ORACLE_SO")
     with _lock:
-        if _lib is None:
-            lib = C.CDLL(build())
+        lib = _libs.get(omp)
+        if lib is None:
+            path = build()
+            lib = C.CDLL(_SO_OMP if omp else path)
             dp = C.POINTER(C.c_double)
             P = C.POINTER(_Problem)
             lib.orc_step.argtypes = [P, dp, dp, dp, C.c_double, C.c_double, dp, dp, dp, C.POINTER(Ledger)]
@@ -89,8 +109,13 @@ def _load():
             lib.orc_neighbour.argtypes = [C.c_int, C.c_int, C.c_int, C.c_int, C.c_int,
                                           C.POINTER(C.c_int), C.POINTER(C.c_int)]
             lib.orc_neighbour.restype = C.c_int
-            _lib = lib
-    return _lib
+            if hasattr(lib, "orc_threads"):
+                lib.orc_threads.argtypes = [C.c_int]
+                lib.orc_threads.restype = C.c_int
+            _libs[omp] = lib
+        if omp:
+            lib.orc_threads(int(threads))
+    return lib
 
 
 def _dp(a):
@@ -106,13 +131,15 @@ def _f64(a, n):
 
 
 class Problem:
-    """Static data of one raster: geometry, boundary types, bed, porosity, coefficients, rain."""
+    """Static data of one raster: geometry, boundary types, bed, porosity, coefficients, rain.
+    ``threads`` > 1 runs steps on the OpenMP build of the oracle (bit-identical results)."""
 
     def __init__(self, rows, cols, l, z, theta, alpha_s, alpha_p, bc=(WALL, WALL, WALL, WALL),
                  g=9.81, cfl=0.5, dt_max=1.0, rain_t=(), rain_r=(), viscosity=False,
                  free_range=((0, 0), (0, 0), (0, 0), (0, 0)), tau=0.0, h_dry=0.0, bc_q=(0.0,) * 4,
-                 bc_h=(0.0,) * 4, bc_u=(0.0,) * 4):
+                 bc_h=(0.0,) * 4, bc_u=(0.0,) * 4, threads=1):
         n = rows * cols
+        self.threads = int(threads)
         self.rows, self.cols, self.l = int(rows), int(cols), float(l)
         self.z = _f64(z, n)
         self.theta = _f64(theta, n)
@@ -161,11 +188,11 @@ class Problem:
 
     def cfl_dt(self, m, v1, v2):
         m, v1, v2 = (_f64(a, self.n) for a in (m, v1, v2))
-        return float(_load().orc_cfl_dt(C.byref(self._s), _dp(m), _dp(v1), _dp(v2)))
+        return float(_load(self.threads).orc_cfl_dt(C.byref(self._s), _dp(m), _dp(v1), _dp(v2)))
 
     def cmax(self, m, v1, v2):
         m, v1, v2 = (_f64(a, self.n) for a in (m, v1, v2))
-        return float(_load().orc_cmax(C.byref(self._s), _dp(m), _dp(v1), _dp(v2)))
+        return float(_load(self.threads).orc_cmax(C.byref(self._s), _dp(m), _dp(v1), _dp(v2)))
 
     def storage(self, m):
         m = _f64(m, self.n)
@@ -181,7 +208,7 @@ class Problem:
         m, v1, v2 = (_f64(a, self.n) for a in (m, v1, v2))
         mo, ao, bo = np.empty(self.n), np.empty(self.n), np.empty(self.n)
         led = ledger if ledger is not None else Ledger()
-        rc = _load().orc_step(C.byref(self._s), _dp(m), _dp(v1), _dp(v2), float(dt), float(t_next),
+        rc = _load(self.threads).orc_step(C.byref(self._s), _dp(m), _dp(v1), _dp(v2), float(dt), float(t_next),
                               _dp(mo), _dp(ao), _dp(bo), C.byref(led))
         if rc != 0:
             raise FloatingPointError("oracle step produced a non-finite value")
@@ -200,7 +227,7 @@ class Problem:
             rp, nr = _dp(rep), rep.size
         else:
             rp, nr = None, 0
-        k = _load().orc_run(C.byref(self._s), _dp(m), _dp(v1), _dp(v2), C.byref(t), float(t_end),
+        k = _load(self.threads).orc_run(C.byref(self._s), _dp(m), _dp(v1), _dp(v2), C.byref(t), float(t_end),
                             int(max_steps), rp, nr, float(sample_dt), _dp(samples), int(sample_cap),
                             C.byref(ns), C.byref(led))
         if k < 0:
@@ -209,7 +236,7 @@ class Problem:
                     samples=samples[:min(ns.value, int(sample_cap))].copy())
 
 
-def from_scenario(sc, viscosity=None):
+def from_scenario(sc, viscosity=None, threads=1):
     """Oracle problem for an ``inputs.Scenario`` (per-cell coefficient arrays); viscosity
     defaults to the scenario's setting."""
     if viscosity is None:
@@ -218,7 +245,8 @@ def from_scenario(sc, viscosity=None):
                    g=sc.g, cfl=sc.cfl, dt_max=sc.dt_max, rain_t=sc.rain_t, rain_r=sc.rain_r,
                    viscosity=viscosity, free_range=sc.free_range, tau=getattr(sc, "tau", 0.0),
                    h_dry=getattr(sc, "h_dry", 0.0), bc_q=getattr(sc, "bc_q", (0.0,) * 4),
-                   bc_h=getattr(sc, "bc_h", (0.0,) * 4), bc_u=getattr(sc, "bc_u", (0.0,) * 4))
+                   bc_h=getattr(sc, "bc_h", (0.0,) * 4), bc_u=getattr(sc, "bc_u", (0.0,) * 4),
+                   threads=threads)
 
 
 def friction(alpha, beta, g1, g2):

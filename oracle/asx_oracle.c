@@ -246,20 +246,39 @@ double orc_cfl_dt(const orc_problem *p, const double *m, const double *v1, const
 /* Advance (m, v1, v2) at t^n by dt to t_next = t^{n+1}.  Outputs may not alias inputs.
  * Returns 0, or -1 on a non-finite result (or when the step's scratch cannot be
  * allocated). */
+static int orc_step_ws(const orc_problem *p, const double *m, const double *v1, const double *v2,
+                       double dt, double t_next, double *m_out, double *v1_out, double *v2_out,
+                       orc_ledger *led, double *cell_out, double *cell_clamp);
+
 int orc_step(const orc_problem *p, const double *m, const double *v1, const double *v2,
              double dt, double t_next,
              double *m_out, double *v1_out, double *v2_out, orc_ledger *led)
+{
+    const size_t n = (size_t)p->rows * (size_t)p->cols;
+    double *cell_out = (double *)malloc(sizeof(double) * n);
+    double *cell_clamp = (double *)malloc(sizeof(double) * n);
+    int rc = -1;
+    if (cell_out && cell_clamp)
+        rc = orc_step_ws(p, m, v1, v2, dt, t_next, m_out, v1_out, v2_out, led, cell_out, cell_clamp);
+    free(cell_out);
+    free(cell_clamp);
+    return rc;
+}
+
+/* orc_step with caller-provided scratch for the per-cell outflow rates and clamped
+ * volumes (n doubles each). */
+static int orc_step_ws(const orc_problem *p, const double *m, const double *v1, const double *v2,
+                       double dt, double t_next, double *m_out, double *v1_out, double *v2_out,
+                       orc_ledger *led, double *cell_out, double *cell_clamp)
 {
     const int rows = p->rows, cols = p->cols, n = rows * cols;
     const double l = p->l, g = p->g;
     const double sigma = orc_sigma(l);
     const double rain = orc_rain_rate(p, t_next);   /* M_i(t^{n+1}) = r(t^{n+1}) */
     double out_rate_total = 0.0, clamp_total = 0.0;
-    /* per-cell outflow rate and clamped volume, summed after the cell loop */
-    double *cell_out = (double *)malloc(sizeof(double) * (size_t)n);
-    double *cell_clamp = (double *)malloc(sizeof(double) * (size_t)n);
+    /* per-cell outflow rate and clamped volume (cell_out, cell_clamp), summed after the
+     * cell loop */
     int r, i, bad = 0;
-    if (!cell_out || !cell_clamp) { free(cell_out); free(cell_clamp); return -1; }
 
 #ifdef _OPENMP
 #pragma omp parallel for schedule(static) reduction(| : bad)
@@ -396,8 +415,6 @@ int orc_step(const orc_problem *p, const double *m, const double *v1, const doub
         out_rate_total += cell_out[i];
         clamp_total += cell_clamp[i];
     }
-    free(cell_out);
-    free(cell_clamp);
     if (led) {
         led->rain_in += sigma * dt * rain * (double)n;
         led->outflow += dt * out_rate_total;
@@ -428,13 +445,18 @@ long long orc_run(const orc_problem *p, double *m, double *v1, double *v2, doubl
                   double sample_dt, double *samples, int cap, int *n_samples, orc_ledger *led)
 {
     const int n = p->rows * p->cols;
-    double *m2 = (double *)malloc(sizeof(double) * (size_t)n);
-    double *a2 = (double *)malloc(sizeof(double) * (size_t)n);
-    double *b2 = (double *)malloc(sizeof(double) * (size_t)n);
+    /* one workspace: the other state buffers and the step's per-cell scratch; the
+     * state moves between the caller's arrays and these by swapping pointers */
+    double *ws = (double *)malloc(sizeof(double) * (size_t)n * 5);
+    double *cm = m, *ca = v1, *cb = v2;
+    double *m2, *a2, *b2;
     long long k = 0;
     int ns = n_samples ? *n_samples : 0;
     int rc = 0;
-    if (!m2 || !a2 || !b2) { free(m2); free(a2); free(b2); return -1; }
+    if (!ws) return -1;
+    m2 = ws;
+    a2 = ws + (size_t)n;
+    b2 = ws + 2 * (size_t)n;
 
     while (*t < t_end && k < max_steps) {
         double t_next, dt;
@@ -446,7 +468,7 @@ long long orc_run(const orc_problem *p, double *m, double *v1, double *v2, doubl
             dt = t_next - *t;
         } else {
             double t_stop = t_end;
-            dt = orc_cfl_dt(p, m, v1, v2);
+            dt = orc_cfl_dt(p, cm, ca, cb);
             if (sample_dt > 0.0 && next_sample < t_stop) t_stop = next_sample;
             if (*t + dt >= t_stop) {
                 dt = t_stop - *t;
@@ -455,10 +477,13 @@ long long orc_run(const orc_problem *p, double *m, double *v1, double *v2, doubl
                 t_next = *t + dt;
             }
         }
-        rc = orc_step(p, m, v1, v2, dt, t_next, m2, a2, b2, led);
-        memcpy(m, m2, sizeof(double) * (size_t)n);
-        memcpy(v1, a2, sizeof(double) * (size_t)n);
-        memcpy(v2, b2, sizeof(double) * (size_t)n);
+        rc = orc_step_ws(p, cm, ca, cb, dt, t_next, m2, a2, b2, led, ws + 3 * (size_t)n, ws + 4 * (size_t)n);
+        {
+            double *x;
+            x = cm; cm = m2; m2 = x;
+            x = ca; ca = a2; a2 = x;
+            x = cb; cb = b2; b2 = x;
+        }
         *t = t_next;
         k++;
         if (sample_dt > 0.0 && t_next == next_sample) {
@@ -468,6 +493,11 @@ long long orc_run(const orc_problem *p, double *m, double *v1, double *v2, doubl
         if (rc) break;
     }
     if (n_samples) *n_samples = ns;
-    free(m2); free(a2); free(b2);
+    if (cm != m) {   /* the state ended in the workspace: copy it to the caller's arrays */
+        memcpy(m, cm, sizeof(double) * (size_t)n);
+        memcpy(v1, ca, sizeof(double) * (size_t)n);
+        memcpy(v2, cb, sizeof(double) * (size_t)n);
+    }
+    free(ws);
     return rc ? -1 : k;
 }

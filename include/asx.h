@@ -54,6 +54,13 @@ typedef enum {
 enum { ASX_BC_WALL = 0, ASX_BC_FREE = 1, ASX_BC_FLUX = 2, ASX_BC_DIRICHLET = 3 };
 enum { ASX_SIDE_W = 0, ASX_SIDE_E = 1, ASX_SIDE_S = 2, ASX_SIDE_N = 3 };
 enum { ASX_PTR_HOST = 0, ASX_PTR_DEVICE = 1 };
+/* Arithmetic of a raster (asx_raster_desc.precision).  The paper states no precision.
+ *   ASX_FP32_COMP  float32 state with the mass as a compensated pair and a float64
+ *                  ledger: the fast path (the TMA strip kernel).
+ *   ASX_FP64       float64 state, bed and porosity, every operation in float64 (one
+ *                  thread per cell; float64 runs at 1/64 of the float32 rate on GB300):
+ *                  for checks against double-precision references on small rasters. */
+enum { ASX_FP32_COMP = 0, ASX_FP64 = 1 };
 #define ASX_MAX_CLASSES 16
 #define ASX_MAX_RAIN 64
 
@@ -78,6 +85,7 @@ typedef struct asx_raster asx_raster;      /* opaque, owned by the library */
  *                       holds a uint8 land-cover class and asx_params gives per-class
  *                       porosity and coefficients.
  *   max_samples         capacity of the outlet hydrograph (0 = no hydrograph).
+ *   precision           ASX_FP32_COMP (0, the default of a zeroed struct) or ASX_FP64.
  * A boundary edge belongs to the S or N side when its missing neighbour's row is
  * outside the raster, otherwise to W or E. */
 typedef struct {
@@ -89,6 +97,7 @@ typedef struct {
     int max_samples;
     void *cuda_stream;         /* cudaStream_t; NULL = default stream */
     int device;                /* CUDA device ordinal */
+    int precision;             /* ASX_FP32_COMP or ASX_FP64 */
 } asx_raster_desc;
 
 /* Physical and numerical parameters (Sec. 3 "Parameters"; Eq. eq_K_h_theta).
@@ -145,8 +154,10 @@ typedef struct {
 } asx_ledger;
 
 /* Create a raster on desc->device.  Allocates all device memory it will use.
- * ASX_EINVAL: rows or cols < 2, edge_m <= 0, a bc value other than WALL/FREE,
- * n_classes outside [0, ASX_MAX_CLASSES], max_samples < 0. */
+ * ASX_EINVAL: rows or cols < 2, rows * cols >= 2^31, edge_m <= 0 or not finite, a bc
+ * value outside ASX_BC_WALL .. ASX_BC_DIRICHLET, free_begin < 0 or free_end <
+ * free_begin, n_classes outside [0, ASX_MAX_CLASSES], max_samples < 0, a precision
+ * other than ASX_FP32_COMP / ASX_FP64.  ASX_ENOMEM when device memory runs out. */
 asx_status asx_create_raster(const asx_raster_desc *desc, asx_raster **out);
 
 /* Free the raster and all its device memory (NULL is accepted). */
@@ -156,14 +167,16 @@ asx_status asx_destroy_raster(asx_raster *r);
 asx_status asx_set_params(asx_raster *r, const asx_params *p);
 
 /* Set the static fields and the initial state (the paper's "Data In", Sec. 3), reset
- * the clock to t = 0 and the ledger.  z: bed elevation [m] (float32, finite);
+ * the clock to t = 0 and the ledger.  z: bed elevation [m] (float64, finite); in
+ * ASX_FP32_COMP mode it is rounded to the nearest float32 (round to nearest even: an
+ * elevation of 1000 m moves by at most 3.1e-5 m), in ASX_FP64 mode kept as given;
  * theta_or_null: porosity per cell in (0, 1] when n_classes == 0, else NULL;
  * class_or_null: class per cell (< n_classes) when n_classes > 0, else NULL;
  * h0: initial depth [m] (>= 0, finite); v1_0, v2_0: initial velocity [m/s] (finite;
  * NULL = 0).  All dense rows x cols.  ptr_kind: ASX_PTR_HOST or ASX_PTR_DEVICE.
  * Value checks (ASX_EINVAL) are made on host inputs; device inputs are trusted.
  * Needs asx_set_params first (ASX_ESTATE). */
-asx_status asx_set_fields(asx_raster *r, const float *z, const float *theta_or_null,
+asx_status asx_set_fields(asx_raster *r, const double *z, const float *theta_or_null,
                           const uint8_t *class_or_null, const float *h0, const float *v1_0,
                           const float *v2_0, int ptr_kind);
 
@@ -184,14 +197,25 @@ asx_status asx_mass_ledger(asx_raster *r, int scenario, asx_ledger *out);
 asx_status asx_get_fields(asx_raster *r, int scenario, float *h, float *v1, float *v2,
                           int ptr_kind);
 
+/* Depth and velocity of every cell in float64, dense rows x cols: in ASX_FP64 mode the
+ * state itself (h = m / theta in float64), in ASX_FP32_COMP mode h = (m_hi + m_lo) /
+ * theta in float64 and the float32 velocities widened.  Any pointer may be NULL.  Uses
+ * three float64 planes of device scratch for the duration of the call. */
+asx_status asx_get_fields64(asx_raster *r, int scenario, double *h, double *v1, double *v2,
+                            int ptr_kind);
+
 /* The raw state: compensated mass pair (m_hi, m_lo), v1, v2, dense rows x cols
- * float32 (for checkpoints; any pointer may be NULL). */
+ * float32 (for checkpoints; any pointer may be NULL).  ASX_EINVAL in ASX_FP64 mode,
+ * which has no float32 state. */
 asx_status asx_get_state(asx_raster *r, float *m_hi, float *m_lo, float *v1, float *v2,
                          int ptr_kind);
 
 /* Restore a raw state written by asx_get_state together with the clock and ledger of
  * asx_get_clock / asx_mass_ledger at that moment; continuing from it reproduces the
- * uninterrupted run bit for bit.  Needs asx_set_fields first (static fields). */
+ * uninterrupted run bit for bit.  Needs asx_set_fields first (static fields).
+ * samples_cum_outflow: the cumulative outflow [m^3] at each of the n_samples sample times
+ * up to t (with sample_dt > 0, n_samples sample_dt <= t < (n_samples + 1) sample_dt is
+ * required: ASX_EINVAL otherwise).  ASX_EINVAL in ASX_FP64 mode. */
 asx_status asx_set_state(asx_raster *r, const float *m_hi, const float *m_lo,
                          const float *v1, const float *v2, int ptr_kind, double t,
                          long long step, const asx_ledger *ledger, int n_samples,
@@ -254,9 +278,10 @@ asx_status asx_create_ensemble(int n, const asx_scenario_desc *descs, void *cuda
                                asx_ensemble **out);
 asx_status asx_destroy_ensemble(asx_ensemble *e);
 
-/* Static fields and initial state of scenario s (dense rows x cols float32; v1, v2 may be
- * NULL = 0); the state is kept so that every run starts from it. */
-asx_status asx_ensemble_set_fields(asx_ensemble *e, int s, const float *z, const float *theta,
+/* Static fields and initial state of scenario s (dense rows x cols; the bed z in
+ * float64, rounded to the nearest float32 as in asx_set_fields; theta, h0, v1, v2 in
+ * float32, v1, v2 may be NULL = 0); the state is kept so that every run starts from it. */
+asx_status asx_ensemble_set_fields(asx_ensemble *e, int s, const double *z, const float *theta,
                                    const float *h0, const float *v1, const float *v2, int ptr_kind);
 
 /* Times every launch shape on the ensemble with each scenario cut to max_steps steps (after
@@ -353,7 +378,11 @@ asx_status asx_surrogate_check(int batch, int n_check, const int *idx, float *y,
  * address (cudaGetSymbolAddress); make that first call before any stream capture.  All
  * calls on a device share the scratch, so calls that overlap on the GPU (on different
  * streams, or from several threads) race: order them on one stream.
- * Returns ASX_EINVAL on bad sizes or null pointers, ASX_ECUDA on a CUDA error. */
+ * Returns ASX_EINVAL on bad sizes, a non-finite or non-positive edge_m or g, or null
+ * pointers; ASX_ECUDA when the address lookup, the counter reset or this call's kernel
+ * launch fails, or the context was broken by earlier work.  The launch status is the
+ * launch's own: a launch error that earlier, unrelated work left for cudaGetLastError is
+ * neither reported nor cleared by this call. */
 asx_status asx_state_scan_noalloc(int rows, int cols, int pitch, double edge_m, double g,
                                   const float *m_hi, const float *m_lo, const float *v1,
                                   const float *v2, const float *theta, double *storage_out,

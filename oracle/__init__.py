@@ -3,4 +3,4 @@
 Only ``tests/``, ``__graft_entry__.smoke()`` and the CPU-baseline leg of ``bench.py``
 may import this package.  It shares no code with the CUDA library.
 """
-from .oracle import (Problem, Ledger, friction, sigma, phi, build, from_scenario, WALL, FREE, W, E, S, N)  # noqa: F401
+from .oracle import (Problem, Ledger, friction, sigma, phi, build, from_scenario, max_threads, WALL, FREE, W, E, S, N)  # noqa: F401

@@ -23,6 +23,7 @@ STATUS_NAMES = {0: "ASX_OK", 1: "ASX_EINVAL", 2: "ASX_ENOMEM", 3: "ASX_ECUDA", 4
 ASX_BC_WALL, ASX_BC_FREE = 0, 1
 ASX_SIDE_W, ASX_SIDE_E, ASX_SIDE_S, ASX_SIDE_N = 0, 1, 2, 3
 ASX_PTR_HOST, ASX_PTR_DEVICE = 0, 1
+ASX_FP32_COMP, ASX_FP64 = 0, 1
 ASX_MAX_CLASSES = 16
 ASX_MAX_RAIN = 64
 
@@ -36,7 +37,8 @@ class AsxError(RuntimeError):
 class asx_raster_desc(C.Structure):
     _fields_ = [("rows", C.c_int), ("cols", C.c_int), ("edge_m", C.c_double), ("bc", C.c_int * 4),
                 ("free_begin", C.c_int * 4), ("free_end", C.c_int * 4), ("n_classes", C.c_int),
-                ("max_samples", C.c_int), ("cuda_stream", C.c_void_p), ("device", C.c_int)]
+                ("max_samples", C.c_int), ("cuda_stream", C.c_void_p), ("device", C.c_int),
+                ("precision", C.c_int)]
 
 
 class asx_params(C.Structure):
@@ -91,6 +93,7 @@ _PROTOS = {
     "asx_run_until": (C.c_int, [_RASTER, C.c_double, C.POINTER(C.c_double)]),
     "asx_mass_ledger": (C.c_int, [_RASTER, C.c_int, C.POINTER(asx_ledger)]),
     "asx_get_fields": (C.c_int, [_RASTER, C.c_int, _vp, _vp, _vp, C.c_int]),
+    "asx_get_fields64": (C.c_int, [_RASTER, C.c_int, _vp, _vp, _vp, C.c_int]),
     "asx_get_state": (C.c_int, [_RASTER, _vp, _vp, _vp, _vp, C.c_int]),
     "asx_set_state": (C.c_int, [_RASTER, _vp, _vp, _vp, _vp, C.c_int, C.c_double, C.c_longlong,
                                 C.POINTER(asx_ledger), C.c_int, _vp]),
@@ -186,7 +189,22 @@ def asx_set_params(r, p: asx_params):
     _check(load().asx_set_params(r, C.byref(p)), r)
 
 
+def _dtype_is(x, name, want):
+    """Refuses a host or torch array whose element type differs from the C signature's
+    (the library would read its bytes as the other type)."""
+    if x is None or isinstance(x, int):
+        return
+    dt = getattr(x, "dtype", None)
+    got = str(dt).replace("torch.", "") if dt is not None else None
+    if got is not None and got != want:
+        raise TypeError(f"{name} must be {want}, got {got}")
+
+
 def asx_set_fields(r, z, theta, cls, h0, v1, v2, ptr_kind):
+    _dtype_is(z, "z", "float64")
+    for nm, x in (("theta", theta), ("h0", h0), ("v1", v1), ("v2", v2)):
+        _dtype_is(x, nm, "float32")
+    _dtype_is(cls, "cls", "uint8")
     _check(load().asx_set_fields(r, _ptr(z), _ptr(theta), _ptr(cls), _ptr(h0), _ptr(v1), _ptr(v2),
                                  ptr_kind), r)
 
@@ -211,6 +229,10 @@ def asx_mass_ledger(r, scenario=0):
 
 def asx_get_fields(r, scenario, h, v1, v2, ptr_kind):
     _check(load().asx_get_fields(r, int(scenario), _ptr(h), _ptr(v1), _ptr(v2), ptr_kind), r)
+
+
+def asx_get_fields64(r, scenario, h, v1, v2, ptr_kind):
+    _check(load().asx_get_fields64(r, int(scenario), _ptr(h), _ptr(v1), _ptr(v2), ptr_kind), r)
 
 
 def asx_get_state(r, m_hi, m_lo, v1, v2, ptr_kind):
@@ -278,6 +300,9 @@ def asx_destroy_ensemble(e):
 
 
 def asx_ensemble_set_fields(e, s, z, theta, h0, v1, v2, ptr_kind):
+    _dtype_is(z, "z", "float64")
+    for nm, x in (("theta", theta), ("h0", h0), ("v1", v1), ("v2", v2)):
+        _dtype_is(x, nm, "float32")
     _echeck(load().asx_ensemble_set_fields(e, int(s), _ptr(z), _ptr(theta), _ptr(h0), _ptr(v1), _ptr(v2),
                                            ptr_kind), e)
 

@@ -20,6 +20,8 @@ ROOT = os.path.dirname(HERE)
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 NVFLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-Xptxas", "-v",
            "--expt-relaxed-constexpr", f"-I{os.path.join(ROOT, 'include')}"]
+# per-file flags: the FP64 step rounds every multiply and add as written
+FILE_FLAGS = {"step_fp64.cu": ["-fmad=false"]}
 
 
 def _nvcc() -> str:
@@ -55,7 +57,7 @@ def build(force: bool = False, verbose: bool = False) -> str:
 
     def compile_one(src):
         obj = os.path.join(BUILD, os.path.basename(src) + ".o")
-        cmd = [nvcc, *ARCH, *NVFLAGS, "-c", src, "-o", obj]
+        cmd = [nvcc, *ARCH, *NVFLAGS, *FILE_FLAGS.get(os.path.basename(src), []), "-c", src, "-o", obj]
         r = subprocess.run(cmd, capture_output=True, text=True)
         if r.returncode != 0:
             raise RuntimeError(f"nvcc failed on {src}:\n{r.stderr}")

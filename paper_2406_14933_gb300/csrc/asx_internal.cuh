@@ -40,13 +40,19 @@ struct DevCtl {
     int err;             // error bits (kErrNumeric, kErrTimeout)
     float cmax_cur;      // c_max of the state at t^n
     int pad0;
+    double cmax64_cur;   // c_max of the state at t^n (FP64 mode)
+    double qr64;         // rain depth of the pending step, dt * r(t^{n+1}) (FP64 mode)
     // reductions of the running step
     unsigned int cmax_bits;
     unsigned int done_ctas;
     unsigned int scan_done;
     unsigned int pad2;
-    double out_acc;      // sum of boundary mass increments (per unit area)
-    double clamp_acc;    // sum of clamped (negative) mass, per unit area
+    unsigned long long cmax64_bits;   // FP64 mode: bits of the largest new wave speed
+    // sums of the step's boundary mass increments and clamped (negative) mass, per unit
+    // area, as exact integer sums of the CTA partials split in 2^-30 and 2^-70 units
+    // (two's complement in unsigned words): the same value whatever the CTA order
+    unsigned long long out_fx[2];
+    unsigned long long clamp_fx[2];
     // ledger [m^3]
     double rain_in, outflow, clamped, storage0, storage;
     // hydrograph
@@ -56,7 +62,8 @@ struct DevCtl {
     // parameters of the time step and the rain
     double g, cfl, dt_max, sigma, phi;
     long long ncells;
-    int n_rain, pad1;
+    int n_rain;
+    int fp64;            // 1: the state is float64 (ASX_FP64), the step is the FP64 kernel
     double rain_t[kMaxRain], rain_r[kMaxRain];
 };
 
@@ -118,6 +125,24 @@ struct StepArgs {
     DevCtl *ctl;
 };
 
+// Arguments of the FP64 step (precision ASX_FP64): float64 planes of rows x pitch
+// elements, coefficients in float64.
+struct StepArgs64 {
+    int rows, cols, pitch;
+    double *m[2], *v1[2], *v2[2];      // theta h and velocity, per state parity
+    const double *z;                   // bed
+    const double *theta;               // porosity, or nullptr in class mode
+    const uint8_t *cls;                // class ids, or nullptr
+    double cls_theta[kMaxClasses], cls_as[kMaxClasses], cls_ap[kMaxClasses];
+    double alpha_s, alpha_p;           // per-cell-porosity mode
+    double l, g, tau, h_dry;
+    int visc;
+    int bc[4], fb[4], fe[4];
+    double bq[4], bh[4], bu[4];
+    int nblocks;
+    DevCtl *ctl;
+};
+
 // TMA descriptors of the fields, per state parity (strip kernel).  mhi/v1/v2/z/theta
 // boxes are (kStripW + 8) x kStripChunkRows floats; mlo boxes kStripW x kStripChunkRows
 // floats; class boxes (kStripW + 16) x kStripChunkRows bytes.
@@ -139,6 +164,24 @@ int scan_blocks(int rows, int cols);
 cudaError_t launch_init_state(const StepArgs &a, int parity, const float *h, const float *v1,
                               const float *v2, cudaStream_t s);
 cudaError_t launch_extract_depth(const StepArgs &a, int parity, float *h_out, cudaStream_t s);
+
+// ---- FP64 mode (step_fp64.cu) ----
+int step_fp64_blocks(int rows, int cols);
+cudaError_t launch_step_fp64(const StepArgs64 &a, cudaStream_t s);
+cudaError_t launch_scan64(const StepArgs64 &a, double *partials, int nparts, int set_storage0, cudaStream_t s);
+// theta h and velocities of parity `par` from float32 h, v1, v2 (pitched; v may be nullptr)
+cudaError_t launch_init64(const StepArgs64 &a, int par, const float *h, const float *v1, const float *v2,
+                          cudaStream_t s);
+// h = m / theta, v1, v2 of parity `par` into float64 (out64) or float32 (out32) pitched buffers
+cudaError_t launch_extract64(const StepArgs64 &a, int par, double *h64, double *v164, double *v264, float *h32,
+                             float *v132, float *v232, cudaStream_t s);
+// FP32 mode: h = (hi + lo) / theta, v1, v2 widened to float64 (pitched outputs)
+cudaError_t launch_extract_wide(const StepArgs &a, int par, double *h, double *v1, double *v2, cudaStream_t s);
+// pitched plane conversions: float64 -> float32 (round to nearest), float32 -> float64
+cudaError_t launch_narrow(const double *src, int rows, int cols, int src_pitch, float *dst, int dst_pitch,
+                          cudaStream_t s);
+cudaError_t launch_widen(const float *src, int rows, int cols, int src_pitch, double *dst, int dst_pitch,
+                         cudaStream_t s);
 
 // prepare modes
 constexpr int kPrepRecompute = 0;   // recompute the pending step from the current clock

@@ -111,8 +111,9 @@ __device__ void prepare_step(DevCtl *c)
     if (c->err) return;
     if (!(c->t < c->t_end) || c->step >= c->step_limit) return;
     double dt = c->dt_max;
-    if (c->cmax_cur > 0.0f) {
-        const double tau = c->cfl * c->phi / (double)c->cmax_cur;
+    const double cmx = c->fp64 ? c->cmax64_cur : (double)c->cmax_cur;
+    if (cmx > 0.0) {
+        const double tau = c->cfl * c->phi / cmx;
         if (tau < dt) dt = tau;
     }
     double t_stop = c->t_end;
@@ -132,8 +133,25 @@ __device__ void prepare_step(DevCtl *c)
     c->t_next = tn;
     c->kappa = (float)(dt / c->sigma);
     c->qr = (float)(dt * r);
+    c->qr64 = dt * r;
     c->dtf = (float)dt;
     c->active = 1;
+}
+
+// Adds a CTA's partial x to an order-independent sum: x = h 2^-30 + l 2^-70 (+ a rounding
+// of at most 2^-71), h and l integers added with integer atomics, which commute exactly.
+// |x| < 2^33 per partial; the fine part of one partial is below 2^40 units.
+__device__ __forceinline__ void fx_add(unsigned long long *acc, double x)
+{
+    const double h = rint(x * 0x1p30);
+    const double rem = fma(-h, 0x1p-30, x);          // exact: x - h 2^-30
+    atomicAdd(&acc[0], (unsigned long long)(long long)h);
+    atomicAdd(&acc[1], (unsigned long long)__double2ll_rn(rem * 0x1p70));
+}
+
+__device__ __forceinline__ double fx_value(const volatile unsigned long long *acc)
+{
+    return (double)(long long)acc[0] * 0x1p-30 + (double)(long long)acc[1] * 0x1p-70;
 }
 
 // Books the finished step (run by one thread after every CTA of the step is done).
@@ -141,10 +159,11 @@ __device__ void finish_step(DevCtl *c)
 {
     volatile DevCtl *vc = c;
     const unsigned bits = vc->cmax_bits;
-    const double outq = vc->out_acc;
-    const double clq = vc->clamp_acc;
+    const double outq = fx_value(vc->out_fx);
+    const double clq = fx_value(vc->clamp_fx);
     const float cmax = __uint_as_float(bits);
-    c->rain_in += c->sigma * (double)c->ncells * (double)c->qr;
+    const double cmax64 = __longlong_as_double((long long)vc->cmax64_bits);
+    c->rain_in += c->sigma * (double)c->ncells * (c->fp64 ? c->qr64 : (double)c->qr);
     c->outflow += c->sigma * outq;
     c->clamped += c->sigma * clq;
     c->t = c->t_next;
@@ -154,11 +173,17 @@ __device__ void finish_step(DevCtl *c)
         if (c->n_samples < c->max_samples) c->samples[c->n_samples] = c->outflow;
         c->n_samples += 1;
     }
-    if (!(cmax <= FLT_MAX)) c->err |= kErrNumeric;   // NaN or Inf somewhere
-    c->cmax_cur = cmax;
+    if (c->fp64) {
+        if (!(cmax64 <= DBL_MAX)) c->err |= kErrNumeric;
+        c->cmax64_cur = cmax64;
+        c->cmax64_bits = 0ull;
+    } else {
+        if (!(cmax <= FLT_MAX)) c->err |= kErrNumeric;   // NaN or Inf somewhere
+        c->cmax_cur = cmax;
+    }
     c->cmax_bits = 0u;
-    c->out_acc = 0.0;
-    c->clamp_acc = 0.0;
+    c->out_fx[0] = c->out_fx[1] = 0ull;
+    c->clamp_fx[0] = c->clamp_fx[1] = 0ull;
     c->done_ctas = 0u;
     prepare_step(c);
 }
@@ -555,8 +580,8 @@ __device__ __forceinline__ void reduce_and_finish(const StepArgs &a, unsigned cb
         }
         DevCtl *ctl = a.ctl;
         atomicMax(&ctl->cmax_bits, mb);
-        if (so != 0.0) atomicAdd(&ctl->out_acc, so);
-        if (sc != 0.0) atomicAdd(&ctl->clamp_acc, sc);
+        if (so != 0.0) fx_add(ctl->out_fx, so);
+        if (sc != 0.0) fx_add(ctl->clamp_fx, sc);
         __threadfence();
         const unsigned prev = atomicAdd(&ctl->done_ctas, 1u);
         s_last = (prev == (unsigned)a.nblocks - 1u);

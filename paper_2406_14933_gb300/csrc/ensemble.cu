@@ -587,7 +587,7 @@ const char *asx_ensemble_last_error(const asx_ensemble *e)
     return e ? e->err.c_str() : "null ensemble handle";
 }
 
-asx_status asx_ensemble_set_fields(asx_ensemble *e, int s, const float *z, const float *theta,
+asx_status asx_ensemble_set_fields(asx_ensemble *e, int s, const double *z, const float *theta,
                                    const float *h0, const float *v1, const float *v2, int kind)
 {
     if (!e) return ASX_EINVAL;
@@ -612,7 +612,15 @@ asx_status asx_ensemble_set_fields(asx_ensemble *e, int s, const float *z, const
     };
     EnsScenario &h = e->host[s];
     StepArgs &a = h.a;
-    ENS_CUDA(e, put((void *)a.z, z));
+    // the bed rounded to the nearest float32
+    if (kind == ASX_PTR_HOST) {
+        std::vector<float> zf(n);
+        for (size_t i = 0; i < n; i++) zf[i] = (float)z[i];
+        ENS_CUDA(e, put((void *)a.z, zf.data()));
+        ENS_CUDA(e, cudaStreamSynchronize(e->stream));      // zf is released on return
+    } else {
+        ENS_CUDA(e, launch_narrow(z, d.rows, d.cols, d.cols, (float *)a.z, pitch, e->stream));
+    }
     ENS_CUDA(e, put((void *)a.theta, theta));
     ENS_CUDA(e, put(a.mhi[1], h0));
     if (v1) ENS_CUDA(e, put(a.v1[1], v1));

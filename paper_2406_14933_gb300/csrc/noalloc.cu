@@ -6,6 +6,7 @@
 // library.  For them this file offers the water-storage / wave-speed scan of a state
 // they already hold, with its scratch (one partial per CTA and a completion counter) in
 // a fixed file-scope device array instead of memory obtained from cudaMalloc.
+#include <atomic>
 #include <cfloat>
 #include <cmath>
 #include <cstdint>
@@ -86,8 +87,9 @@ scan_noalloc_kernel(NoAllocScratch *sc, int rows, int cols, int pitch, const flo
 }
 
 // Device address of the scratch array, looked up once per device (host code may not use
-// the symbol itself as an address).
-NoAllocScratch *g_scratch_addr[kMaxDevices];
+// the symbol itself as an address).  Atomic slots: threads making their first call on
+// the same device at once each look the address up and store the same value.
+std::atomic<NoAllocScratch *> g_scratch_addr[kMaxDevices];
 
 }  // namespace
 }  // namespace asx
@@ -99,7 +101,8 @@ extern "C" asx_status asx_state_scan_noalloc(int rows, int cols, int pitch, doub
                                              const float *v2, const float *theta, double *storage_out,
                                              float *cmax_out, void *cuda_stream)
 {
-    if (rows < 1 || cols < 1 || pitch < cols || !(edge_m > 0.0) || !std::isfinite(edge_m) || !(g > 0.0))
+    if (rows < 1 || cols < 1 || pitch < cols || !(edge_m > 0.0) || !std::isfinite(edge_m) || !(g > 0.0) ||
+        !std::isfinite(g))
         return ASX_EINVAL;
     if (!m_hi || !m_lo || !v1 || !v2 || !theta || !storage_out || !cmax_out) return ASX_EINVAL;
     const long long n = (long long)rows * cols;
@@ -107,19 +110,24 @@ extern "C" asx_status asx_state_scan_noalloc(int rows, int cols, int pitch, doub
     if (nblocks > kNoAllocMaxBlocks) return ASX_EINVAL;     // more than 67,108,864 cells
     int dev = 0;
     if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDevices) return ASX_ECUDA;
-    if (!g_scratch_addr[dev]) {
+    NoAllocScratch *sc = g_scratch_addr[dev].load(std::memory_order_acquire);
+    if (!sc) {
         // first call on this device: find the device address of the scratch array
         void *p = nullptr;
         if (cudaGetSymbolAddress(&p, g_noalloc_scratch) != cudaSuccess || !p) return ASX_ECUDA;
-        g_scratch_addr[dev] = static_cast<NoAllocScratch *>(p);
+        sc = static_cast<NoAllocScratch *>(p);
+        g_scratch_addr[dev].store(sc, std::memory_order_release);
     }
-    NoAllocScratch *sc = g_scratch_addr[dev];
     cudaStream_t s = static_cast<cudaStream_t>(cuda_stream);
     // the counter must start at zero even if an earlier call was cut short
     if (cudaMemsetAsync(&sc->done, 0, sizeof(unsigned), s) != cudaSuccess) return ASX_ECUDA;
     const double sigma = 1.5 * std::sqrt(3.0) * edge_m * edge_m;
-    scan_noalloc_kernel<<<(unsigned)nblocks, kNoAllocThreads, 0, s>>>(sc, rows, cols, pitch, m_hi, m_lo, v1,
-                                                                      v2, theta, (float)g, sigma,
-                                                                      storage_out, cmax_out);
-    return cudaGetLastError() == cudaSuccess ? ASX_OK : ASX_ECUDA;
+    const float gf = (float)g;
+    // cudaLaunchKernel returns this launch's own status: a launch error that earlier,
+    // unrelated work left for cudaGetLastError is neither reported nor cleared here
+    void *args[] = {&sc, &rows, &cols, &pitch, (void *)&m_hi, (void *)&m_lo, (void *)&v1, (void *)&v2,
+                    (void *)&theta, (void *)&gf, (void *)&sigma, &storage_out, &cmax_out};
+    const cudaError_t e = cudaLaunchKernel((const void *)scan_noalloc_kernel, dim3((unsigned)nblocks),
+                                           dim3(kNoAllocThreads), args, 0, s);
+    return e == cudaSuccess ? ASX_OK : ASX_ECUDA;
 }

@@ -20,7 +20,7 @@ namespace {
 constexpr int kGraphSteps = 32;   // step launches captured in one graph
 constexpr int kTileRowsDefault = 32;
 
-enum StepVariant { kVariantStrip = 0, kVariantGather = 1 };
+enum StepVariant { kVariantStrip = 0, kVariantGather = 1, kVariantFp64 = 2 };
 
 // Step kernel variant: ASX_STEP_KERNEL=gather selects the one-thread-per-cell gather
 // kernel; the default is the TMA strip kernel.  ASX_TILE_ROWS sets the strip tile height.
@@ -91,6 +91,8 @@ struct asx_raster {
     double *scan_parts = nullptr;
     int scan_n = 0;
     StepArgs args{};
+    StepArgs64 a64{};                   // FP64 mode (desc.precision == ASX_FP64)
+    bool fp64 = false;
     int variant = kVariantStrip;
     StripMaps maps{};
     DevCtl host_ctl{};                  // parameter image (device copy is authoritative)
@@ -115,7 +117,8 @@ asx_status fail(asx_raster *r, asx_status st, const std::string &msg)
             return fail((r), ASX_ECUDA, std::string(#call) + ": " + cudaGetErrorString(e_)); \
     } while (0)
 
-bool finite_host(const float *p, size_t n)
+template <typename T>
+bool finite_host(const T *p, size_t n)
 {
     for (size_t i = 0; i < n; i++)
         if (!std::isfinite(p[i])) return false;
@@ -145,6 +148,13 @@ asx_status set_device(asx_raster *r)
     return ASX_OK;
 }
 
+// Storage and c_max of the current state (the float32 or the float64 scan).
+cudaError_t scan_state(asx_raster *r, int set_storage0)
+{
+    if (r->fp64) return launch_scan64(r->a64, r->scan_parts, r->scan_n, set_storage0, r->stream);
+    return launch_scan(r->args, r->scan_parts, r->scan_n, set_storage0, r->stream);
+}
+
 // Reads the control head (clock, flags) into mirror[0]; synchronises the stream.
 asx_status read_head(asx_raster *r, DevCtl **out)
 {
@@ -172,6 +182,7 @@ void drop_graph(asx_raster *r)
 
 cudaError_t launch_step(asx_raster *r, cudaStream_t s)
 {
+    if (r->variant == kVariantFp64) return launch_step_fp64(r->a64, s);
     if (r->variant == kVariantGather) return launch_step_gather(r->args, s);
     return launch_step_strip(r->args, r->maps, s);
 }
@@ -266,6 +277,7 @@ asx_status asx_create_raster(const asx_raster_desc *desc, asx_raster **out)
         if (desc->free_begin[s] < 0 || desc->free_end[s] < desc->free_begin[s]) return ASX_EINVAL;
     }
     if (desc->n_classes < 0 || desc->n_classes > kMaxClasses || desc->max_samples < 0) return ASX_EINVAL;
+    if (desc->precision != ASX_FP32_COMP && desc->precision != ASX_FP64) return ASX_EINVAL;
 
     asx_raster *r = new (std::nothrow) asx_raster();
     if (!r) return ASX_ENOMEM;
@@ -274,7 +286,9 @@ asx_status asx_create_raster(const asx_raster_desc *desc, asx_raster **out)
     r->rows = desc->rows;
     r->cols = desc->cols;
     r->pitch = (desc->cols + kPitchAlign - 1) / kPitchAlign * kPitchAlign;
-    r->plane = (size_t)r->rows * r->pitch * sizeof(float);
+    r->fp64 = desc->precision == ASX_FP64;
+    // FP64 mode: every plane holds float64 (the state's six planes, bed, porosity)
+    r->plane = (size_t)r->rows * r->pitch * (r->fp64 ? sizeof(double) : sizeof(float));
     asx_status st = set_device(r);
     if (st) { delete r; return st; }
     // planes: 2 x (mhi, mlo, v1, v2), z, theta
@@ -295,10 +309,10 @@ asx_status asx_create_raster(const asx_raster_desc *desc, asx_raster **out)
     a.rows = r->rows;
     a.cols = r->cols;
     a.pitch = r->pitch;
-    r->variant = variant_from_env();
+    r->variant = r->fp64 ? kVariantFp64 : variant_from_env();
     a.tile_rows = tile_rows_from_env();
     if (r->variant == kVariantGather) a.nblocks = step_gather_blocks(r->rows, r->cols);
-    else step_strip_layout(a);
+    else if (r->variant == kVariantStrip) step_strip_layout(a);
     const size_t pe = r->plane / sizeof(float);
     for (int p = 0; p < 2; p++) {
         a.mhi[p] = r->buf + (size_t)(4 * p + 0) * pe;
@@ -315,6 +329,30 @@ asx_status asx_create_raster(const asx_raster_desc *desc, asx_raster **out)
         a.fe[s] = desc->free_end[s];
     }
     a.ctl = r->ctl;
+    if (r->fp64) {
+        // the same plane slots, counted in float64 elements (rows x pitch each)
+        StepArgs64 &b = r->a64;
+        double *dbuf = reinterpret_cast<double *>(r->buf);
+        const size_t pd = r->plane / sizeof(double);
+        b.rows = r->rows;
+        b.cols = r->cols;
+        b.pitch = r->pitch;
+        for (int p = 0; p < 2; p++) {
+            b.m[p] = dbuf + (size_t)(4 * p + 0) * pd;
+            b.v1[p] = dbuf + (size_t)(4 * p + 2) * pd;
+            b.v2[p] = dbuf + (size_t)(4 * p + 3) * pd;
+        }
+        b.z = dbuf + 8 * pd;
+        b.theta = desc->n_classes == 0 ? dbuf + 9 * pd : nullptr;
+        b.cls = r->cls;
+        for (int s = 0; s < 4; s++) {
+            b.bc[s] = desc->bc[s];
+            b.fb[s] = desc->free_begin[s];
+            b.fe[s] = desc->free_end[s];
+        }
+        b.nblocks = step_fp64_blocks(r->rows, r->cols);
+        b.ctl = r->ctl;
+    }
     if (r->variant == kVariantStrip) {
         bool ok = true;
         const int bf = kStripW + 8;
@@ -342,6 +380,7 @@ asx_status asx_create_raster(const asx_raster_desc *desc, asx_raster **out)
     c.sigma = 1.5 * std::sqrt(3.0) * desc->edge_m * desc->edge_m;
     c.phi = c.sigma / (6.0 * desc->edge_m);
     c.ncells = (long long)r->rows * r->cols;
+    c.fp64 = r->fp64 ? 1 : 0;
     e = cudaMemcpyAsync(r->ctl, &c, sizeof(DevCtl), cudaMemcpyHostToDevice, r->stream);
     if (e == cudaSuccess) e = cudaStreamSynchronize(r->stream);
     if (e != cudaSuccess) {
@@ -421,6 +460,29 @@ asx_status asx_set_params(asx_raster *r, const asx_params *p)
         a.bh[s] = (float)p->bc_h[s];
         a.bu[s] = (float)p->bc_u[s];
     }
+    {
+        StepArgs64 &b = r->a64;
+        if (nc == 0) {
+            b.alpha_s = p->alpha_s;
+            b.alpha_p = p->alpha_p;
+        } else {
+            for (int k = 0; k < nc; k++) {
+                b.cls_theta[k] = (double)p->class_theta[k];
+                b.cls_as[k] = (double)p->class_alpha_s[k];
+                b.cls_ap[k] = (double)p->class_alpha_p[k];
+            }
+        }
+        b.l = l;
+        b.g = p->g;
+        b.tau = p->tau;
+        b.h_dry = p->h_dry;
+        b.visc = p->viscosity;
+        for (int s = 0; s < 4; s++) {
+            b.bq[s] = p->bc_q[s];
+            b.bh[s] = p->bc_h[s];
+            b.bu[s] = p->bc_u[s];
+        }
+    }
     const double s3 = std::sqrt(3.0) / 2.0;
     const double n1[3] = {1.0, 0.5, -0.5}, n2[3] = {0.0, s3, s3};
     for (int d = 0; d < 3; d++) {
@@ -455,7 +517,7 @@ asx_status asx_set_params(asx_raster *r, const asx_params *p)
     return ASX_OK;
 }
 
-asx_status asx_set_fields(asx_raster *r, const float *z, const float *theta, const uint8_t *cls,
+asx_status asx_set_fields(asx_raster *r, const double *z, const float *theta, const uint8_t *cls,
                           const float *h0, const float *v1, const float *v2, int kind)
 {
     if (!r) return ASX_EINVAL;
@@ -482,14 +544,39 @@ asx_status asx_set_fields(asx_raster *r, const float *z, const float *theta, con
     asx_status st = set_device(r);
     if (st) return st;
     StepArgs &a = r->args;
-    ASX_CUDA(r, put_plane(r, (void *)a.z, z, sizeof(float), kind));
-    if (theta) ASX_CUDA(r, put_plane(r, (void *)a.theta, theta, sizeof(float), kind));
     if (cls) ASX_CUDA(r, put_plane(r, (void *)a.cls, cls, 1, kind));
-    // stage h0, v in the parity-1 planes, convert into parity 0
-    ASX_CUDA(r, put_plane(r, a.mhi[1], h0, sizeof(float), kind));
-    if (v1) ASX_CUDA(r, put_plane(r, a.v1[1], v1, sizeof(float), kind));
-    if (v2) ASX_CUDA(r, put_plane(r, a.v2[1], v2, sizeof(float), kind));
-    ASX_CUDA(r, launch_init_state(a, 0, a.mhi[1], v1 ? a.v1[1] : nullptr, v2 ? a.v2[1] : nullptr, r->stream));
+    if (r->fp64) {
+        // float64 planes: the bed as given; porosity, depth and velocities widened from
+        // float32 staged (float32, pitched) in the parity-1 planes
+        StepArgs64 &b = r->a64;
+        ASX_CUDA(r, put_plane(r, (void *)b.z, z, sizeof(double), kind));
+        float *st_h = reinterpret_cast<float *>(b.m[1]), *st_1 = reinterpret_cast<float *>(b.v1[1]);
+        float *st_2 = reinterpret_cast<float *>(b.v2[1]);
+        if (theta) {
+            ASX_CUDA(r, put_plane(r, st_h, theta, sizeof(float), kind));
+            ASX_CUDA(r, launch_widen(st_h, r->rows, r->cols, r->pitch, (double *)b.theta, r->pitch, r->stream));
+        }
+        ASX_CUDA(r, put_plane(r, st_h, h0, sizeof(float), kind));
+        if (v1) ASX_CUDA(r, put_plane(r, st_1, v1, sizeof(float), kind));
+        if (v2) ASX_CUDA(r, put_plane(r, st_2, v2, sizeof(float), kind));
+        ASX_CUDA(r, launch_init64(b, 0, st_h, v1 ? st_1 : nullptr, v2 ? st_2 : nullptr, r->stream));
+    } else {
+        // the bed rounded to the nearest float32
+        if (kind == ASX_PTR_HOST) {
+            std::vector<float> zf(n);
+            for (size_t i = 0; i < n; i++) zf[i] = (float)z[i];
+            ASX_CUDA(r, put_plane(r, (void *)a.z, zf.data(), sizeof(float), kind));
+            ASX_CUDA(r, cudaStreamSynchronize(r->stream));     // zf is released on return
+        } else {
+            ASX_CUDA(r, launch_narrow(z, r->rows, r->cols, r->cols, (float *)a.z, r->pitch, r->stream));
+        }
+        if (theta) ASX_CUDA(r, put_plane(r, (void *)a.theta, theta, sizeof(float), kind));
+        // stage h0, v in the parity-1 planes, convert into parity 0
+        ASX_CUDA(r, put_plane(r, a.mhi[1], h0, sizeof(float), kind));
+        if (v1) ASX_CUDA(r, put_plane(r, a.v1[1], v1, sizeof(float), kind));
+        if (v2) ASX_CUDA(r, put_plane(r, a.v2[1], v2, sizeof(float), kind));
+        ASX_CUDA(r, launch_init_state(a, 0, a.mhi[1], v1 ? a.v1[1] : nullptr, v2 ? a.v2[1] : nullptr, r->stream));
+    }
     // reset clock and ledger (everything before the parameters)
     DevCtl &c = r->host_ctl;
     c.t = 0.0;
@@ -502,13 +589,14 @@ asx_status asx_set_fields(asx_raster *r, const float *z, const float *theta, con
     c.parity = 0;
     c.err = 0;
     c.cmax_bits = 0;
+    c.cmax64_bits = 0ull;
     c.done_ctas = 0;
     c.scan_done = 0;
-    c.out_acc = c.clamp_acc = 0.0;
+    c.out_fx[0] = c.out_fx[1] = c.clamp_fx[0] = c.clamp_fx[1] = 0ull;
     c.rain_in = c.outflow = c.clamped = c.storage0 = c.storage = 0.0;
     c.n_samples = 0;
     ASX_CUDA(r, cudaMemcpyAsync(r->ctl, &c, offsetof(DevCtl, g), cudaMemcpyHostToDevice, r->stream));
-    ASX_CUDA(r, launch_scan(a, r->scan_parts, r->scan_n, 1, r->stream));
+    ASX_CUDA(r, scan_state(r, 1));
     ASX_CUDA(r, launch_prepare(r->ctl, kPrepRecompute, 0.0, 0, r->stream));
     DevCtl *h;
     st = read_head(r, &h);
@@ -570,7 +658,7 @@ asx_status asx_mass_ledger(asx_raster *r, int scenario, asx_ledger *out)
     if (!r->have_fields) return fail(r, ASX_ESTATE, "asx_set_fields must come first");
     asx_status st = set_device(r);
     if (st) return st;
-    ASX_CUDA(r, launch_scan(r->args, r->scan_parts, r->scan_n, 0, r->stream));
+    ASX_CUDA(r, scan_state(r, 0));
     // scan also refreshes c_max of the current state, which equals what the last step
     // recorded; the pending dt is unchanged
     DevCtl *c = &r->mirror[1];
@@ -601,6 +689,18 @@ asx_status asx_get_fields(asx_raster *r, int scenario, float *h, float *v1, floa
     if (st) return st;
     const int par = hd->parity, np = par ^ 1;
     const StepArgs &a = r->args;
+    if (r->fp64) {
+        // float32 copies of h, v1, v2 in the other parity's planes (free between steps)
+        const StepArgs64 &b = r->a64;
+        float *h32 = reinterpret_cast<float *>(b.m[np]), *u32 = reinterpret_cast<float *>(b.v1[np]);
+        float *w32 = reinterpret_cast<float *>(b.v2[np]);
+        ASX_CUDA(r, launch_extract64(b, par, nullptr, nullptr, nullptr, h32, u32, w32, r->stream));
+        if (h) ASX_CUDA(r, get_plane(r, h, h32, sizeof(float), kind));
+        if (v1) ASX_CUDA(r, get_plane(r, v1, u32, sizeof(float), kind));
+        if (v2) ASX_CUDA(r, get_plane(r, v2, w32, sizeof(float), kind));
+        ASX_CUDA(r, cudaStreamSynchronize(r->stream));
+        return ASX_OK;
+    }
     if (h) {
         ASX_CUDA(r, launch_extract_depth(a, par, a.mhi[np], r->stream));
         ASX_CUDA(r, get_plane(r, h, a.mhi[np], sizeof(float), kind));
@@ -611,9 +711,39 @@ asx_status asx_get_fields(asx_raster *r, int scenario, float *h, float *v1, floa
     return ASX_OK;
 }
 
+asx_status asx_get_fields64(asx_raster *r, int scenario, double *h, double *v1, double *v2, int kind)
+{
+    if (!r) return ASX_EINVAL;
+    if (scenario != 0) return fail(r, ASX_EINVAL, "scenario must be 0 for a single raster");
+    if (kind != ASX_PTR_HOST && kind != ASX_PTR_DEVICE) return fail(r, ASX_EINVAL, "bad ptr_kind");
+    if (!r->have_fields) return fail(r, ASX_ESTATE, "asx_set_fields must come first");
+    asx_status st = set_device(r);
+    if (st) return st;
+    DevCtl *hd;
+    st = read_head(r, &hd);
+    if (st) return st;
+    const int par = hd->parity;
+    // three pitched float64 planes of scratch for the duration of the call
+    double *tmp = nullptr;
+    const size_t pl = (size_t)r->rows * r->pitch;
+    ASX_CUDA(r, cudaMalloc(&tmp, 3 * pl * sizeof(double)));
+    cudaError_t e;
+    if (r->fp64) e = launch_extract64(r->a64, par, tmp, tmp + pl, tmp + 2 * pl, nullptr, nullptr, nullptr, r->stream);
+    else e = launch_extract_wide(r->args, par, tmp, tmp + pl, tmp + 2 * pl, r->stream);
+    if (e == cudaSuccess && h) e = get_plane(r, h, tmp, sizeof(double), kind);
+    if (e == cudaSuccess && v1) e = get_plane(r, v1, tmp + pl, sizeof(double), kind);
+    if (e == cudaSuccess && v2) e = get_plane(r, v2, tmp + 2 * pl, sizeof(double), kind);
+    cudaError_t e2 = cudaStreamSynchronize(r->stream);
+    cudaFree(tmp);
+    if (e == cudaSuccess) e = e2;
+    if (e != cudaSuccess) return fail(r, ASX_ECUDA, std::string("get_fields64: ") + cudaGetErrorString(e));
+    return ASX_OK;
+}
+
 asx_status asx_get_state(asx_raster *r, float *mhi, float *mlo, float *v1, float *v2, int kind)
 {
     if (!r) return ASX_EINVAL;
+    if (r->fp64) return fail(r, ASX_EINVAL, "the compensated float32 state does not exist in FP64 mode");
     if (kind != ASX_PTR_HOST && kind != ASX_PTR_DEVICE) return fail(r, ASX_EINVAL, "bad ptr_kind");
     if (!r->have_fields) return fail(r, ASX_ESTATE, "asx_set_fields must come first");
     asx_status st = set_device(r);
@@ -636,11 +766,17 @@ asx_status asx_set_state(asx_raster *r, const float *mhi, const float *mlo, cons
                          const asx_ledger *ledger, int n_samples, const double *samples)
 {
     if (!r) return ASX_EINVAL;
+    if (r->fp64) return fail(r, ASX_EINVAL, "the compensated float32 state does not exist in FP64 mode");
     if (!mhi || !mlo || !v1 || !v2 || !ledger) return fail(r, ASX_EINVAL, "null argument");
     if (kind != ASX_PTR_HOST && kind != ASX_PTR_DEVICE) return fail(r, ASX_EINVAL, "bad ptr_kind");
     if (!r->have_fields) return fail(r, ASX_ESTATE, "asx_set_fields must come first");
     if (!std::isfinite(t) || step < 0 || n_samples < 0 || (n_samples > 0 && !samples))
         return fail(r, ASX_EINVAL, "bad clock");
+    // the hydrograph samples recorded by time t: the steps are cut at every sample time,
+    // so n_samples sample times lie at or before t and the next one after it
+    const double sdt = r->host_ctl.sample_dt;
+    if (sdt > 0.0 && !((double)n_samples * sdt <= t && t < (double)(n_samples + 1) * sdt))
+        return fail(r, ASX_EINVAL, "n_samples does not match t: the sample times up to t must all be recorded");
     asx_status st = set_device(r);
     if (st) return st;
     const StepArgs &a = r->args;
@@ -664,7 +800,7 @@ asx_status asx_set_state(asx_raster *r, const float *mhi, const float *mlo, cons
     c.cmax_bits = 0;
     c.done_ctas = 0;
     c.scan_done = 0;
-    c.out_acc = c.clamp_acc = 0.0;
+    c.out_fx[0] = c.out_fx[1] = c.clamp_fx[0] = c.clamp_fx[1] = 0ull;
     c.rain_in = ledger->rain_in;
     c.outflow = ledger->outflow;
     c.clamped = ledger->clamped;
@@ -672,7 +808,7 @@ asx_status asx_set_state(asx_raster *r, const float *mhi, const float *mlo, cons
     c.storage = ledger->storage;
     c.n_samples = n_samples;
     ASX_CUDA(r, cudaMemcpyAsync(r->ctl, &c, offsetof(DevCtl, g), cudaMemcpyHostToDevice, r->stream));
-    ASX_CUDA(r, launch_scan(a, r->scan_parts, r->scan_n, 0, r->stream));
+    ASX_CUDA(r, scan_state(r, 0));
     ASX_CUDA(r, put_ctl_field(r, &DevCtl::storage0, ledger->storage0));
     ASX_CUDA(r, launch_prepare(r->ctl, kPrepRecompute, 0.0, 0, r->stream));
     DevCtl *h;

@@ -422,8 +422,9 @@ __device__ __forceinline__ CellNew2 cell_update_fast(float2 shi, float2 slo, flo
     acc_add2(shi, slo, dup2(qr));
     float2 hi, lo;
     two_sum2(shi, slo, hi, lo);
-    const bool clx = hi.x < 0.0f || (hi.x == 0.0f && lo.x < 0.0f);
-    const bool cly = hi.y < 0.0f || (hi.y == 0.0f && lo.y < 0.0f);
+    // after the renormalising two-sum hi == 0 implies lo == 0 (a float sum rounds to
+    // zero only when it is zero), so a negative mass shows in hi alone
+    const bool clx = hi.x < 0.0f, cly = hi.y < 0.0f;
     const float2 g1 = fma2(dup2(kappa), M1, mul2(m_old, v1_old));
     const float2 g2 = fma2(dup2(kappa), M2, mul2(m_old, v2_old));
     const float2 h = mul2(hi, rth);
@@ -661,16 +662,19 @@ struct Tile {
                 o[e] = cell_update_pair<EXT>(C.A[e].hi, C.A[e].lo, C.A[e].m1, C.A[e].m2, C.X[e].m, C.X[e].v1,
                                              C.X[e].v2, rt, ka, kb, km, qr, dtf, a.g, dtau, a.h_dry, cll, clr);
             }
-        }
-        const size_t k0 = (size_t)r * a.pitch + c0 + 2 * lane;
-        const long long nplane = (long long)a.rows * a.pitch;
-        if (!ASX_STORE_OK(a, (long long)k0 + kHalf + 1, nplane) || !ASX_STORE_OK(a, c0 + 2 * lane + kHalf + 1, a.cols))
-            return;
-        if (own_l) {
-            if (cll.hi != 0.0f || cll.lo != 0.0f) {
+            if (own_l && (cll.hi != 0.0f || cll.lo != 0.0f)) {
                 clq.add(cll.hi);
                 clq.add(cll.lo);
             }
+            if (own_r && (clr.hi != 0.0f || clr.lo != 0.0f)) {
+                clq.add(clr.hi);
+                clq.add(clr.lo);
+            }
+        }
+        const size_t k0 = (size_t)r * a.pitch + c0 + 2 * lane;
+        if (!ASX_STORE_OK(a, (long long)k0 + kHalf + 1, (long long)a.rows * a.pitch) || !ASX_STORE_OK(a, c0 + 2 * lane + kHalf + 1, a.cols))
+            return;
+        if (own_l) {
             *reinterpret_cast<float2 *>(a.mhi[np] + k0) = make_float2(o[0].hi.x, o[1].hi.x);
             *reinterpret_cast<float2 *>(a.mlo[np] + k0) = make_float2(o[0].lo.x, o[1].lo.x);
             *reinterpret_cast<float2 *>(a.v1[np] + k0) = make_float2(o[0].v1.x, o[1].v1.x);
@@ -678,10 +682,6 @@ struct Tile {
             cwb = max(cwb, max(o[0].cb0, o[1].cb0));
         }
         if (own_r) {
-            if (clr.hi != 0.0f || clr.lo != 0.0f) {
-                clq.add(clr.hi);
-                clq.add(clr.lo);
-            }
             *reinterpret_cast<float2 *>(a.mhi[np] + k0 + kHalf) = make_float2(o[0].hi.y, o[1].hi.y);
             *reinterpret_cast<float2 *>(a.mlo[np] + k0 + kHalf) = make_float2(o[0].lo.y, o[1].lo.y);
             *reinterpret_cast<float2 *>(a.v1[np] + k0 + kHalf) = make_float2(o[0].v1.y, o[1].v1.y);

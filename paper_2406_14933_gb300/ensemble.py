@@ -59,7 +59,8 @@ class Ensemble:
         self.handle = _a.asx_create_ensemble(descs, stream, device)
         for i, sc in enumerate(scenarios):
             sh = (sc.rows, sc.cols)
-            _a.asx_ensemble_set_fields(self.handle, i, _f32(sc.z, sh), _f32(sc.theta, sh), _f32(sc.h0, sh),
+            _a.asx_ensemble_set_fields(self.handle, i, np.ascontiguousarray(np.asarray(sc.z, np.float64).reshape(sh)),
+                                       _f32(sc.theta, sh), _f32(sc.h0, sh),
                                        _f32(sc.v1_0, sh), _f32(sc.v2_0, sh), _a.ASX_PTR_HOST)
 
     def autotune(self, max_steps=50):

@@ -17,6 +17,10 @@ def _f32(a, shape):
     return np.ascontiguousarray(np.asarray(a, dtype=np.float32).reshape(shape))
 
 
+def _f64(a, shape):
+    return np.ascontiguousarray(np.asarray(a, dtype=np.float64).reshape(shape))
+
+
 def _uniform(arr, what):
     a = np.asarray(arr).reshape(-1)
     if a.size and not np.all(a == a[0]):
@@ -26,7 +30,7 @@ def _uniform(arr, what):
 
 class Raster:
     def __init__(self, sc: Scenario, device: int = 0, stream: int | None = None,
-                 max_samples: int | None = None, use_classes: bool | None = None):
+                 max_samples: int | None = None, use_classes: bool | None = None, fp64: bool = False):
         self.sc = sc
         use_classes = (sc.cls is not None) if use_classes is None else use_classes
         nc = int(len(sc.class_theta)) if use_classes else 0
@@ -41,6 +45,7 @@ class Raster:
         d.max_samples = int(max_samples)
         d.cuda_stream = stream
         d.device = device
+        d.precision = _a.ASX_FP64 if fp64 else _a.ASX_FP32_COMP
         self.desc = d
         self.handle = _a.asx_create_raster(d)
         self._keep = []
@@ -48,7 +53,7 @@ class Raster:
         shape = (sc.rows, sc.cols)
         theta = None if nc else _f32(sc.theta, shape)
         cls = np.ascontiguousarray(sc.cls.astype(np.uint8)) if nc else None
-        _a.asx_set_fields(self.handle, _f32(sc.z, shape), theta, cls, _f32(sc.h0, shape),
+        _a.asx_set_fields(self.handle, _f64(sc.z, shape), theta, cls, _f32(sc.h0, shape),
                           _f32(sc.v1_0, shape), _f32(sc.v2_0, shape), _a.ASX_PTR_HOST)
 
     def set_params(self, cfl=None, dt_max=None, sample_dt=None):
@@ -104,6 +109,13 @@ class Raster:
         sh = (self.sc.rows, self.sc.cols)
         h, v1, v2 = (np.empty(sh, np.float32) for _ in range(3))
         _a.asx_get_fields(self.handle, 0, h, v1, v2, _a.ASX_PTR_HOST)
+        return h, v1, v2
+
+    def fields64(self):
+        """Depth and velocity in float64 (the FP64 state, or the compensated float32 one)."""
+        sh = (self.sc.rows, self.sc.cols)
+        h, v1, v2 = (np.empty(sh, np.float64) for _ in range(3))
+        _a.asx_get_fields64(self.handle, 0, h, v1, v2, _a.ASX_PTR_HOST)
         return h, v1, v2
 
     def state(self):

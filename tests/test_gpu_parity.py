@@ -78,27 +78,68 @@ def test_one_step_matches_oracle(asx, orc, rows, cols, bc):
                                           (77, 130, (0, 1, 0, 1)), (66, 270, (1, 1, 0, 1))])
 @pytest.mark.parametrize("rough", [False, True])
 def test_many_steps_with_dt_replay(asx, orc, rows, cols, bc, rough):
-    """The oracle replays the GPU's time levels.  Budget defect <= 1e-10.
-    On a smooth random bed, 200 steps: depth and discharge relative L2 <= 1e-4 (the stated
-    target).  On a bed drawn independently per cell (a step of up to 0.2 m at every edge,
-    30 % of the cells dry) the flow is chaotic: the wet/dry and upwind decisions of
-    Eqs. fvm_2D_eq.05-06 at the fronts amplify float32-vs-float64 rounding, and
-    neighbouring dry cells pick up velocities of order 1 m/s from the pressure term.  There
-    30 steps are checked, depth to 1e-4 and discharge to 1e-3."""
-    n_steps = 30 if rough else 200
+    """200 steps; the oracle replays the GPU's time levels.  Budget defect <= 1e-10.
+
+    Smooth random bed: depth and discharge relative L2 <= 1e-4 at step 200 (the stated
+    target).
+
+    Bed drawn independently per cell (a step of up to 0.2 m at every edge, 30 % of the
+    cells dry): every one of the 200 GPU steps is replayed by the oracle from the GPU's
+    own state and agrees to 2e-6 of each field's largest value (local parity, measured
+    ~2.5e-7); the trajectories agree to 1e-4 at step 30.  Later a front decision can
+    switch (Eqs. fvm_2D_eq.05-06): the FP64 oracle itself, disturbed by float32-sized
+    rounding at every step, then moves up to 1e-4 .. 3e-2 from its undisturbed run
+    (tests/envelope.py).  At step 200 the GPU is held to the larger of 1e-4 and that
+    envelope (twice the largest of its 12 seeded runs: a sample of the distribution of
+    outcomes, not its maximum), measured here on the same raster and time levels."""
+    from envelope import per_step_envelope
     sc = inputs.tiny(rows, cols, seed=99 + rows, bc=bc, rain_mm_h=40.0, smooth=not rough)
     R = _raster(asx, sc)
-    ts = [R.step(1) for _ in range(n_steps)]
     p = _oracle_problem(orc, sc)
-    res = p.run(p.mass(sc.h0), sc.v1_0, sc.v2_0, 0.0, ts[-1], t_replay=np.array(ts))
-    assert res["steps"] == n_steps
+    ts, local = [], 0.0
+    snap = {}
+    t = 0.0
+    for k in range(200):
+        if rough:
+            mg, vg1, vg2 = R.mass64()
+            mg, vg1, vg2 = mg.ravel(), vg1.ravel().astype(np.float64), vg2.ravel().astype(np.float64)
+        tn = R.step(1)
+        ts.append(tn)
+        if rough:
+            lm, l1, l2 = p.step(mg, vg1, vg2, tn - t, tn)
+            mn, wn1, wn2 = R.mass64()
+            mn = mn.ravel()
+            dq = np.concatenate([mn * wn1.ravel() - lm * l1, mn * wn2.ravel() - lm * l2])
+            sq = max(np.abs(np.concatenate([lm * l1, lm * l2])).max(), 1e-30)
+            local = max(local, float(np.abs(dq).max() / sq), float(np.abs(mn - lm).max() / max(np.abs(lm).max(), 1e-30)))
+            if k + 1 == 30:
+                snap[30] = (mn.copy(), wn1.copy(), wn2.copy())
+        t = tn
     mg, vg1, vg2 = R.mass64()
-    ho, hg = p.depth(res["m"]), p.depth(mg.ravel())
-    qo = np.concatenate([res["m"] * res["v1"], res["m"] * res["v2"]])
-    qg = np.concatenate([mg.ravel() * vg1.ravel(), mg.ravel() * vg2.ravel()])
-    eh, eq = _rel_l2(hg, ho), _rel_l2(qg, qo)
-    print(f"[parity] {rows}x{cols} rough={rough}: depth {eh:.2e} discharge {eq:.2e}")
-    assert eh <= 1e-4 and eq <= (1e-3 if rough else 1e-4)
+    m0, a0, b0 = p.mass(sc.h0), sc.v1_0.ravel().astype(np.float64), sc.v2_0.ravel().astype(np.float64)
+
+    def errs(m, v1, v2, res):
+        m = np.asarray(m, np.float64).ravel()
+        qo = np.concatenate([res["m"] * res["v1"], res["m"] * res["v2"]])
+        qg = np.concatenate([m * np.asarray(v1, np.float64).ravel(), m * np.asarray(v2, np.float64).ravel()])
+        return _rel_l2(p.depth(m), p.depth(res["m"])), _rel_l2(qg, qo)
+
+    if not rough:
+        res = p.run(m0, sc.v1_0, sc.v2_0, 0.0, ts[-1], t_replay=np.array(ts))
+        assert res["steps"] == 200
+        eh, eq = errs(mg, vg1, vg2, res)
+        print(f"[parity] {rows}x{cols} smooth: depth {eh:.2e} discharge {eq:.2e}")
+        assert eh <= 1e-4 and eq <= 1e-4
+    else:
+        res30 = p.run(m0, sc.v1_0, sc.v2_0, 0.0, ts[29], t_replay=np.array(ts[:30]))
+        eh30, eq30 = errs(*snap[30], res30)
+        env_h, env_q, res = per_step_envelope(p, m0, a0, b0, ts)
+        eh, eq = errs(mg, vg1, vg2, res)
+        print(f"[parity] {rows}x{cols} rough: local {local:.2e}; step 30 depth {eh30:.2e} discharge {eq30:.2e}; "
+              f"step 200 depth {eh:.2e} discharge {eq:.2e}, oracle envelope depth {env_h:.2e} discharge {env_q:.2e}")
+        assert local <= 2e-6
+        assert eh30 <= 1e-4 and eq30 <= 1e-4
+        assert eh <= max(1e-4, 2.0 * env_h) and eq <= max(1e-4, 2.0 * env_q)
     assert R.ledger().defect_rel <= 1e-10
     R.close()
 
@@ -205,8 +246,40 @@ def test_resume_is_bitwise(asx):
     for a, b in zip(ref, out):
         assert np.array_equal(a, b)
     assert R2.clock() == R.clock()
+    # the ledger continues bit for bit: every step's outflow and clamp sums are exact
+    # integer sums of the CTA partials, independent of the order the CTAs finish in
+    l1, l2 = R.ledger(), R2.ledger()
+    for k in ("rain_in", "outflow", "clamped", "storage", "storage0"):
+        assert getattr(l1, k) == getattr(l2, k), k
+    n0 = len(cum)
+    q1, q2 = R.hydrograph(), R2.hydrograph()
+    assert len(q1) == len(q2) > n0 + 2
+    assert np.array_equal(q1[n0 + 1:], q2[n0 + 1:])
     R.close()
     R2.close()
+
+
+@pytest.mark.parametrize("variant", ["strip", "gather"])
+def test_ledger_and_hydrograph_are_deterministic(asx, monkeypatch, variant):
+    """Two runs of the same raster, in fresh handles, give the same ledger and outlet
+    hydrograph bit for bit: outflow crosses free sides in many CTAs of every step, and
+    their partial sums are combined exactly."""
+    monkeypatch.setenv("ASX_STEP_KERNEL", variant)
+    sc = inputs.tiny(300, 700, seed=31, bc=(1, 1, 1, 1), rain_mm_h=80.0, smooth=True)
+    sc.sample_dt = 2.0
+    sc.t_end = 40.0
+    runs = []
+    for _ in range(2):
+        R = _raster(asx, sc)
+        R.run_until(sc.t_end)
+        led = R.ledger()
+        runs.append(((led.rain_in, led.outflow, led.clamped, led.storage), R.hydrograph(), R.state()))
+        R.close()
+    (la, qa, sa), (lb, qb, sb) = runs
+    assert la == lb and la[1] > 0
+    assert np.array_equal(qa, qb) and len(qa) == 20
+    for a, b in zip(sa, sb):
+        assert np.array_equal(a, b)
 
 
 def test_device_pointer_inputs_and_numeric_error(asx):
@@ -217,7 +290,8 @@ def test_device_pointer_inputs_and_numeric_error(asx):
     sc = inputs.tiny(24, 40, seed=4, bc=(1, 1, 1, 1))
     R = _raster(asx, sc)
     dev = {k: torch.from_numpy(np.ascontiguousarray(getattr(sc, k))).cuda()
-           for k in ("z", "theta", "h0", "v1_0", "v2_0")}
+           for k in ("theta", "h0", "v1_0", "v2_0")}
+    dev["z"] = torch.from_numpy(np.ascontiguousarray(sc.z, np.float64)).cuda()
     A.asx_set_fields(R.handle, dev["z"], dev["theta"], None, dev["h0"], dev["v1_0"], dev["v2_0"],
                      A.ASX_PTR_DEVICE)
     torch.cuda.synchronize()
@@ -261,16 +335,24 @@ def test_invalid_arguments(asx):
     with pytest.raises(A.AsxError) as e:
         R.step(-1)
     assert e.value.status == A.ASX_EINVAL
+    z64 = np.ascontiguousarray(sc.z, np.float64)
     bad = sc.h0.copy()
     bad[0, 0] = -1.0
     with pytest.raises(A.AsxError) as e:
-        A.asx_set_fields(R.handle, sc.z, sc.theta, None, bad, sc.v1_0, sc.v2_0, A.ASX_PTR_HOST)
+        A.asx_set_fields(R.handle, z64, sc.theta, None, bad, sc.v1_0, sc.v2_0, A.ASX_PTR_HOST)
     assert e.value.status == A.ASX_EINVAL
     th = sc.theta.copy()
     th[1, 1] = 0.0
     with pytest.raises(A.AsxError) as e:
-        A.asx_set_fields(R.handle, sc.z, th, None, sc.h0, sc.v1_0, sc.v2_0, A.ASX_PTR_HOST)
+        A.asx_set_fields(R.handle, z64, th, None, sc.h0, sc.v1_0, sc.v2_0, A.ASX_PTR_HOST)
     assert e.value.status == A.ASX_EINVAL
+    zb = z64.copy()
+    zb[2, 3] = np.inf
+    with pytest.raises(A.AsxError) as e:
+        A.asx_set_fields(R.handle, zb, sc.theta, None, sc.h0, sc.v1_0, sc.v2_0, A.ASX_PTR_HOST)
+    assert e.value.status == A.ASX_EINVAL
+    with pytest.raises(TypeError):                  # a float32 bed is refused by the binding
+        A.asx_set_fields(R.handle, sc.z, sc.theta, None, sc.h0, sc.v1_0, sc.v2_0, A.ASX_PTR_HOST)
     with pytest.raises(A.AsxError):
         R.set_params(cfl=1.5)
     R.close()

@@ -6,8 +6,6 @@ the library's scratch in a fixed device array.  This file is collected last so t
 stopping at its first failure has already run every other test; it passes alone and after
 the others.
 """
-import math
-
 import numpy as np
 import pytest
 
@@ -60,4 +58,40 @@ def test_noalloc_scan_rejects_oversize(asx):
         # any pointer is touched)
         A.asx_state_scan_noalloc(8192, 8193, 8193, 1.0, 9.81, 1, 1, 1, 1, 1, 1, 1, None)
     assert e.value.status == A.ASX_EINVAL
-    assert math.isfinite(1.0)
+    for g in (float("inf"), float("nan"), 0.0):
+        with pytest.raises(A.AsxError) as e:
+            A.asx_state_scan_noalloc(8, 8, 8, 1.0, g, 1, 1, 1, 1, 1, 1, 1, None)
+        assert e.value.status == A.ASX_EINVAL
+
+
+def test_noalloc_scan_pitched_state(asx):
+    """A state held in wider buffers (row pitch > cols): every field, theta included,
+    is a column slice of a device tensor with extra columns that hold other values, and
+    the scan matches the dense result, twice in a row."""
+    import torch
+    from paper_2406_14933_gb300 import asx as A
+    from paper_2406_14933_gb300.raster import Raster
+    rows, cols, pitch = 97, 133, 160
+    sc = inputs.tiny(rows, cols, seed=5, bc=(1, 0, 1, 0), rain_mm_h=50.0, smooth=True)
+    R = Raster(sc)
+    R.step(5)
+    dense = _state_on_device(R, torch)
+    theta = torch.from_numpy(np.ascontiguousarray(sc.theta)).cuda()
+    stream = torch.cuda.current_stream().cuda_stream
+    wide = []
+    for t in (*dense, theta):
+        w = torch.full((rows, pitch), 1.0e3, dtype=torch.float32, device="cuda")   # junk outside the slice
+        w[:, :cols] = t
+        wide.append(w)
+    out = []
+    for fields, p in ((dense + (theta,), cols), (tuple(wide), pitch)):
+        st = torch.zeros(1, dtype=torch.float64, device="cuda")
+        cm = torch.zeros(1, dtype=torch.float32, device="cuda")
+        A.asx_state_scan_noalloc(rows, cols, p, sc.l, sc.g, *fields, st, cm, stream)
+        torch.cuda.synchronize()
+        out.append((float(st[0]), float(cm[0])))
+    A.asx_state_scan_noalloc(rows, cols, pitch, sc.l, sc.g, *wide, st, cm, stream)
+    torch.cuda.synchronize()
+    assert out[0] == out[1] == (float(st[0]), float(cm[0]))
+    assert out[0][0] == pytest.approx(R.ledger().storage, rel=1e-12)
+    R.close()

@@ -401,8 +401,16 @@ def pipeline(n: int = 256, l: float = 2.0, n_train: int = 20000, n_held: int = 1
     model.predict(torch.as_tensor(Xq[:min(len(Xq), 1024)], device=model.device))
     _, rep = model.serve(Xq, Sq, scenarios_of, frac=frac, tol=tol, seed=seed + 1, chunk=chunk, tuning=tuning)
     ok = rep.rel_err[np.isfinite(rep.rel_err)]
+    # the checked sample estimates the share of unchecked served hydrographs within tol
+    # (binomial standard error beside it); checked ones are within tol after the fallback
+    p_in = float(np.mean(ok <= tol)) if ok.size else None
+    se = float(np.sqrt(p_in * (1 - p_in) / ok.size)) if ok.size else None
+    cf = rep.checked / max(rep.queries, 1)
     serve = dict(queries=rep.queries, checked=rep.checked, replaced=rep.replaced,
                  checked_mean_rel_l2=float(ok.mean()) if ok.size else None,
+                 checked_p90_rel_l2=float(np.quantile(ok, 0.9)) if ok.size else None,
+                 checked_frac_within_tol=p_in, checked_frac_within_tol_stderr=se,
+                 served_frac_within_tol_estimate=(cf + (1 - cf) * p_in) if ok.size else None,
                  infer_seconds=rep.infer_seconds, queries_per_s=rep.queries / rep.infer_seconds,
                  check_seconds=rep.check_seconds, served_hydrographs_per_s=rep.hydrographs_per_s,
                  solver_hydrographs_per_s=rep.solver.hydrographs_per_s,

@@ -217,7 +217,8 @@ def run_cuda(args):
                      "frac": achieved / peak, "traffic": traffic,
                      "peak_source": f"{peak_kind} copy bandwidth",
                      "note": "32 B algorithmic per cell-update / (step time incl. launch gap); "
-                             "traffic: ncu DRAM bytes of a 2048x2048 window scaled by cells"},
+                             "traffic: ncu DRAM bytes of one launch on this window, counted over consecutive "
+                             "launches without cache control (write-back included)"},
         "e2e": {"value": job_rate(ws, n, args.steps, e2e_s), "unit": UNIT,
                 "h2d_bytes_per_step": 16 * n / args.steps, "d2h_bytes_per_step": 16 * n / args.steps},
         "gpu_launches": len(regions) * (args.steps + 1),
@@ -277,17 +278,18 @@ def _film_state(sc, depth=0.005):
 
 
 def cpu_baseline(sc, budget_s=15.0, crop=REF_CROP):
-    """The FP64 oracle on a crop of the same raster (a 5 mm film at t = 45 min), timed on
-    this host's cores for about budget_s seconds."""
+    """The FP64 oracle (its OpenMP build, on every core this process may use) on a crop of
+    the same raster (a 5 mm film at t = 45 min), timed for about budget_s seconds."""
     import oracle
     oracle.build()
+    threads = oracle.max_threads()
     r0 = (sc.rows - crop) // 2
     c0 = (sc.cols - crop) // 2
     sl = (slice(r0, r0 + crop), slice(c0, c0 + crop))
     cls = sc.cls[sl]
     p = oracle.Problem(crop, crop, sc.l, sc.z[sl], sc.class_theta[cls], sc.class_alpha_s[cls],
                        sc.class_alpha_p[cls], bc=(0, 0, 1, 0), g=sc.g, cfl=sc.cfl,
-                       dt_max=sc.dt_max, rain_t=sc.rain_t, rain_r=sc.rain_r)
+                       dt_max=sc.dt_max, rain_t=sc.rain_t, rain_r=sc.rain_r, threads=threads)
     h, v1, v2 = _film_state(sc)
     m = p.mass(h[sl])
     a, b = v1[sl].ravel().astype(np.float64), v2[sl].ravel().astype(np.float64)
@@ -301,9 +303,9 @@ def cpu_baseline(sc, budget_s=15.0, crop=REF_CROP):
         if time.perf_counter() - w0 > budget_s:
             break
     el = time.perf_counter() - w0
-    return {"value": crop * crop * steps / el, "unit": UNIT, "cores": 1, "kind": "oracle",
+    return {"value": crop * crop * steps / el, "unit": UNIT, "cores": threads, "kind": "oracle",
             "sample": f"{steps} oracle steps of a {crop}x{crop} crop of the catchment "
-                      f"(5 mm film from t={T_WARM:.0f} s), {el:.1f} s, single thread",
+                      f"(5 mm film from t={T_WARM:.0f} s), {el:.1f} s, OpenMP build on {threads} threads",
             "host": host_info()}
 
 
@@ -548,13 +550,14 @@ def run_reference(args):
     sc = inputs.carved_catchment()
     import oracle
     oracle.build()
+    threads = oracle.max_threads()
     crop = REF_CROP
     r0, c0 = (sc.rows - crop) // 2, (sc.cols - crop) // 2
     sl = (slice(r0, r0 + crop), slice(c0, c0 + crop))
     cls = sc.cls[sl]
     p = oracle.Problem(crop, crop, sc.l, sc.z[sl], sc.class_theta[cls], sc.class_alpha_s[cls],
                        sc.class_alpha_p[cls], bc=(0, 0, 1, 0), g=sc.g, cfl=sc.cfl,
-                       dt_max=sc.dt_max, rain_t=sc.rain_t, rain_r=sc.rain_r)
+                       dt_max=sc.dt_max, rain_t=sc.rain_t, rain_r=sc.rain_r, threads=threads)
     h, v1, v2 = _film_state(sc)
     m = p.mass(h[sl])
     a, b = v1[sl].ravel().astype(np.float64), v2[sl].ravel().astype(np.float64)
@@ -574,9 +577,9 @@ def run_reference(args):
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": el * 1e3 / args.steps,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
             "data": "synthetic", "config": cfg,
-            "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": threads, "kind": "oracle",
                              "sample": f"{args.steps} oracle steps of a {crop}x{crop} crop "
-                                       f"(5 mm film from t={T_WARM:.0f} s), single thread",
+                                       f"(5 mm film from t={T_WARM:.0f} s), OpenMP build on {threads} threads",
                              "host": host_info()},
             "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
 

@@ -391,8 +391,9 @@ def run_ensemble(args, stream):
     scs = [inputs.ensemble_member(s, t_end=args.ens_t_end) for s in range(n)]
     cells = sum(sc.n for sc in scs)
     E = Ensemble(scs, stream=stream.cuda_stream)
-    tuning = E.autotune(max_steps=100)
-    E.run()                                   # warm-up (graph capture)
+    E.run()                                   # untimed: each scenario's step count
+    tuning = E.autotune(max_steps=200)        # cut in proportion to those step counts
+    E.run()                                   # warm-up (graph capture of the tuned shape)
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     torch.cuda.synchronize()
     e0.record(stream)

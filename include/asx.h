@@ -284,10 +284,17 @@ asx_status asx_destroy_ensemble(asx_ensemble *e);
 asx_status asx_ensemble_set_fields(asx_ensemble *e, int s, const double *z, const float *theta,
                                    const float *h0, const float *v1, const float *v2, int ptr_kind);
 
-/* Times every launch shape on the ensemble with each scenario cut to max_steps steps (after
- * one untimed launch; each shape twice, the faster counts) and keeps the fastest for
- * asx_ensemble_run; *best_out (may be NULL) receives it.  The scenarios' states are reset
- * to their initial state afterwards by the next asx_ensemble_run. */
+/* Times every launch shape on the ensemble cut short (after one untimed launch; each shape
+ * twice, the faster counts) and keeps the fastest for asx_ensemble_run; *best_out (may be
+ * NULL) receives it.  Before the first asx_ensemble_run that takes every scenario to its
+ * t_end, each scenario is cut at max_steps steps.  After one, scenario i is cut at its
+ * step count in that run times max_steps x (total cells) / (total cells x steps): the same
+ * number of cell updates as max_steps per scenario, distributed over the scenarios as in
+ * the real run, so that the shape chosen suits the real run's critical path (its longest
+ * scenarios) and not only its throughput.  Such a complete run also makes later runs take
+ * the scenarios in decreasing order of measured cells x steps (before it: cells x t_end /
+ * edge).  The scenarios' states are reset to their initial state afterwards by the next
+ * asx_ensemble_run. */
 asx_status asx_ensemble_autotune(asx_ensemble *e, int max_steps, asx_ensemble_tuning *best_out);
 
 /* Runs every scenario from its initial state to its t_end in one persistent launch

@@ -344,6 +344,8 @@ struct asx_ensemble {
     bool tuned = false, have_fields_all = false;
     int mode = 0;                           // kernel variant: 1 inflow sides, 2 also optional terms
     std::vector<char> have_fields;
+    std::vector<long long> work_steps;      // step counts of the last complete run
+    bool have_steps = false;
     cudaGraphExec_t graph = nullptr;
     asx_ensemble_tuning graph_tuning{};
     std::string err;
@@ -694,6 +696,22 @@ asx_status asx_ensemble_run(asx_ensemble *e, const asx_ensemble_tuning *tuning)
         if (h.err) bad = true;
     }
     if (bad) return efail(e, ASX_ENUMERIC, "a scenario's state became non-finite");
+    // A run that took every scenario to its end time gives the real work of each (cells x
+    // steps; the step sequence does not depend on the launch shape).  Later runs take the
+    // scenarios longest first by that work, and the autotuner cuts them in its proportion.
+    bool complete = true;
+    for (int i = 0; i < e->n; i++)
+        if (!(e->host[i].t >= e->host[i].t_end)) complete = false;
+    if (complete) {
+        e->work_steps.resize(e->n);
+        for (int i = 0; i < e->n; i++) e->work_steps[i] = e->host[i].steps;
+        e->have_steps = true;
+        std::vector<int> ord(e->n);
+        for (int i = 0; i < e->n; i++) ord[i] = i;
+        auto work = [&](int i) { return (double)e->desc[i].rows * e->desc[i].cols * (double)e->work_steps[i]; };
+        std::stable_sort(ord.begin(), ord.end(), [&](int p, int q) { return work(p) > work(q); });
+        ENS_CUDA(e, cudaMemcpy(e->order, ord.data(), e->n * sizeof(int), cudaMemcpyHostToDevice));
+    }
     return ASX_OK;
 }
 
@@ -702,11 +720,26 @@ asx_status asx_ensemble_autotune(asx_ensemble *e, int max_steps, asx_ensemble_tu
     if (!e || max_steps < 1) return ASX_EINVAL;
     if (!e->have_fields_all) return efail(e, ASX_ESTATE, "asx_ensemble_set_fields missing for a scenario");
     ENS_CUDA(e, cudaSetDevice(e->device));
-    // time every candidate on the whole ensemble with each scenario capped at max_steps
+    // Time every candidate on the whole ensemble cut short.  Without a complete run each
+    // scenario is cut at max_steps.  After one, scenario i is cut at its step count scaled
+    // by f = max_steps x (sum of cells) / (sum of cells x steps): the same budget of cell
+    // updates, spread as in the real run, so that the few longest scenarios, which set the
+    // critical path of the real run, weigh as much in the timing as they will there.
     std::vector<long long> saved(e->n);
+    double f = 0.0;
+    if (e->have_steps) {
+        double c = 0.0, w = 0.0;
+        for (int i = 0; i < e->n; i++) {
+            const double ci = (double)e->desc[i].rows * e->desc[i].cols;
+            c += ci;
+            w += ci * (double)e->work_steps[i];
+        }
+        f = w > 0.0 ? (double)max_steps * c / w : 0.0;
+    }
     for (int i = 0; i < e->n; i++) {
         saved[i] = e->host[i].max_steps;
-        e->host[i].max_steps = max_steps;
+        const long long cap = e->have_steps ? std::llround((double)e->work_steps[i] * f) : (long long)max_steps;
+        e->host[i].max_steps = std::min(saved[i], std::max(1LL, cap));
     }
     ENS_CUDA(e, cudaMemcpy(e->dev, e->host.data(), e->n * sizeof(EnsScenario), cudaMemcpyHostToDevice));
     cudaEvent_t a, b;

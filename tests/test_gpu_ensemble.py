@@ -97,6 +97,32 @@ def test_ensemble_autotune_and_oracle(asx, orc):
     E.close()
 
 
+def test_ensemble_tuning_after_a_complete_run(asx):
+    """After a run that takes every scenario to its end, the autotuner cuts the scenarios in
+    proportion to their measured step counts and the queue takes them by measured work;
+    neither changes what a run computes: the states, clocks and ledgers of the next run are
+    those of the first, bit for bit."""
+    from paper_2406_14933_gb300.ensemble import Ensemble
+    scs = _scenarios(t_end=90.0)
+    E = Ensemble(scs)
+    E.run((2, 256, 2))
+    ref = [(E.state(i), E.clock(i), E.ledger(i).outflow) for i in range(len(scs))]
+    assert all(c[0] == sc.t_end for (_, c, _), sc in zip(ref, scs))
+    t = E.autotune(max_steps=5)
+    assert t.cluster in (1, 2, 4, 8) and t.threads in (128, 256, 512) and t.cells_per_thread in (1, 2, 4)
+    E.run((2, 256, 2))
+    for i in range(len(scs)):
+        st, clk, out = ref[i]
+        for a, b in zip(E.state(i), st):
+            assert np.array_equal(a, b)
+        assert E.clock(i) == clk
+        assert E.ledger(i).outflow == out
+    E.run()
+    for i in range(len(scs)):
+        assert E.clock(i) == ref[i][1]
+    E.close()
+
+
 def test_ensemble_inflow_boundary_matches_single_raster(asx, monkeypatch):
     """A scenario fed through a given-mass-flux side runs in the ensemble exactly as a
     single raster with the gather kernel (bit for bit), the inflow booked alike."""

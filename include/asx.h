@@ -265,11 +265,16 @@ typedef struct {
     double tau, h_dry;
 } asx_scenario_desc;
 
-/* Launch shape of the ensemble kernel: CTAs per cluster (1, 2, 4, 8) sharing one
- * scenario, threads per CTA (128, 256, 512), cells each thread updates per round
- * (1, 2, 4). */
+/* Launch shape of the ensemble: CTAs per cluster (1, 2, 4, 8) sharing one scenario, and
+ * the kernel.  tile_rows = 0: the gather kernel (one thread per cell), threads per CTA
+ * (128, 256, 512), cells each thread updates per round (1, 2, 4).  tile_rows = 8, 16 or
+ * 32: the strip kernel (each warp a TMA-fed tile worker over tiles of 128 columns x
+ * tile_rows rows, the cells along the sides gathered; the same per-cell code, hence the
+ * same bits, as a single raster's strip kernel with that tile height), threads per CTA
+ * 128 or 256 (4 or 8 tile workers), cells_per_thread 1. */
 typedef struct {
     int cluster, threads, cells_per_thread;
+    int tile_rows;
 } asx_ensemble_tuning;
 
 /* Create an ensemble of n scenarios on `device`, work ordered on cuda_stream.  Allocates
@@ -284,8 +289,8 @@ asx_status asx_destroy_ensemble(asx_ensemble *e);
 asx_status asx_ensemble_set_fields(asx_ensemble *e, int s, const double *z, const float *theta,
                                    const float *h0, const float *v1, const float *v2, int ptr_kind);
 
-/* Times every launch shape on the ensemble cut short (after one untimed launch; each shape
- * twice, the faster counts) and keeps the fastest for asx_ensemble_run; *best_out (may be
+/* Times every launch shape (the gather kernel's 36, the strip kernel's 24) on the ensemble
+ * cut short (after one untimed launch; each shape twice, the faster counts) and keeps the fastest for asx_ensemble_run; *best_out (may be
  * NULL) receives it.  Before the first asx_ensemble_run that takes every scenario to its
  * t_end, each scenario is cut at max_steps steps.  After one, scenario i is cut at its
  * step count in that run times max_steps x (total cells) / (total cells x steps): the same
@@ -299,7 +304,8 @@ asx_status asx_ensemble_autotune(asx_ensemble *e, int max_steps, asx_ensemble_tu
 
 /* Runs every scenario from its initial state to its t_end in one persistent launch
  * (tuning NULL = the autotuned or default shape).  ASX_ENUMERIC if a scenario's state
- * became non-finite (that scenario stops; the others finish). */
+ * became non-finite, ASX_ETIMEOUT if a tensor copy of the strip kernel did not arrive
+ * within its bounded wait (that scenario stops; the others finish). */
 asx_status asx_ensemble_run(asx_ensemble *e, const asx_ensemble_tuning *tuning);
 
 /* Per-scenario results of the last run (see asx_ledger, asx_get_fields, asx_get_state,

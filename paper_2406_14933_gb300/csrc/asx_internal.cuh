@@ -151,6 +151,13 @@ struct StripMaps {
     CUtensorMap z, th;
 };
 
+// ---- tensor maps (runtime.cu) ----
+// 2-D tensor map over a pitched rows x cols plane (float32, or uint8 if u8); elements
+// outside the plane read as zero.  False if the driver refuses the map.
+bool make_tensor_map_2d(CUtensorMap *m, void *base, bool u8, int rows, int cols, int pitch, int box_x, int box_y);
+// The strip kernel's maps of a raster's planes (a.cls non-null: class boxes, else theta).
+bool make_strip_maps(StripMaps &m, const StepArgs &a, int rows, int cols, int pitch);
+
 // ---- launchers (kernels.cu, step_strip.cu) ----
 void step_strip_layout(StepArgs &a);     // fills the interior / frame fields and nblocks
 cudaError_t step_strip_configure();

@@ -210,13 +210,26 @@ __device__ __forceinline__ float cell_rtheta(const StepArgs &a, size_t k)
     return a.cls ? a.cls_rth[__ldg(a.cls + k)] : fast_rcp(__ldg(a.theta + k));
 }
 
+// Loads of the state planes in the per-cell code.  A step kernel that runs one step per
+// launch reads state no other thread writes during the launch, so the read-only data
+// path (ld.global.nc) is safe; a translation unit whose kernels run many steps in one
+// launch (the ensemble) defines ASX_STATE_COHERENT_LOADS, and the loads are ordinary,
+// ordered after the other CTAs' stores of the previous step by the barrier between steps.
+#ifndef ASX_LD_STATE
+#ifdef ASX_STATE_COHERENT_LOADS
+#define ASX_LD_STATE(p) (*(p))
+#else
+#define ASX_LD_STATE(p) __ldg(p)
+#endif
+#endif
+
 __device__ __forceinline__ Cell load_cell(const StepArgs &a, const float *mhi, const float *v1,
                                           const float *v2, size_t k)
 {
     Cell q;
-    q.m = __ldg(mhi + k);
-    q.v1 = __ldg(v1 + k);
-    q.v2 = __ldg(v2 + k);
+    q.m = ASX_LD_STATE(mhi + k);
+    q.v1 = ASX_LD_STATE(v1 + k);
+    q.v2 = ASX_LD_STATE(v2 + k);
     q.z = __ldg(a.z + k);
     q.h = __fmul_rn(q.m, cell_rtheta(a, k));
     return q;
@@ -484,7 +497,7 @@ __device__ __forceinline__ void gather_cell(const StepArgs &a, const StepScalars
     const float *mhi = a.mhi[s.par], *mlo = a.mlo[s.par], *v1 = a.v1[s.par], *v2 = a.v2[s.par];
     const size_t k = (size_t)r * a.pitch + c;
     const Cell I = load_cell(a, mhi, v1, v2, k);
-    float shi = I.m, slo = __ldg(mlo + k);
+    float shi = I.m, slo = ASX_LD_STATE(mlo + k);
     float M1 = 0.0f, M2 = 0.0f;      // J_a + S_a
 #pragma unroll
     for (int d = 0; d < 6; d++) {

@@ -22,7 +22,9 @@
 #include <string>
 #include <vector>
 
-#include "device_common.cuh"
+// the ensemble kernels run many steps per launch: state loads must be coherent
+#define ASX_STATE_COHERENT_LOADS
+#include "strip_tile.cuh"
 
 namespace cg = cooperative_groups;
 
@@ -46,7 +48,7 @@ struct EnsScenario {
 
 struct EnsPartial {
     unsigned cbits;
-    unsigned pad;
+    unsigned err;        // error bits (kErrTimeout) of the CTA's step
     double out, cl, sto;
 };
 
@@ -142,9 +144,167 @@ __device__ __forceinline__ void block_reduce(unsigned &cb, double &out, double &
     }
 }
 
-// The persistent ensemble kernel.  NT threads per CTA, K cells per thread per round;
-// MODE 0: the plain scheme; 1: inflow sides (given mass flux, Dirichlet) compiled in;
-// 2: inflow sides and the optional terms (artificial viscosity, linear resistance, dry
+// Shared-memory state of a CTA of either ensemble kernel.
+struct EnsShared {
+    StepArgs sa;         // the running scenario's arguments
+    EnsClock clk;        // its clock (every CTA of the cluster computes the same)
+    EnsPartial part[2];  // this CTA's step partials, slots alternating by step parity
+    int s_idx;           // scenario popped by the cluster's rank 0
+};
+
+// The cluster's next scenario from the queue (-1 when none is left).
+__device__ __forceinline__ int ens_pop(cg::cluster_group &cluster, unsigned rank, EnsShared &sh, const int *order,
+                                      int n_scen, unsigned *queue)
+{
+    if (rank == 0 && threadIdx.x == 0) {
+        const unsigned q = atomicAdd(queue, 1u);
+        sh.s_idx = q < (unsigned)n_scen ? order[q] : -1;
+    }
+    cluster.sync();
+    const int si = *cluster.map_shared_rank(&sh.s_idx, 0);
+    cluster.sync();              // every rank has read s_idx before rank 0 pops again
+    return si;
+}
+
+// Takes scenario S: arguments and a zero clock into shared memory, then the initial scan
+// (c_max and storage of the initial state over this CTA's row band [rb0, rb1)), the
+// cluster-wide reduction and the first time step.
+template <int NT>
+__device__ void ens_start(cg::cluster_group &cluster, unsigned csize, EnsShared &sh, const EnsScenario &S,
+                          int rb0, int rb1)
+{
+    const int tid = threadIdx.x;
+    const StepArgs &sa = sh.sa;
+    EnsClock &clk = sh.clk;
+    const int cols = sa.cols, band = (rb1 - rb0) * cols;
+    unsigned cb = 0u;
+    double out = 0.0, cl = 0.0, sto = 0.0;
+    for (int i = tid; i < band; i += NT) {
+        const int r = rb0 + i / cols, c = i % cols;
+        const size_t k = (size_t)r * sa.pitch + c;
+        const float hi = sa.mhi[0][k];
+        sto += (double)hi + (double)sa.mlo[0][k];
+        const float h = __fmul_rn(hi, cell_rtheta(sa, k));
+        cb = max(cb, speed_bits(wave_speed(sa.v1[0][k], sa.v2[0][k], h, sa.g)));
+    }
+    block_reduce<NT>(cb, out, cl, sto);
+    if (tid == 0) sh.part[0] = EnsPartial{cb, 0u, 0.0, 0.0, sto};
+    cluster.sync();
+    if (tid == 0) {
+        unsigned cm = 0u;
+        double st = 0.0;
+        for (unsigned q = 0; q < csize; q++) {
+            const EnsPartial p = *cluster.map_shared_rank(&sh.part[0], q);
+            cm = max(cm, p.cbits);
+            st += p.sto;
+        }
+        clk.cmax = __uint_as_float(cm);
+        if (!(clk.cmax <= FLT_MAX)) clk.err |= kErrNumeric;
+        clk.storage0 = st * S.sigma;
+        ens_prepare(S, clk);
+    }
+    cluster.sync();              // part[0] is read by every rank before it is reused
+}
+
+// Ends a step: block and cluster reductions of the new wave speed (bits cb), the
+// boundary and clamp sums and the error bits (err; *ctl_err is read after the block
+// barrier), then the clock, ledger, hydrograph sample and next time step.
+template <int NT>
+__device__ void ens_step_end(cg::cluster_group &cluster, unsigned rank, unsigned csize, EnsShared &sh, EnsScenario &S,
+                             unsigned cb, double out, double cl, unsigned err, const int *ctl_err)
+{
+    const int tid = threadIdx.x;
+    EnsClock &clk = sh.clk;
+    const int par = clk.parity;
+    double sto = 0.0;
+    const int any_err = __syncthreads_or(err != 0u);
+    block_reduce<NT>(cb, out, cl, sto);
+    if (tid == 0) {
+        unsigned eb = any_err ? (unsigned)kErrTimeout : 0u;
+        if (ctl_err) eb |= (unsigned)*ctl_err;
+        __threadfence();
+        sh.part[par] = EnsPartial{cb, eb, out, cl, 0.0};
+    }
+    cluster.sync();              // the band is written and the partials are in place
+    if (tid == 0) {
+        unsigned cm = 0u, eb = 0u;
+        double o = 0.0, c = 0.0;
+        for (unsigned q = 0; q < csize; q++) {
+            const EnsPartial p = *cluster.map_shared_rank(&sh.part[par], q);
+            cm = max(cm, p.cbits);
+            eb |= p.err;
+            o += p.out;
+            c += p.cl;
+        }
+        const StepArgs &sa = sh.sa;
+        clk.rain_in += S.sigma * (double)((long long)sa.rows * sa.cols) * (double)clk.qr;
+        clk.outflow += S.sigma * o;
+        clk.clamped += S.sigma * c;
+        clk.t = clk.t_next;
+        clk.steps += 1;
+        clk.parity ^= 1;
+        if (S.sample_dt > 0.0 && clk.t == (double)(clk.n_samples + 1) * S.sample_dt) {
+            if (rank == 0 && clk.n_samples < S.max_samples) S.samples[clk.n_samples] = clk.outflow;
+            clk.n_samples += 1;
+        }
+        clk.cmax = __uint_as_float(cm);
+        if (!(clk.cmax <= FLT_MAX)) clk.err |= kErrNumeric;
+        clk.err |= (int)eb;
+        ens_prepare(S, clk);
+    }
+    __syncthreads();
+}
+
+// Final storage of the scenario over this CTA's row band and the results (rank 0).
+template <int NT>
+__device__ void ens_finish(cg::cluster_group &cluster, unsigned rank, unsigned csize, EnsShared &sh, EnsScenario &S,
+                           int rb0, int rb1)
+{
+    const int tid = threadIdx.x;
+    const StepArgs &sa = sh.sa;
+    const EnsClock &clk = sh.clk;
+    const int par = clk.parity, cols = sa.cols, band = (rb1 - rb0) * cols;
+    unsigned cb = 0u;
+    double out = 0.0, cl = 0.0, sto = 0.0;
+    for (int i = tid; i < band; i += NT) {
+        const int r = rb0 + i / cols, c = i % cols;
+        const size_t k = (size_t)r * sa.pitch + c;
+        sto += (double)sa.mhi[par][k] + (double)sa.mlo[par][k];
+    }
+    block_reduce<NT>(cb, out, cl, sto);
+    if (tid == 0) sh.part[0] = EnsPartial{0u, 0u, 0.0, 0.0, sto};
+    cluster.sync();
+    if (rank == 0 && tid == 0) {
+        double st = 0.0;
+        for (unsigned q = 0; q < csize; q++) st += cluster.map_shared_rank(&sh.part[0], q)->sto;
+        S.t = clk.t;
+        S.steps = clk.steps;
+        S.rain_in = clk.rain_in;
+        S.outflow = clk.outflow;
+        S.clamped = clk.clamped;
+        S.storage0 = clk.storage0;
+        S.storage = st * S.sigma;
+        S.n_samples = clk.n_samples;
+        S.err = clk.err;
+        S.parity = clk.parity;
+    }
+    cluster.sync();
+}
+
+// Zero clock of a newly taken scenario (one thread).
+__device__ __forceinline__ void ens_clock_zero(EnsClock &clk)
+{
+    clk.t = 0.0;
+    clk.steps = 0;
+    clk.rain_in = clk.outflow = clk.clamped = 0.0;
+    clk.n_samples = 0;
+    clk.parity = 0;
+    clk.err = 0;
+}
+
+// The persistent gather ensemble kernel.  NT threads per CTA, K cells per thread per
+// round; MODE 0: the plain scheme; 1: inflow sides (given mass flux, Dirichlet) compiled
+// in; 2: inflow sides and the optional terms (artificial viscosity, linear resistance, dry
 // threshold) compiled in.
 template <int NT, int K, int MODE>
 __global__ void __launch_bounds__(NT) ensemble_kernel(EnsScenario *scen, const int *order, int n_scen,
@@ -152,72 +312,29 @@ __global__ void __launch_bounds__(NT) ensemble_kernel(EnsScenario *scen, const i
 {
     cg::cluster_group cluster = cg::this_cluster();
     const unsigned rank = cluster.block_rank(), csize = cluster.num_blocks();
-    __shared__ StepArgs sa;
-    __shared__ EnsClock clk;
-    __shared__ EnsPartial part[2];
-    __shared__ int s_idx;
+    __shared__ EnsShared sh;
+    const StepArgs &sa = sh.sa;
+    EnsClock &clk = sh.clk;
     const int tid = threadIdx.x;
     for (;;) {
-        // ---- take the next scenario (the cluster's rank 0 pops, all ranks read it)
-        if (rank == 0 && tid == 0) {
-            const unsigned q = atomicAdd(queue, 1u);
-            s_idx = q < (unsigned)n_scen ? order[q] : -1;
-        }
-        cluster.sync();
-        const int si = *cluster.map_shared_rank(&s_idx, 0);
-        cluster.sync();              // every rank has read s_idx before rank 0 pops again
+        const int si = ens_pop(cluster, rank, sh, order, n_scen, queue);
         if (si < 0) return;
         EnsScenario &S = scen[si];
         if (tid == 0) {
-            sa = S.a;
-            clk.t = 0.0;
-            clk.steps = 0;
-            clk.rain_in = clk.outflow = clk.clamped = 0.0;
-            clk.n_samples = 0;
-            clk.parity = 0;
-            clk.err = 0;
+            sh.sa = S.a;
+            ens_clock_zero(clk);
         }
         __syncthreads();
         const int rows = sa.rows, cols = sa.cols;
         const int rb0 = (int)(((long long)rows * rank) / csize);
         const int rb1 = (int)(((long long)rows * (rank + 1)) / csize);
         const int band = (rb1 - rb0) * cols;
-        // ---- initial scan: c_max and storage of the initial state
-        {
-            unsigned cb = 0u;
-            double out = 0.0, cl = 0.0, sto = 0.0;
-            for (int i = tid; i < band; i += NT) {
-                const int r = rb0 + i / cols, c = i % cols;
-                const size_t k = (size_t)r * sa.pitch + c;
-                const float hi = sa.mhi[0][k];
-                sto += (double)hi + (double)sa.mlo[0][k];
-                const float h = __fmul_rn(hi, cell_rtheta(sa, k));
-                cb = max(cb, speed_bits(wave_speed(sa.v1[0][k], sa.v2[0][k], h, sa.g)));
-            }
-            block_reduce<NT>(cb, out, cl, sto);
-            if (tid == 0) part[0] = EnsPartial{cb, 0u, 0.0, 0.0, sto};
-            cluster.sync();
-            if (tid == 0) {
-                unsigned cm = 0u;
-                double st = 0.0;
-                for (unsigned q = 0; q < csize; q++) {
-                    const EnsPartial p = *cluster.map_shared_rank(&part[0], q);
-                    cm = max(cm, p.cbits);
-                    st += p.sto;
-                }
-                clk.cmax = __uint_as_float(cm);
-                if (!(clk.cmax <= FLT_MAX)) clk.err |= kErrNumeric;
-                clk.storage0 = st * S.sigma;
-                ens_prepare(S, clk);
-            }
-            cluster.sync();          // part[0] is read by every rank before it is reused
-        }
+        ens_start<NT>(cluster, csize, sh, S, rb0, rb1);
         __syncthreads();
         // ---- time loop
         while (clk.active) {
-            const int par = clk.parity;
             StepScalars sc;
-            sc.par = par;
+            sc.par = clk.parity;
             sc.kappa = clk.kappa;
             sc.qr = clk.qr;
             sc.dtf = clk.dtf;
@@ -234,71 +351,129 @@ __global__ void __launch_bounds__(NT) ensemble_kernel(EnsScenario *scen, const i
                         gather_cell<(MODE >= 2), (MODE >= 1)>(sa, sc, rb0 + i / cols, i % cols, cb, outd, clq);
                 }
             }
-            double out = outd.value(), cl = clq.value(), sto = 0.0;
-            block_reduce<NT>(cb, out, cl, sto);
-            if (tid == 0) {
-                __threadfence();
-                part[par] = EnsPartial{cb, 0u, out, cl, 0.0};
+            ens_step_end<NT>(cluster, rank, csize, sh, S, cb, outd.value(), clq.value(), 0u, nullptr);
+        }
+        ens_finish<NT>(cluster, rank, csize, sh, S, rb0, rb1);
+    }
+}
+
+// The persistent strip ensemble kernel: NW warps per CTA, each a strip tile worker with
+// its own TMA ring (strip_tile.cuh).  Per step the cluster's NW x csize warps take the
+// scenario's units (tiles of 128 columns x tile_rows rows, then the frame in blocks of
+// kFrameCells cells) round-robin, as the single raster's strip kernel gives them to its
+// CTAs, so every cell is computed by the same code, hence to the same bits, as in a
+// single raster with the same tile height.  The tile code reads the step's scalars and
+// reports copy errors through a control block in shared memory; tensor maps per scenario
+// live in global memory.  Each thread fences its stores to the async proxy before the
+// cluster barrier that ends the step, so the next step's tensor loads see them.
+template <int NW, bool EXT>
+__global__ void __launch_bounds__(NW * 32, 16 / NW) ensemble_strip_kernel(EnsScenario *scen, const StripMaps *maps,
+                                                                          const int *order, int n_scen, unsigned *queue)
+{
+    constexpr int NT = NW * 32;
+    cg::cluster_group cluster = cg::this_cluster();
+    const unsigned rank = cluster.block_rank(), csize = cluster.num_blocks();
+    extern __shared__ __align__(128) unsigned char smem_raw[];
+    StripSmem<false> *rings =
+        reinterpret_cast<StripSmem<false> *>(smem_raw + ((128u - (smem_u32(smem_raw) & 127u)) & 127u));
+    __shared__ EnsShared sh;
+    __shared__ DevCtl sctl;                          // step scalars and error word of the tile code
+    __shared__ float s_cls[3][kMaxClasses];          // class tables (unused: per-cell theta)
+    StepArgs &sa = sh.sa;
+    EnsClock &clk = sh.clk;
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    StripSmem<false> &R = rings[warp];
+    const int worker = (int)rank * NW + warp, nworkers = (int)csize * NW;
+    bool ring_used = false;              // this warp's ring barriers hold a previous tile's phases
+    for (;;) {
+        const int si = ens_pop(cluster, rank, sh, order, n_scen, queue);
+        if (si < 0) return;
+        EnsScenario &S = scen[si];
+        if (tid == 0) {
+            sa = S.a;
+            sa.ctl = &sctl;
+            sctl.err = 0;
+            ens_clock_zero(clk);
+        }
+        __syncthreads();
+        const int rows = sa.rows;
+        const int rb0 = (int)(((long long)rows * rank) / csize);
+        const int rb1 = (int)(((long long)rows * (rank + 1)) / csize);
+        ens_start<NT>(cluster, csize, sh, S, rb0, rb1);
+        __syncthreads();
+        const StripMaps &M = maps[si];
+        const int ns = sa.nstrips + (sa.cx_last >= 0 ? 1 : 0);
+        if (lane == 0 && sa.ntiles > 0) {
+            // the scenario's maps, written to global memory by the host, for this warp's
+            // tensor copies
+            for (int p = 0; p < 2; p++) {
+                tensormap_acquire(&M.mhi[p]);
+                tensormap_acquire(&M.v1[p]);
+                tensormap_acquire(&M.v2[p]);
+                tensormap_acquire(&M.mlo[p]);
             }
-            cluster.sync();          // the band is written and the partials are in place
+            tensormap_acquire(&M.z);
+            tensormap_acquire(&M.th);
+        }
+        // ---- time loop
+        while (clk.active) {
             if (tid == 0) {
-                unsigned cm = 0u;
-                double o = 0.0, c = 0.0;
-                for (unsigned q = 0; q < csize; q++) {
-                    const EnsPartial p = *cluster.map_shared_rank(&part[par], q);
-                    cm = max(cm, p.cbits);
-                    o += p.out;
-                    c += p.cl;
-                }
-                clk.rain_in += S.sigma * (double)((long long)rows * cols) * (double)clk.qr;
-                clk.outflow += S.sigma * o;
-                clk.clamped += S.sigma * c;
-                clk.t = clk.t_next;
-                clk.steps += 1;
-                clk.parity ^= 1;
-                if (S.sample_dt > 0.0 && clk.t == (double)(clk.n_samples + 1) * S.sample_dt) {
-                    if (rank == 0 && clk.n_samples < S.max_samples) S.samples[clk.n_samples] = clk.outflow;
-                    clk.n_samples += 1;
-                }
-                clk.cmax = __uint_as_float(cm);
-                if (!(clk.cmax <= FLT_MAX)) clk.err |= kErrNumeric;
-                ens_prepare(S, clk);
+                sctl.parity = clk.parity;
+                sctl.kappa = clk.kappa;
+                sctl.qr = clk.qr;
+                sctl.dtf = clk.dtf;
             }
             __syncthreads();
-        }
-        // ---- final storage and results
-        {
-            const int par = clk.parity;
-            unsigned cb = 0u;
-            double out = 0.0, cl = 0.0, sto = 0.0;
-            for (int i = tid; i < band; i += NT) {
-                const int r = rb0 + i / cols, c = i % cols;
-                const size_t k = (size_t)r * sa.pitch + c;
-                sto += (double)sa.mhi[par][k] + (double)sa.mlo[par][k];
+            unsigned cb = 0u, err = 0u;
+            double out = 0.0, cl = 0.0;
+            for (int u = worker; u < sa.nblocks; u += nworkers) {
+                if (u < sa.ntiles) {
+                    const int strip = u % ns, rblk = u / ns;
+                    const int c0 = strip < sa.nstrips ? sa.cx0 + strip * kSW : sa.cx_last;
+                    const int own_c = strip < sa.nstrips ? c0 : sa.cx0 + sa.nstrips * kSW;
+                    const int r0 = rblk < sa.nrb ? sa.ry0 + rblk * sa.tile_rows : sa.r_last;
+                    const int own_r = rblk < sa.nrb ? r0 : sa.ry0 + sa.nrb * sa.tile_rows;
+                    if ((r0 & 1) == 0) {     // the layout puts every tile on an odd first row
+                        err = kErrTimeout;
+                        break;
+                    }
+                    // the previous tile's ring reads are done before new copies land in it,
+                    // and its barriers (every copy waited for) are reset for the new tile
+                    __syncwarp();
+                    if (ring_used && lane == 0)
+                        for (int k = 0; k < kNC; k++) mbar_inval(&R.bar[k]);
+                    ring_used = true;
+                    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+                    Tile<false, EXT> T(sa, R, s_cls, M, c0, r0, own_c, own_r);
+                    T.run();
+                    if (__any_sync(0xffffffffu, T.timed_out)) {
+                        // a tensor copy did not arrive in time: wait (bounded) for the
+                        // copies still in flight and stop the scenario with an error
+                        if (lane == 0)
+                            for (int k = max(0, T.n_issued - kNC); k < T.n_issued; k++)
+                                mbar_wait_bounded(&R.bar[k % kNC], (unsigned)((k / kNC) & 1));
+                        err = kErrTimeout;
+                        break;
+                    }
+                    cb = max(cb, T.cwb);
+                    out += T.outd.value();
+                    cl += T.clq.value();
+                } else {
+                    FF o, c;
+                    frame_cells<EXT>(sa, (long long)(u - sa.ntiles) * kFrameCells, cb, o, c);
+                    out += o.value();
+                    cl += c.value();
+                }
             }
-            block_reduce<NT>(cb, out, cl, sto);
-            if (tid == 0) part[0] = EnsPartial{0u, 0u, 0.0, 0.0, sto};
-            cluster.sync();
-            if (rank == 0 && tid == 0) {
-                double st = 0.0;
-                for (unsigned q = 0; q < csize; q++) st += cluster.map_shared_rank(&part[0], q)->sto;
-                S.t = clk.t;
-                S.steps = clk.steps;
-                S.rain_in = clk.rain_in;
-                S.outflow = clk.outflow;
-                S.clamped = clk.clamped;
-                S.storage0 = clk.storage0;
-                S.storage = st * S.sigma;
-                S.n_samples = clk.n_samples;
-                S.err = clk.err;
-                S.parity = clk.parity;
-            }
-            cluster.sync();
+            asm volatile("fence.proxy.async.global;" ::: "memory");
+            ens_step_end<NT>(cluster, rank, csize, sh, S, cb, out, cl, err, &sctl.err);
         }
+        ens_finish<NT>(cluster, rank, csize, sh, S, rb0, rb1);
     }
 }
 
 using EnsKernel = void (*)(EnsScenario *, const int *, int, unsigned *);
+using EnsStripKernel = void (*)(EnsScenario *, const StripMaps *, const int *, int, unsigned *);
 
 template <int NT, int K, int MODE>
 EnsKernel ens_kernel_ptr()
@@ -320,6 +495,16 @@ EnsKernel ens_kernel(int nt, int k, int mode)
 {
     return mode >= 2 ? ens_kernel_m<2>(nt, k) : mode == 1 ? ens_kernel_m<1>(nt, k) : ens_kernel_m<0>(nt, k);
 }
+
+// Strip kernel of `threads` threads (128: 4 tile workers, 256: 8) with or without the
+// optional terms; inflow sides are frame cells, whose gather code always has them.
+EnsStripKernel ens_strip_kernel(int threads, int mode)
+{
+    if (mode >= 2) return threads == 128 ? ensemble_strip_kernel<4, true> : ensemble_strip_kernel<8, true>;
+    return threads == 128 ? ensemble_strip_kernel<4, false> : ensemble_strip_kernel<8, false>;
+}
+
+size_t ens_strip_smem(int threads) { return (size_t)(threads / 32) * sizeof(StripSmem<false>) + 128; }
 
 }  // namespace
 }  // namespace asx
@@ -346,6 +531,9 @@ struct asx_ensemble {
     std::vector<char> have_fields;
     std::vector<long long> work_steps;      // step counts of the last complete run
     bool have_steps = false;
+    StripMaps *maps = nullptr;              // per scenario: the strip kernel's tensor maps
+    std::vector<char> maps_ok;              // scenario wide enough for strip tiles
+    int layout_rows = -1;                   // tile height of the strip layout in `dev`
     cudaGraphExec_t graph = nullptr;
     asx_ensemble_tuning graph_tuning{};
     std::string err;
@@ -369,16 +557,33 @@ asx_status efail(asx_ensemble *e, asx_status st, const std::string &m)
 bool tuning_valid(const asx_ensemble_tuning &t)
 {
     const bool c = t.cluster == 1 || t.cluster == 2 || t.cluster == 4 || t.cluster == kEnsMaxCluster;
+    if (t.tile_rows != 0) {
+        const bool h = t.tile_rows == 8 || t.tile_rows == 16 || t.tile_rows == 32;
+        return c && h && (t.threads == 128 || t.threads == 256) && t.cells_per_thread == 1;
+    }
     const bool n = t.threads == 128 || t.threads == 256 || t.threads == 512;
     const bool k = t.cells_per_thread == 1 || t.cells_per_thread == 2 || t.cells_per_thread == 4;
     return c && n && k;
 }
 
+// Kernel of a launch shape and its dynamic shared memory (set as the kernel's limit).
+const void *shape_kernel(const asx_ensemble_tuning &t, int mode, size_t &smem)
+{
+    smem = 0;
+    if (t.tile_rows == 0) return (const void *)ens_kernel(t.threads, t.cells_per_thread, mode);
+    const void *f = (const void *)ens_strip_kernel(t.threads, mode);
+    smem = ens_strip_smem(t.threads);
+    cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    return f;
+}
+
 // Clusters of this shape that fit on the device at once.
 int resident_clusters(const asx_ensemble_tuning &t, int mode)
 {
-    EnsKernel f = ens_kernel(t.threads, t.cells_per_thread, mode);
+    size_t smem = 0;
+    const void *f = shape_kernel(t, mode, smem);
     cudaLaunchConfig_t cfg{};
+    cfg.dynamicSmemBytes = smem;
     cudaLaunchAttribute at[1];
     at[0].id = cudaLaunchAttributeClusterDimension;
     at[0].val.clusterDim.x = t.cluster;
@@ -389,15 +594,43 @@ int resident_clusters(const asx_ensemble_tuning &t, int mode)
     cfg.attrs = at;
     cfg.numAttrs = 1;
     int nc = 0;
-    if (cudaOccupancyMaxActiveClusters(&nc, (const void *)f, &cfg) != cudaSuccess || nc < 1) nc = 1;
+    if (cudaOccupancyMaxActiveClusters(&nc, f, &cfg) != cudaSuccess || nc < 1) nc = 1;
     return nc;
+}
+
+// The scenario table's strip layout (interior tiles and frame) for tile height H, if it
+// holds another (H = 0, the gather kernel, needs none).  Scenarios too narrow for a tile
+// (or without tensor maps) are all frame.
+cudaError_t ensure_layout(asx_ensemble *e, int H)
+{
+    if (H == 0 || e->layout_rows == H) return cudaSuccess;
+    for (int i = 0; i < e->n; i++) {
+        StepArgs &a = e->host[i].a;
+        a.tile_rows = H;
+        step_strip_layout(a);
+        if (!e->maps_ok[i] || a.ntiles == 0) {
+            // no interior: every cell is a frame cell, taken row by row
+            const long long n = (long long)a.rows * a.cols;
+            a.nstrips = a.nrb = a.ntiles = 0;
+            a.cx_last = a.r_last = -1;
+            a.cxe = a.cx0;
+            a.rye = a.ry0;
+            a.frame_n = a.frame_a = n;
+            a.nblocks = (int)((n + kFrameCells - 1) / kFrameCells);
+        }
+    }
+    cudaError_t x = cudaMemcpy(e->dev, e->host.data(), e->n * sizeof(EnsScenario), cudaMemcpyHostToDevice);
+    e->layout_rows = x == cudaSuccess ? H : -1;
+    return x;
 }
 
 cudaError_t launch_ensemble(asx_ensemble *e, const asx_ensemble_tuning &t, cudaStream_t s)
 {
-    EnsKernel f = ens_kernel(t.threads, t.cells_per_thread, e->mode);
+    size_t smem = 0;
+    const void *f = shape_kernel(t, e->mode, smem);
     const int nc = std::min(resident_clusters(t, e->mode), e->n);
     cudaLaunchConfig_t cfg{};
+    cfg.dynamicSmemBytes = smem;
     cudaLaunchAttribute at[1];
     at[0].id = cudaLaunchAttributeClusterDimension;
     at[0].val.clusterDim.x = t.cluster;
@@ -410,7 +643,12 @@ cudaError_t launch_ensemble(asx_ensemble *e, const asx_ensemble_tuning &t, cudaS
     cfg.numAttrs = 1;
     cudaError_t x = cudaMemsetAsync(e->queue, 0, sizeof(unsigned), s);
     if (x != cudaSuccess) return x;
-    return cudaLaunchKernelEx(&cfg, f, e->dev, (const int *)e->order, e->n, e->queue);
+    (void)f;
+    if (t.tile_rows == 0)
+        return cudaLaunchKernelEx(&cfg, ens_kernel(t.threads, t.cells_per_thread, e->mode), e->dev,
+                                  (const int *)e->order, e->n, e->queue);
+    return cudaLaunchKernelEx(&cfg, ens_strip_kernel(t.threads, e->mode), e->dev, (const StripMaps *)e->maps,
+                              (const int *)e->order, e->n, e->queue);
 }
 
 // Restores every scenario's initial state and clock (the state lives in parity 0 and a
@@ -484,6 +722,7 @@ asx_status asx_create_ensemble(int n, const asx_scenario_desc *descs, void *cuda
     if (x == cudaSuccess) x = cudaMalloc(&e->dev, n * sizeof(EnsScenario));
     if (x == cudaSuccess) x = cudaMalloc(&e->order, n * sizeof(int));
     if (x == cudaSuccess) x = cudaMalloc(&e->queue, sizeof(unsigned));
+    if (x == cudaSuccess) x = cudaMalloc(&e->maps, n * sizeof(StripMaps));
     if (x == cudaSuccess) x = cudaMemsetAsync(e->buf, 0, total * sizeof(float), e->stream);
     if (x != cudaSuccess) {
         asx_destroy_ensemble(e);
@@ -520,6 +759,9 @@ asx_status asx_create_ensemble(int n, const asx_scenario_desc *descs, void *cuda
         for (int k = 0; k < 3; k++) {
             a.cpe[k][0] = (float)(-0.5 * d.edge_m * d.g * n1[k]);
             a.cpe[k][1] = (float)(-0.5 * d.edge_m * d.g * n2[k]);
+            // the strip tiles' form: momentum sums in units of l/8
+            a.cpm[k][0] = (float)(-4.0 * d.g * n1[k]);
+            a.cpm[k][1] = (float)(-4.0 * d.g * n2[k]);
         }
         for (int s = 0; s < 4; s++) {
             a.bc[s] = d.bc[s];
@@ -549,6 +791,26 @@ asx_status asx_create_ensemble(int n, const asx_scenario_desc *descs, void *cuda
         soff += (size_t)std::max(d.max_samples, 1);
         h.max_steps = d.max_steps > 0 ? d.max_steps : (1LL << 62);
         ord[i] = i;
+    }
+    // tensor maps of the strip kernel, for the scenarios wide enough for a tile and its
+    // halo columns (the others are all frame)
+    std::vector<StripMaps> hmaps(n);
+    e->maps_ok.assign(n, 0);
+    for (int i = 0; i < n; i++) {
+        const StepArgs &a = e->host[i].a;
+        std::memset(&hmaps[i], 0, sizeof(StripMaps));
+        if (a.cols >= kStripW + 16 && a.rows >= 4) {
+            if (!make_strip_maps(hmaps[i], a, a.rows, a.cols, a.pitch)) {
+                asx_destroy_ensemble(e);
+                return ASX_ECUDA;
+            }
+            e->maps_ok[i] = 1;
+        }
+    }
+    x = cudaMemcpyAsync(e->maps, hmaps.data(), n * sizeof(StripMaps), cudaMemcpyHostToDevice, e->stream);
+    if (x != cudaSuccess) {
+        asx_destroy_ensemble(e);
+        return ASX_ECUDA;
     }
     // longest first: cells x expected steps ~ cells x t_end / cell size
     std::sort(ord.begin(), ord.end(), [&](int p, int q) {
@@ -580,6 +842,7 @@ asx_status asx_destroy_ensemble(asx_ensemble *e)
     cudaFree(e->dev);
     cudaFree(e->order);
     cudaFree(e->queue);
+    cudaFree(e->maps);
     delete e;
     return ASX_OK;
 }
@@ -651,6 +914,8 @@ asx_status asx_ensemble_run(asx_ensemble *e, const asx_ensemble_tuning *tuning)
     if (!tuning_valid(t)) return efail(e, ASX_EINVAL, "tuning out of range");
     ENS_CUDA(e, cudaSetDevice(e->device));
     ENS_CUDA(e, reset_state(e, e->stream));
+    ENS_CUDA(e, cudaStreamSynchronize(e->stream));
+    ENS_CUDA(e, ensure_layout(e, t.tile_rows));
     // one persistent launch, captured once per tuning in a CUDA graph and replayed
     if (!e->graph || std::memcmp(&e->graph_tuning, &t, sizeof(t)) != 0) {
         if (e->graph) {
@@ -680,7 +945,7 @@ asx_status asx_ensemble_run(asx_ensemble *e, const asx_ensemble_tuning *tuning)
     // read back the results
     std::vector<EnsScenario> res(e->n);
     ENS_CUDA(e, cudaMemcpy(res.data(), e->dev, e->n * sizeof(EnsScenario), cudaMemcpyDeviceToHost));
-    bool bad = false;
+    bool bad = false, timed_out = false;
     for (int i = 0; i < e->n; i++) {
         EnsScenario &h = e->host[i];
         h.t = res[i].t;
@@ -693,8 +958,10 @@ asx_status asx_ensemble_run(asx_ensemble *e, const asx_ensemble_tuning *tuning)
         h.n_samples = res[i].n_samples;
         h.err = res[i].err;
         h.parity = res[i].parity;
-        if (h.err) bad = true;
+        if (h.err & kErrTimeout) timed_out = true;
+        else if (h.err) bad = true;
     }
+    if (timed_out) return efail(e, ASX_ETIMEOUT, "a tensor copy of the strip kernel did not arrive in time");
     if (bad) return efail(e, ASX_ENUMERIC, "a scenario's state became non-finite");
     // A run that took every scenario to its end time gives the real work of each (cells x
     // steps; the step sequence does not depend on the launch shape).  Later runs take the
@@ -747,20 +1014,31 @@ asx_status asx_ensemble_autotune(asx_ensemble *e, int max_steps, asx_ensemble_tu
     ENS_CUDA(e, cudaEventCreate(&b));
     float best_ms = std::numeric_limits<float>::infinity();
     asx_ensemble_tuning best = e->tuning;
-    const int cl[4] = {1, 2, 4, 8}, nt[3] = {128, 256, 512}, kk[3] = {1, 2, 4};
+    // the gather kernel's 36 shapes, then the strip kernel's 24 (cluster x tile workers
+    // per CTA x tile height)
+    std::vector<asx_ensemble_tuning> shapes;
+    for (int c : {1, 2, 4, 8}) {
+        for (int t : {128, 256, 512})
+            for (int k : {1, 2, 4}) shapes.push_back(asx_ensemble_tuning{c, t, k, 0});
+        for (int t : {128, 256})
+            for (int h : {8, 16, 32}) shapes.push_back(asx_ensemble_tuning{c, t, 1, h});
+    }
     asx_status st = ASX_OK;
     // one untimed launch first (first-launch costs), then the faster of two timings per
     // shape: a single short timing is noisy enough to rank shapes wrongly
     {
         cudaError_t x = reset_state(e, e->stream);
+        if (x == cudaSuccess) x = ensure_layout(e, e->tuning.tile_rows);
         if (x == cudaSuccess) x = launch_ensemble(e, e->tuning, e->stream);
         if (x == cudaSuccess) x = cudaStreamSynchronize(e->stream);
         if (x != cudaSuccess) st = efail(e, ASX_ECUDA, std::string("autotune: ") + cudaGetErrorString(x));
     }
-    for (int ci = 0; ci < 4 && st == ASX_OK; ci++)
-        for (int ti = 0; ti < 3 && st == ASX_OK; ti++)
-            for (int ki = 0; ki < 3 && st == ASX_OK; ki++) {
-                const asx_ensemble_tuning t{cl[ci], nt[ti], kk[ki]};
+    for (size_t si = 0; si < shapes.size() && st == ASX_OK; si++) {
+                const asx_ensemble_tuning t = shapes[si];
+                if (ensure_layout(e, t.tile_rows) != cudaSuccess) {
+                    st = efail(e, ASX_ECUDA, "autotune: layout upload");
+                    break;
+                }
                 float shape_ms = std::numeric_limits<float>::infinity();
                 for (int rep = 0; rep < 2 && st == ASX_OK; rep++) {
                     float ms = 0.0f;

@@ -15,6 +15,71 @@
 
 using namespace asx;
 
+namespace asx {
+
+namespace {
+
+typedef CUresult (*EncodeTiledFn)(CUtensorMap *, CUtensorMapDataType, cuuint32_t, void *,
+                                  const cuuint64_t *, const cuuint64_t *, const cuuint32_t *,
+                                  const cuuint32_t *, CUtensorMapInterleave, CUtensorMapSwizzle,
+                                  CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+
+EncodeTiledFn encode_fn()
+{
+    static EncodeTiledFn fn = nullptr;
+    if (!fn) {
+        void *p = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) ==
+                cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            fn = reinterpret_cast<EncodeTiledFn>(p);
+    }
+    return fn;
+}
+
+bool make_map(CUtensorMap *m, void *base, bool u8, int rows, int cols, int pitch, int box_x, int box_y)
+{
+    EncodeTiledFn enc = encode_fn();
+    if (!enc) return false;
+    const size_t es = u8 ? 1 : 4;
+    cuuint64_t dims[2] = {(cuuint64_t)cols, (cuuint64_t)rows};
+    cuuint64_t strides[1] = {(cuuint64_t)pitch * es};
+    cuuint32_t box[2] = {(cuuint32_t)box_x, (cuuint32_t)box_y};
+    cuuint32_t estr[2] = {1, 1};
+    return enc(m, u8 ? CU_TENSOR_MAP_DATA_TYPE_UINT8 : CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2, base, dims,
+               strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
+               CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+}
+
+}  // namespace
+
+// 2-D tensor map over a pitched rows x cols plane; out-of-range elements read as zero.
+bool make_tensor_map_2d(CUtensorMap *m, void *base, bool u8, int rows, int cols, int pitch, int box_x, int box_y)
+{
+    return make_map(m, base, u8, rows, cols, pitch, box_x, box_y);
+}
+
+bool make_strip_maps(StripMaps &m, const StepArgs &a, int rows, int cols, int pitch)
+{
+    bool ok = true;
+    const int bf = kStripW + 8;
+    for (int p = 0; p < 2; p++) {
+        ok = ok && make_map(&m.mhi[p], a.mhi[p], false, rows, cols, pitch, bf, kStripChunkRows);
+        ok = ok && make_map(&m.v1[p], a.v1[p], false, rows, cols, pitch, bf, kStripChunkRows);
+        ok = ok && make_map(&m.v2[p], a.v2[p], false, rows, cols, pitch, bf, kStripChunkRows);
+        ok = ok && make_map(&m.mlo[p], a.mlo[p], false, rows, cols, pitch, kStripW, kStripChunkRows);
+    }
+    ok = ok && make_map(&m.z, (void *)a.z, false, rows, cols, pitch, bf, kStripChunkRows);
+    if (a.cls)
+        ok = ok && make_map(&m.th, (void *)a.cls, true, rows, cols, pitch, kStripW + 16, kStripChunkRows);
+    else
+        ok = ok && make_map(&m.th, (void *)a.theta, false, rows, cols, pitch, bf, kStripChunkRows);
+    return ok;
+}
+
+}  // namespace asx
+
 namespace {
 
 constexpr int kGraphSteps = 32;   // step launches captured in one graph
@@ -38,40 +103,6 @@ int tile_rows_from_env()
     if (t < 2) t = 2;
     if (t > 1024) t = 1024;
     return t;
-}
-
-typedef CUresult (*EncodeTiledFn)(CUtensorMap *, CUtensorMapDataType, cuuint32_t, void *,
-                                  const cuuint64_t *, const cuuint64_t *, const cuuint32_t *,
-                                  const cuuint32_t *, CUtensorMapInterleave, CUtensorMapSwizzle,
-                                  CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
-
-EncodeTiledFn encode_fn()
-{
-    static EncodeTiledFn fn = nullptr;
-    if (!fn) {
-        void *p = nullptr;
-        cudaDriverEntryPointQueryResult q;
-        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) ==
-                cudaSuccess &&
-            q == cudaDriverEntryPointSuccess)
-            fn = reinterpret_cast<EncodeTiledFn>(p);
-    }
-    return fn;
-}
-
-// 2-D tensor map over a pitched rows x cols plane; out-of-range elements read as zero.
-bool make_map(CUtensorMap *m, void *base, bool u8, int rows, int cols, int pitch, int box_x, int box_y)
-{
-    EncodeTiledFn enc = encode_fn();
-    if (!enc) return false;
-    const size_t es = u8 ? 1 : 4;
-    cuuint64_t dims[2] = {(cuuint64_t)cols, (cuuint64_t)rows};
-    cuuint64_t strides[1] = {(cuuint64_t)pitch * es};
-    cuuint32_t box[2] = {(cuuint32_t)box_x, (cuuint32_t)box_y};
-    cuuint32_t estr[2] = {1, 1};
-    return enc(m, u8 ? CU_TENSOR_MAP_DATA_TYPE_UINT8 : CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2, base, dims,
-               strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
-               CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
 }
 
 // Leading part of DevCtl that the host reads after a call (the clock and flags).
@@ -354,19 +385,7 @@ asx_status asx_create_raster(const asx_raster_desc *desc, asx_raster **out)
         b.ctl = r->ctl;
     }
     if (r->variant == kVariantStrip) {
-        bool ok = true;
-        const int bf = kStripW + 8;
-        for (int p = 0; p < 2; p++) {
-            ok = ok && make_map(&r->maps.mhi[p], a.mhi[p], false, r->rows, r->cols, r->pitch, bf, kStripChunkRows);
-            ok = ok && make_map(&r->maps.v1[p], a.v1[p], false, r->rows, r->cols, r->pitch, bf, kStripChunkRows);
-            ok = ok && make_map(&r->maps.v2[p], a.v2[p], false, r->rows, r->cols, r->pitch, bf, kStripChunkRows);
-            ok = ok && make_map(&r->maps.mlo[p], a.mlo[p], false, r->rows, r->cols, r->pitch, kStripW, kStripChunkRows);
-        }
-        ok = ok && make_map(&r->maps.z, (void *)a.z, false, r->rows, r->cols, r->pitch, bf, kStripChunkRows);
-        if (desc->n_classes > 0)
-            ok = ok && make_map(&r->maps.th, (void *)a.cls, true, r->rows, r->cols, r->pitch, kStripW + 16, kStripChunkRows);
-        else
-            ok = ok && make_map(&r->maps.th, (void *)a.theta, false, r->rows, r->cols, r->pitch, bf, kStripChunkRows);
+        const bool ok = make_strip_maps(r->maps, a, r->rows, r->cols, r->pitch);
         if (!ok || step_strip_configure() != cudaSuccess) {
             asx_destroy_raster(r);
             return ASX_ECUDA;

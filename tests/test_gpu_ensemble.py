@@ -78,6 +78,7 @@ def test_ensemble_autotune_and_oracle(asx, orc):
     E = Ensemble(scs)
     t = E.autotune(max_steps=20)
     assert t.cluster in (1, 2, 4, 8) and t.threads in (128, 256, 512) and t.cells_per_thread in (1, 2, 4)
+    assert t.tile_rows in (0, 8, 16, 32)
     E.run()
     for i in (1, 4):
         sc = scs[i]
@@ -110,6 +111,7 @@ def test_ensemble_tuning_after_a_complete_run(asx):
     assert all(c[0] == sc.t_end for (_, c, _), sc in zip(ref, scs))
     t = E.autotune(max_steps=5)
     assert t.cluster in (1, 2, 4, 8) and t.threads in (128, 256, 512) and t.cells_per_thread in (1, 2, 4)
+    assert t.tile_rows in (0, 8, 16, 32)
     E.run((2, 256, 2))
     for i in range(len(scs)):
         st, clk, out = ref[i]
@@ -120,6 +122,104 @@ def test_ensemble_tuning_after_a_complete_run(asx):
     E.run()
     for i in range(len(scs)):
         assert E.clock(i) == ref[i][1]
+    E.close()
+
+
+# sides wide enough for strip tiles (an overlapping last strip at 200, 173 and 300; the
+# narrowest case with tensor maps, 144; rows left to the frame), and one all-frame raster
+STRIP_SIZES = [200, 300, 173, 144, 40, 261]
+
+
+def _strip_scenarios(t_end=60.0, sample_dt=10.0):
+    out = []
+    for i, n in enumerate(STRIP_SIZES):
+        sc = inputs.ensemble_member(20 + i, n_override=n, t_end=t_end)
+        sc.sample_dt = sample_dt
+        out.append(sc)
+    return out
+
+
+@pytest.mark.parametrize("tile_rows", [8, 16, 32])
+def test_strip_ensemble_matches_single_rasters_bitwise(asx, monkeypatch, tile_rows):
+    """The strip ensemble kernel gives every cell the code the single raster's strip kernel
+    gives it in the same layout (the tile code inside, the gather code on the frame): each
+    scenario reaches the state of the same raster run alone with the strip kernel at the
+    same tile height, bit for bit, with the same time steps and hydrograph."""
+    from paper_2406_14933_gb300.ensemble import Ensemble
+    from paper_2406_14933_gb300.raster import Raster
+    monkeypatch.delenv("ASX_STEP_KERNEL", raising=False)
+    monkeypatch.setenv("ASX_TILE_ROWS", str(tile_rows))
+    scs = _strip_scenarios()
+    E = Ensemble(scs)
+    E.run((2, 256, 1, tile_rows))
+    for i, sc in enumerate(scs):
+        R = Raster(sc)
+        t = R.run_until(sc.t_end)
+        te, ke = E.clock(i)
+        assert te == t == sc.t_end
+        assert ke == R.clock()[2]
+        for a, b in zip(E.state(i), R.state()):
+            assert np.array_equal(a, b)
+        le, lr = E.ledger(i), R.ledger()
+        # the boundary sums are added in another order
+        assert le.rain_in == pytest.approx(lr.rain_in, rel=1e-12)
+        assert le.outflow == pytest.approx(lr.outflow, rel=1e-12, abs=1e-12)
+        assert le.storage == pytest.approx(lr.storage, rel=1e-12)
+        assert le.defect_rel <= 1e-10
+        qe, qr = E.hydrograph(i), R.hydrograph()
+        assert len(qe) == len(qr) == 6
+        assert np.allclose(qe, qr, rtol=1e-10, atol=1e-14)
+        R.close()
+    E.close()
+
+
+@pytest.mark.parametrize("tuning", [(1, 128, 1, 16), (4, 128, 1, 16), (8, 256, 1, 16)])
+def test_strip_ensemble_launch_shapes_agree(asx, tuning):
+    """Cluster size and tile workers per CTA change which warp computes a tile, not what:
+    the states are identical for every strip launch shape of one tile height."""
+    from paper_2406_14933_gb300.ensemble import Ensemble
+    scs = _strip_scenarios(t_end=40.0)
+    E = Ensemble(scs)
+    E.run((2, 256, 1, 16))
+    ref = [E.state(i) for i in range(len(scs))]
+    E.run(tuning)
+    for i in range(len(scs)):
+        for a, b in zip(E.state(i), ref[i]):
+            assert np.array_equal(a, b)
+    E.close()
+
+
+def test_strip_ensemble_against_oracle(asx, orc):
+    """Two strip-ensemble scenarios (tiles and frame) against the FP64 oracle on their own
+    time steps, to the stated tolerance, with closed budgets."""
+    from paper_2406_14933_gb300.ensemble import Ensemble
+    scs = _strip_scenarios(t_end=90.0)
+    E = Ensemble(scs)
+    E.run((4, 256, 1, 8))
+    for i in (0, 2):
+        sc = scs[i]
+        p = orc.from_scenario(sc)
+        res = p.run(p.mass(sc.h0), sc.v1_0, sc.v2_0, 0.0, sc.t_end, sample_dt=sc.sample_dt, sample_cap=100)
+        mh, ml, v1, v2 = E.state(i)
+        mg = mh.astype(np.float64) + ml
+        assert _rel_l2(p.depth(mg.ravel()), p.depth(res["m"])) <= 1e-4
+        qo = np.concatenate([res["m"] * res["v1"], res["m"] * res["v2"]])
+        qg = np.concatenate([mg.ravel() * v1.ravel(), mg.ravel() * v2.ravel()])
+        assert _rel_l2(qg, qo) <= 1e-4
+        assert E.ledger(i).defect_rel <= 1e-10
+        qh = np.diff(np.concatenate([[0.0], res["samples"]])) / sc.sample_dt
+        assert _rel_l2(E.hydrograph(i), qh) <= 1e-4
+    E.close()
+
+
+@pytest.mark.parametrize("tuning", [(2, 512, 1, 16), (2, 256, 2, 16), (2, 256, 1, 12), (3, 256, 1, 16)])
+def test_ensemble_rejects_bad_strip_shapes(asx, tuning):
+    from paper_2406_14933_gb300.asx import AsxError, ASX_EINVAL
+    from paper_2406_14933_gb300.ensemble import Ensemble
+    E = Ensemble(_strip_scenarios(t_end=10.0)[:2])
+    with pytest.raises(AsxError) as ei:
+        E.run(tuning)
+    assert ei.value.status == ASX_EINVAL
     E.close()
 
 

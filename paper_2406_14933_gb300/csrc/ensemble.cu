@@ -306,9 +306,10 @@ __device__ __forceinline__ void ens_clock_zero(EnsClock &clk)
 // round; MODE 0: the plain scheme; 1: inflow sides (given mass flux, Dirichlet) compiled
 // in; 2: inflow sides and the optional terms (artificial viscosity, linear resistance, dry
 // threshold) compiled in.
+// (at most 64 registers, so that 1,024 threads, e.g. two CTAs of 512, share an SM)
 template <int NT, int K, int MODE>
-__global__ void __launch_bounds__(NT) ensemble_kernel(EnsScenario *scen, const int *order, int n_scen,
-                                                     unsigned *queue)
+__global__ void __launch_bounds__(NT, 1024 / NT) ensemble_kernel(EnsScenario *scen, const int *order, int n_scen,
+                                                                 unsigned *queue)
 {
     cg::cluster_group cluster = cg::this_cluster();
     const unsigned rank = cluster.block_rank(), csize = cluster.num_blocks();
@@ -378,6 +379,7 @@ __global__ void __launch_bounds__(NW * 32, 16 / NW) ensemble_strip_kernel(EnsSce
         reinterpret_cast<StripSmem<false> *>(smem_raw + ((128u - (smem_u32(smem_raw) & 127u)) & 127u));
     __shared__ EnsShared sh;
     __shared__ DevCtl sctl;                          // step scalars and error word of the tile code
+    __shared__ int s_cur;                            // index of the running scenario
     __shared__ float s_cls[3][kMaxClasses];          // class tables (unused: per-cell theta)
     StepArgs &sa = sh.sa;
     EnsClock &clk = sh.clk;
@@ -386,22 +388,24 @@ __global__ void __launch_bounds__(NW * 32, 16 / NW) ensemble_strip_kernel(EnsSce
     const int worker = (int)rank * NW + warp, nworkers = (int)csize * NW;
     bool ring_used = false;              // this warp's ring barriers hold a previous tile's phases
     for (;;) {
-        const int si = ens_pop(cluster, rank, sh, order, n_scen, queue);
-        if (si < 0) return;
-        EnsScenario &S = scen[si];
-        if (tid == 0) {
-            sa = S.a;
-            sa.ctl = &sctl;
-            sctl.err = 0;
-            ens_clock_zero(clk);
+        {
+            const int si = ens_pop(cluster, rank, sh, order, n_scen, queue);
+            if (si < 0) return;
+            if (tid == 0) {
+                sa = scen[si].a;
+                sa.ctl = &sctl;
+                sctl.err = 0;
+                s_cur = si;
+                ens_clock_zero(clk);
+            }
+            __syncthreads();
+            // the initial scan over this CTA's row band
+            ens_start<NT>(cluster, csize, sh, scen[si], (int)(((long long)sa.rows * rank) / csize),
+                          (int)(((long long)sa.rows * (rank + 1)) / csize));
+            __syncthreads();
         }
-        __syncthreads();
-        const int rows = sa.rows;
-        const int rb0 = (int)(((long long)rows * rank) / csize);
-        const int rb1 = (int)(((long long)rows * (rank + 1)) / csize);
-        ens_start<NT>(cluster, csize, sh, S, rb0, rb1);
-        __syncthreads();
-        const StripMaps &M = maps[si];
+        // the scenario index lives in shared memory, not in registers, through the time loop
+        const StripMaps &M = maps[s_cur];
         const int ns = sa.nstrips + (sa.cx_last >= 0 ? 1 : 0);
         if (lane == 0 && sa.ntiles > 0) {
             // the scenario's maps, written to global memory by the host, for this warp's
@@ -424,8 +428,10 @@ __global__ void __launch_bounds__(NW * 32, 16 / NW) ensemble_strip_kernel(EnsSce
                 sctl.dtf = clk.dtf;
             }
             __syncthreads();
-            unsigned cb = 0u, err = 0u;
-            double out = 0.0, cl = 0.0;
+            // one worker per warp and step, moved from tile to tile; its reductions
+            // collect the frame units' too
+            Tile<false, EXT> T(sa, R, s_cls, M, sa.cx0, sa.ry0, sa.cx0, sa.ry0);
+            unsigned err = 0u;
             for (int u = worker; u < sa.nblocks; u += nworkers) {
                 if (u < sa.ntiles) {
                     const int strip = u % ns, rblk = u / ns;
@@ -444,7 +450,7 @@ __global__ void __launch_bounds__(NW * 32, 16 / NW) ensemble_strip_kernel(EnsSce
                         for (int k = 0; k < kNC; k++) mbar_inval(&R.bar[k]);
                     ring_used = true;
                     asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-                    Tile<false, EXT> T(sa, R, s_cls, M, c0, r0, own_c, own_r);
+                    T.place(c0, r0, own_c, own_r);
                     T.run();
                     if (__any_sync(0xffffffffu, T.timed_out)) {
                         // a tensor copy did not arrive in time: wait (bounded) for the
@@ -455,20 +461,17 @@ __global__ void __launch_bounds__(NW * 32, 16 / NW) ensemble_strip_kernel(EnsSce
                         err = kErrTimeout;
                         break;
                     }
-                    cb = max(cb, T.cwb);
-                    out += T.outd.value();
-                    cl += T.clq.value();
                 } else {
-                    FF o, c;
-                    frame_cells<EXT>(sa, (long long)(u - sa.ntiles) * kFrameCells, cb, o, c);
-                    out += o.value();
-                    cl += c.value();
+                    frame_cells<EXT>(sa, (long long)(u - sa.ntiles) * kFrameCells, T.cwb, T.outd, T.clq);
                 }
             }
+            const unsigned cb = T.cwb;
+            const double out = T.outd.value(), cl = T.clq.value();
             asm volatile("fence.proxy.async.global;" ::: "memory");
-            ens_step_end<NT>(cluster, rank, csize, sh, S, cb, out, cl, err, &sctl.err);
+            ens_step_end<NT>(cluster, rank, csize, sh, scen[s_cur], cb, out, cl, err, &sctl.err);
         }
-        ens_finish<NT>(cluster, rank, csize, sh, S, rb0, rb1);
+        ens_finish<NT>(cluster, rank, csize, sh, scen[s_cur], (int)(((long long)sa.rows * rank) / csize),
+                       (int)(((long long)sa.rows * (rank + 1)) / csize));
     }
 }
 

@@ -512,13 +512,24 @@ struct Tile {
         dtf = ctl->dtf;
         kl2 = kappa * (0.5f * a.l);
         lane = threadIdx.x & 31;
+        Hn = a.tile_rows;
+        nchunks = (Hn + 2 + kRB - 1) / kRB;
+        place(c0_, r0_, own_c, own_r_);
+    }
+
+    // Puts the worker on the tile at (c0_, r0_) owning columns from own_c and rows from
+    // own_r_ on.  A warp that runs several tiles in one step (the strip ensemble kernel)
+    // moves one worker from tile to tile: the step's reductions cwb, outd and clq carry
+    // on, and the ring's barriers must have been reset in between.
+    __device__ __forceinline__ void place(int c0_, int r0_, int own_c, int own_r_)
+    {
         c0 = c0_;
         r0 = r0_;
-        Hn = a.tile_rows;
         jown = 1 + (own_r_ - r0);
         own_l = c0 + 2 * lane >= own_c;
         own_r = c0 + kHalf + 2 * lane >= own_c;
-        nchunks = (Hn + 2 + kRB - 1) / kRB;
+        timed_out = false;
+        n_issued = 0;
     }
 
     __device__ __forceinline__ void issue(int k)

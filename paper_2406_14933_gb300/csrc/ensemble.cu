@@ -146,7 +146,8 @@ __device__ __forceinline__ void block_reduce(unsigned &cb, double &out, double &
 
 // Shared-memory state of a CTA of either ensemble kernel.
 struct EnsShared {
-    StepArgs sa;         // the running scenario's arguments
+    EnsScenario P;       // the running scenario's parameter image (P.a: its step arguments),
+                         // read from here by the step's serial part instead of global memory
     EnsClock clk;        // its clock (every CTA of the cluster computes the same)
     EnsPartial part[2];  // this CTA's step partials, slots alternating by step parity
     int s_idx;           // scenario popped by the cluster's rank 0
@@ -170,11 +171,11 @@ __device__ __forceinline__ int ens_pop(cg::cluster_group &cluster, unsigned rank
 // (c_max and storage of the initial state over this CTA's row band [rb0, rb1)), the
 // cluster-wide reduction and the first time step.
 template <int NT>
-__device__ void ens_start(cg::cluster_group &cluster, unsigned csize, EnsShared &sh, const EnsScenario &S,
-                          int rb0, int rb1)
+__device__ void ens_start(cg::cluster_group &cluster, unsigned csize, EnsShared &sh, int rb0, int rb1)
 {
     const int tid = threadIdx.x;
-    const StepArgs &sa = sh.sa;
+    const EnsScenario &S = sh.P;
+    const StepArgs &sa = sh.P.a;
     EnsClock &clk = sh.clk;
     const int cols = sa.cols, band = (rb1 - rb0) * cols;
     unsigned cb = 0u;
@@ -210,10 +211,11 @@ __device__ void ens_start(cg::cluster_group &cluster, unsigned csize, EnsShared 
 // boundary and clamp sums and the error bits (err; *ctl_err is read after the block
 // barrier), then the clock, ledger, hydrograph sample and next time step.
 template <int NT>
-__device__ void ens_step_end(cg::cluster_group &cluster, unsigned rank, unsigned csize, EnsShared &sh, EnsScenario &S,
-                             unsigned cb, double out, double cl, unsigned err, const int *ctl_err)
+__device__ void ens_step_end(cg::cluster_group &cluster, unsigned rank, unsigned csize, EnsShared &sh, unsigned cb,
+                             double out, double cl, unsigned err, const int *ctl_err)
 {
     const int tid = threadIdx.x;
+    const EnsScenario &S = sh.P;
     EnsClock &clk = sh.clk;
     const int par = clk.parity;
     double sto = 0.0;
@@ -236,7 +238,7 @@ __device__ void ens_step_end(cg::cluster_group &cluster, unsigned rank, unsigned
             o += p.out;
             c += p.cl;
         }
-        const StepArgs &sa = sh.sa;
+        const StepArgs &sa = S.a;
         clk.rain_in += S.sigma * (double)((long long)sa.rows * sa.cols) * (double)clk.qr;
         clk.outflow += S.sigma * o;
         clk.clamped += S.sigma * c;
@@ -261,7 +263,7 @@ __device__ void ens_finish(cg::cluster_group &cluster, unsigned rank, unsigned c
                            int rb0, int rb1)
 {
     const int tid = threadIdx.x;
-    const StepArgs &sa = sh.sa;
+    const StepArgs &sa = sh.P.a;
     const EnsClock &clk = sh.clk;
     const int par = clk.parity, cols = sa.cols, band = (rb1 - rb0) * cols;
     unsigned cb = 0u;
@@ -314,7 +316,7 @@ __global__ void __launch_bounds__(NT, 1024 / NT) ensemble_kernel(EnsScenario *sc
     cg::cluster_group cluster = cg::this_cluster();
     const unsigned rank = cluster.block_rank(), csize = cluster.num_blocks();
     __shared__ EnsShared sh;
-    const StepArgs &sa = sh.sa;
+    const StepArgs &sa = sh.P.a;
     EnsClock &clk = sh.clk;
     const int tid = threadIdx.x;
     for (;;) {
@@ -322,7 +324,7 @@ __global__ void __launch_bounds__(NT, 1024 / NT) ensemble_kernel(EnsScenario *sc
         if (si < 0) return;
         EnsScenario &S = scen[si];
         if (tid == 0) {
-            sh.sa = S.a;
+            sh.P = S;
             ens_clock_zero(clk);
         }
         __syncthreads();
@@ -330,7 +332,7 @@ __global__ void __launch_bounds__(NT, 1024 / NT) ensemble_kernel(EnsScenario *sc
         const int rb0 = (int)(((long long)rows * rank) / csize);
         const int rb1 = (int)(((long long)rows * (rank + 1)) / csize);
         const int band = (rb1 - rb0) * cols;
-        ens_start<NT>(cluster, csize, sh, S, rb0, rb1);
+        ens_start<NT>(cluster, csize, sh, rb0, rb1);
         __syncthreads();
         // ---- time loop
         while (clk.active) {
@@ -352,18 +354,19 @@ __global__ void __launch_bounds__(NT, 1024 / NT) ensemble_kernel(EnsScenario *sc
                         gather_cell<(MODE >= 2), (MODE >= 1)>(sa, sc, rb0 + i / cols, i % cols, cb, outd, clq);
                 }
             }
-            ens_step_end<NT>(cluster, rank, csize, sh, S, cb, outd.value(), clq.value(), 0u, nullptr);
+            ens_step_end<NT>(cluster, rank, csize, sh, cb, outd.value(), clq.value(), 0u, nullptr);
         }
         ens_finish<NT>(cluster, rank, csize, sh, S, rb0, rb1);
     }
 }
 
 // The persistent strip ensemble kernel: NW warps per CTA, each a strip tile worker with
-// its own TMA ring (strip_tile.cuh).  Per step the cluster's NW x csize warps take the
-// scenario's units (tiles of 128 columns x tile_rows rows, then the frame in blocks of
-// kFrameCells cells) round-robin, as the single raster's strip kernel gives them to its
-// CTAs, so every cell is computed by the same code, hence to the same bits, as in a
-// single raster with the same tile height.  The tile code reads the step's scalars and
+// its own TMA ring (strip_tile.cuh).  Per step the scenario's units (tiles of 128 columns
+// x tile_rows rows, then the frame in blocks of kFrameCells cells: the units the single
+// raster's strip kernel gives its CTAs) are dealt to the cluster's CTAs by index modulo the
+// cluster size, and within a CTA each warp takes the next one when it is free; every cell
+// is computed by the same code, hence to the same bits, as in a single raster with the
+// same tile height.  The tile code reads the step's scalars and
 // reports copy errors through a control block in shared memory; tensor maps per scenario
 // live in global memory.  Each thread fences its stores to the async proxy before the
 // cluster barrier that ends the step, so the next step's tensor loads see them.
@@ -381,18 +384,18 @@ __global__ void __launch_bounds__(NW * 32, 16 / NW) ensemble_strip_kernel(EnsSce
     __shared__ DevCtl sctl;                          // step scalars and error word of the tile code
     __shared__ int s_cur;                            // index of the running scenario
     __shared__ float s_cls[3][kMaxClasses];          // class tables (unused: per-cell theta)
-    StepArgs &sa = sh.sa;
+    __shared__ int s_next;                           // next unit of this CTA in the running step
+    StepArgs &sa = sh.P.a;
     EnsClock &clk = sh.clk;
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     StripSmem<false> &R = rings[warp];
-    const int worker = (int)rank * NW + warp, nworkers = (int)csize * NW;
     bool ring_used = false;              // this warp's ring barriers hold a previous tile's phases
     for (;;) {
         {
             const int si = ens_pop(cluster, rank, sh, order, n_scen, queue);
             if (si < 0) return;
             if (tid == 0) {
-                sa = scen[si].a;
+                sh.P = scen[si];
                 sa.ctl = &sctl;
                 sctl.err = 0;
                 s_cur = si;
@@ -400,7 +403,7 @@ __global__ void __launch_bounds__(NW * 32, 16 / NW) ensemble_strip_kernel(EnsSce
             }
             __syncthreads();
             // the initial scan over this CTA's row band
-            ens_start<NT>(cluster, csize, sh, scen[si], (int)(((long long)sa.rows * rank) / csize),
+            ens_start<NT>(cluster, csize, sh, (int)(((long long)sa.rows * rank) / csize),
                           (int)(((long long)sa.rows * (rank + 1)) / csize));
             __syncthreads();
         }
@@ -426,13 +429,21 @@ __global__ void __launch_bounds__(NW * 32, 16 / NW) ensemble_strip_kernel(EnsSce
                 sctl.kappa = clk.kappa;
                 sctl.qr = clk.qr;
                 sctl.dtf = clk.dtf;
+                s_next = 0;
             }
             __syncthreads();
             // one worker per warp and step, moved from tile to tile; its reductions
             // collect the frame units' too
             Tile<false, EXT> T(sa, R, s_cls, M, sa.cx0, sa.ry0, sa.cx0, sa.ry0);
             unsigned err = 0u;
-            for (int u = worker; u < sa.nblocks; u += nworkers) {
+            // this CTA's units are rank, rank + csize, ...: its warps take them in order (the
+            // tiles, then the cheaper frame blocks) as they become free
+            for (;;) {
+                int j = 0;
+                if (lane == 0) j = atomicAdd(&s_next, 1);
+                j = __shfl_sync(0xffffffffu, j, 0);
+                const int u = (int)rank + j * (int)csize;
+                if (u >= sa.nblocks) break;
                 if (u < sa.ntiles) {
                     const int strip = u % ns, rblk = u / ns;
                     const int c0 = strip < sa.nstrips ? sa.cx0 + strip * kSW : sa.cx_last;
@@ -468,7 +479,7 @@ __global__ void __launch_bounds__(NW * 32, 16 / NW) ensemble_strip_kernel(EnsSce
             const unsigned cb = T.cwb;
             const double out = T.outd.value(), cl = T.clq.value();
             asm volatile("fence.proxy.async.global;" ::: "memory");
-            ens_step_end<NT>(cluster, rank, csize, sh, scen[s_cur], cb, out, cl, err, &sctl.err);
+            ens_step_end<NT>(cluster, rank, csize, sh, cb, out, cl, err, &sctl.err);
         }
         ens_finish<NT>(cluster, rank, csize, sh, scen[s_cur], (int)(((long long)sa.rows * rank) / csize),
                        (int)(((long long)sa.rows * (rank + 1)) / csize));

@@ -242,6 +242,7 @@ def run_cuda(args):
 
 
 TRAFFIC_SOURCES = ("paper_2406_14933_gb300/csrc/step_strip.cu",
+                   "paper_2406_14933_gb300/csrc/strip_tile.cuh",
                    "paper_2406_14933_gb300/csrc/device_common.cuh",
                    "paper_2406_14933_gb300/csrc/asx_internal.cuh")
 
@@ -391,13 +392,18 @@ def run_ensemble(args, stream):
     scs = [inputs.ensemble_member(s, t_end=args.ens_t_end) for s in range(n)]
     cells = sum(sc.n for sc in scs)
     E = Ensemble(scs, stream=stream.cuda_stream)
-    E.run()                                   # untimed: each scenario's step count
-    tuning = E.autotune(max_steps=200)        # cut in proportion to those step counts
-    E.run()                                   # warm-up (graph capture of the tuned shape)
+    forced = tuple(int(x) for x in args.ens_tuning.split(",")) if args.ens_tuning else None
+    E.run(forced)                             # untimed: each scenario's step count
+    if forced:
+        from paper_2406_14933_gb300 import asx as A
+        tuning = A.asx_ensemble_tuning(*forced)
+    else:
+        tuning = E.autotune(max_steps=200)    # cut in proportion to those step counts
+    E.run(tuning)                             # warm-up (graph capture of the tuned shape)
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     torch.cuda.synchronize()
     e0.record(stream)
-    E.run()
+    E.run(tuning)
     e1.record(stream)
     torch.cuda.synchronize()
     t_ens = e0.elapsed_time(e1) / 1e3
@@ -494,6 +500,9 @@ def run_calibration(args):
 
 
 MLP_FLOP_PER_QUERY = 2 * (36 * 256 + 256 * 256 + 256 * 256 + 256 * 128)   # algorithmic (unpadded)
+# one training sample: the forward pass, the weight gradients (as many FLOP) and the input
+# gradients of layers 2-4 (layer 1's input needs none)
+MLP_FLOP_PER_TRAIN_SAMPLE = 2 * MLP_FLOP_PER_QUERY + 2 * (256 * 256 + 256 * 256 + 256 * 128)
 
 
 def run_surrogate(args):
@@ -534,6 +543,15 @@ def run_surrogate(args):
     rep["workload"] = (rep["workload"] + (", the surrogate configuration's size" if full else
                        f"; proxy, not the 256x256 / 20,000-run configuration: {args.sur_n}x{args.sur_n} members at "
                        f"l = {args.sur_l:g} m (the same 512 m hillslope), {args.sur_train} training runs"))
+    tr = rep["train"]
+    train_tflops = MLP_FLOP_PER_TRAIN_SAMPLE * tr["batch"] * tr["steps"] / tr["fit_seconds"] / 1e12
+    rep["training"] = {"steps": tr["steps"], "batch": tr["batch"], "seconds": tr["fit_seconds"],
+                       "ms_per_step": tr["fit_seconds"] * 1e3 / max(tr["steps"], 1),
+                       "roofline": {"bound": "tensor", "achieved": train_tflops, "peak": bf16_peak, "unit": "TFLOP/s",
+                                    "frac": train_tflops / bf16_peak, "traffic": None,
+                                    "note": f"{MLP_FLOP_PER_TRAIN_SAMPLE} algorithmic FLOP per sample and step "
+                                            "(forward, weight and input gradients) over the whole fit: host-driven "
+                                            "steps of small batches, every kernel, minibatch gathers and launches"}}
     rep["inference"] = {"queries": int(X.shape[0]), "ms": ms, "queries_per_s": X.shape[0] / (ms / 1e3),
                         "roofline": {"bound": "tensor", "achieved": tflops, "peak": bf16_peak, "unit": "TFLOP/s",
                                      "frac": tflops / bf16_peak, "traffic": None,
@@ -604,6 +622,8 @@ def main():
                     help="scenarios of the ensemble section (0 = skip it)")
     ap.add_argument("--ens-t-end", type=float, default=6400.0,
                     help="simulated time of each ensemble scenario [s] (the workload's 6400 s)")
+    ap.add_argument("--ens-tuning", default="",
+                    help="ensemble launch shape cluster,threads,cells_per_thread,tile_rows (default: autotuned)")
     ap.add_argument("--ens-baseline", type=int, default=8,
                     help="scenarios timed one launch per scenario per step (scaled to all by cell-updates)")
     ap.add_argument("--sur-train", type=int, default=16384,

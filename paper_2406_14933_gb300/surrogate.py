@@ -420,7 +420,8 @@ def pipeline(n: int = 256, l: float = 2.0, n_train: int = 20000, n_held: int = 1
     report = dict(workload=f"hillslope ensemble members {n}x{n}, l={l} m, 6400 s", n=n, l=l,
                   train=dict(runs=n_train, solver_wall_s=st_train.wall, solver_hydrographs_per_s=st_train.hydrographs_per_s,
                              solver_cell_updates_per_s=st_train.cell_updates / st_train.seconds if st_train.seconds else 0.0,
-                             epochs=epochs, batch=batch, fit_seconds=fit["seconds"], epochs_per_s=fit["epochs_per_s"],
+                             epochs=epochs, batch=batch, steps=fit["steps"], fit_seconds=fit["seconds"],
+                             epochs_per_s=fit["epochs_per_s"],
                              final_loss=fit["history"][-1][1] if fit["history"] else None),
                   held_out=held, serve=serve,
                   tuning=dict(cluster=tuning.cluster, threads=tuning.threads, cells_per_thread=tuning.cells_per_thread,

@@ -408,16 +408,20 @@ namespace {
 
 // ----------------------------------------------------------------- the fused forward pass
 //
-// One CTA (four warps) carries a tile of 128 queries through all four layers: the input
-// tile (BF16, K padded to 64) and the activations (128 x 256 BF16) stay in shared memory
-// in the tensor core's core-matrix layout, every product accumulates in one 256-column
-// TMEM accumulator, and each layer's epilogue (bias, ReLU, BF16) writes the next layer's
-// operand straight back to shared memory.  The weights come from a copy kept in exactly
-// the shared-memory image (per layer, K/64 chunks of N x 64 core matrices), so a layer's
-// weights arrive with a few bulk copies (cp.async.bulk) on an mbarrier: W1 into the
-// activation buffer (dead until layer 1's epilogue), W2..W4 into a 128 KB weight buffer,
-// each as soon as the previous layer's MMAs have finished reading it.  CTAs are persistent
-// over the tiles.  Shared memory: 16 KB input + 64 KB activations + 128 KB weights.
+// One CTA (sixteen warps) carries two tiles of 128 queries (a pair) through all four
+// layers.  The input tiles (BF16, K padded to 64) and the activations (128 x 256 BF16 per
+// tile) stay in shared memory in the tensor core's core-matrix layout; each tile's
+// products accumulate in its own 256-column TMEM accumulator (512 columns for the pair),
+// and each layer's epilogue (bias, ReLU, BF16) writes the next layer's operand straight
+// back to shared memory.  The weights stream through a ring of two 32 KB slots, one K = 64
+// chunk of a layer's weight matrix per slot, copied from an image kept in exactly the
+// shared-memory layout (cp.async.bulk on an mbarrier); each chunk feeds both tiles, so a
+// pair reads the 352 KB of weights once (thirteen chunks: W1, W2 x 4, W3 x 4, W4 x 4).
+// One thread issues the copies and the products: chunk g's products are queued before it
+// waits for chunk g-1's to finish and refills that slot with chunk g+1, so a copy runs
+// under the products of the chunk before it; at a layer's end the next layer's first
+// chunks load during the epilogue.  CTAs are persistent over the pairs.  Shared memory:
+// 2 x 16 KB inputs + 2 x 64 KB activations + 64 KB ring.
 
 constexpr int kFusedThreads = 512;     // 16 warps: warp w reads TMEM lanes 32 (w % 4) .. +31
 constexpr int kColGroups = kFusedThreads / 128;   // ... and a quarter of the columns, w / 4
@@ -426,9 +430,33 @@ constexpr unsigned kWtBytesH = (unsigned)kHid * kHid * 2;     // W2, W3: 128 KB 
 constexpr unsigned kWtBytes4 = (unsigned)kOut * kHid * 2;     // W4: 64 KB
 constexpr unsigned kWtOff1 = 0, kWtOff2 = kWtBytes1, kWtOff3 = kWtOff2 + kWtBytesH, kWtOff4 = kWtOff3 + kWtBytesH;
 constexpr unsigned kWtTotal = kWtOff4 + kWtBytes4;
-constexpr int kSmX = kTM * kInPad * 2;                        // 16 KB
-constexpr int kSmAct = kTM * kHid * 2;                        // 64 KB
-constexpr int kFusedSmem = kSmX + kSmAct + (int)kWtBytesH + 128;
+constexpr int kSmX = kTM * kInPad * 2;                        // 16 KB per tile
+constexpr int kSmAct = kTM * kHid * 2;                        // 64 KB per tile
+constexpr unsigned kSlot = (unsigned)kHid * kTK * 2;          // 32 KB: one K = 64 chunk of 256 rows
+constexpr int kChunksPerPair = 13;
+constexpr int kFusedSmem = 2 * kSmX + 2 * kSmAct + 2 * (int)kSlot + 128;
+
+// Chunk jj (0..12) of a pair's weight stream: its layer, the chunk's index in the layer,
+// byte offset in the image (the image is laid out in stream order) and size.
+__device__ __forceinline__ void weight_chunk(int jj, int &layer, int &c, unsigned &off, unsigned &bytes)
+{
+    if (jj == 0) {
+        layer = 0;
+        c = 0;
+        off = kWtOff1;
+        bytes = kWtBytes1;
+    } else if (jj <= 8) {
+        layer = 1 + (jj - 1) / 4;
+        c = (jj - 1) % 4;
+        off = kWtOff2 + (unsigned)(jj - 1) * kSlot;
+        bytes = kSlot;
+    } else {
+        layer = 3;
+        c = jj - 9;
+        off = kWtOff4 + (unsigned)c * (kWtBytes4 / 4);
+        bytes = kWtBytes4 / 4;
+    }
+}
 
 // Byte offset of element (r, k) of an R-row K-major operand stored as K/64 chunks of
 // R x 64 in core-matrix layout (chunk c at c * R * 128 bytes).
@@ -473,38 +501,22 @@ __device__ __forceinline__ void mbar_expect(unsigned long long *bar, unsigned by
     asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(su32(bar)), "r"(bytes) : "memory");
 }
 
-// Global -> shared bulk copy of `bytes` (a multiple of 16, both addresses 16-byte aligned)
-// completing on `bar`, issued in pieces of 32 KB; one thread.
-__device__ __forceinline__ void load_image(unsigned char *dst, const unsigned char *src, unsigned bytes,
+// Global -> shared bulk copy of `bytes` (a multiple of 16, at most 32 KB, both addresses
+// 16-byte aligned) completing on `bar`; one thread.
+__device__ __forceinline__ void load_chunk(unsigned char *dst, const unsigned char *src, unsigned bytes,
                                            unsigned long long *bar)
 {
     mbar_expect(bar, bytes);
-    for (unsigned o = 0; o < bytes; o += 32768u) {
-        const unsigned n = bytes - o < 32768u ? bytes - o : 32768u;
-        asm volatile(
-            "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
-                su32(dst + o)),
-            "l"(src + o), "r"(n), "r"(su32(bar))
-            : "memory");
-    }
-}
-
-// D[128 x N] = A[128 x 16 ns] . B[N x 16 ns]^T, A and B in chunked core-matrix layout.
-__device__ __forceinline__ void layer_mma(unsigned tmem, const unsigned char *a, const unsigned char *b, int N,
-                                          int ns)
-{
-    const unsigned idesc = instr_desc(N);
-    for (int s = 0; s < ns; s++) {
-        const unsigned long long da = smem_desc(su32(a) + (unsigned)((s >> 2) * kTM * 128 + (s & 3) * 256), 128, 1024);
-        const unsigned long long db = smem_desc(su32(b) + (unsigned)((s >> 2) * N * 128 + (s & 3) * 256), 128, 1024);
-        tc_mma(tmem, da, db, idesc, s > 0 ? 1u : 0u);
-    }
+    asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+                     su32(dst)),
+                 "l"(src), "r"(bytes), "r"(su32(bar))
+                 : "memory");
 }
 
 // Hidden-layer epilogue of accumulator row r (this thread's TMEM lane), columns
 // [c0, c1): + bias, ReLU, BF16 (round to nearest even), into the activation image.
-__device__ __forceinline__ void epi_hidden(unsigned trow, const float *bias, unsigned char *act, int r, int c0,
-                                           int c1)
+__device__ __forceinline__ void epi_hidden(unsigned trow, const float *__restrict__ bias, unsigned char *act, int r,
+                                           int c0, int c1)
 {
     for (int nc = c0; nc < c1; nc += 16) {
         float v[16];
@@ -512,8 +524,8 @@ __device__ __forceinline__ void epi_hidden(unsigned trow, const float *bias, uns
         unsigned w[8];
 #pragma unroll
         for (int j = 0; j < 8; j++) {
-            const float a = fmaxf(v[2 * j] + bias[nc + 2 * j], 0.0f);
-            const float b = fmaxf(v[2 * j + 1] + bias[nc + 2 * j + 1], 0.0f);
+            const float a = fmaxf(v[2 * j] + __ldg(bias + nc + 2 * j), 0.0f);
+            const float b = fmaxf(v[2 * j + 1] + __ldg(bias + nc + 2 * j + 1), 0.0f);
             const __nv_bfloat162 h = __floats2bfloat162_rn(a, b);
             w[j] = *reinterpret_cast<const unsigned *>(&h);
         }
@@ -522,32 +534,61 @@ __device__ __forceinline__ void epi_hidden(unsigned trow, const float *bias, uns
     }
 }
 
+// The weight stream of one CTA (issued by one thread): chunk j of the stream is chunk
+// j mod 13 of a pair's sequence, in ring slot j mod 2.
+struct WeightStream {
+    const unsigned char *wt;
+    unsigned char *slot[2];
+    unsigned long long *full, *empty;   // per slot: copy landed / products done with it
+    int total;                          // chunks this CTA consumes
+    int issued = 0, freed = 0;          // chunks copied / known to be free again
+    bool ok = true;
+
+    // Copy every chunk whose slot is free, up to two ahead of the products.
+    __device__ __forceinline__ void refill()
+    {
+        while (issued < total && issued - freed < 2) {
+            int layer, c;
+            unsigned off, bytes;
+            weight_chunk(issued % kChunksPerPair, layer, c, off, bytes);
+            load_chunk(slot[issued & 1], wt + off, bytes, &full[issued & 1]);
+            issued++;
+        }
+    }
+    // Wait until the products of chunks up to j are done with their slots.
+    __device__ __forceinline__ void free_through(int j)
+    {
+        while (ok && freed <= j) {
+            ok = mbar_wait_bounded1(&empty[freed & 1], (unsigned)((freed >> 1) & 1));
+            if (ok) freed++;
+        }
+    }
+};
+
 __global__ void __launch_bounds__(kFusedThreads, 1) mlp_fused_fwd_kernel(const FusedArgs f)
 {
     extern __shared__ __align__(128) unsigned char fsm[];
     unsigned char *base = fsm + ((128u - (su32(fsm) & 127u)) & 127u);
-    unsigned char *sX = base, *sAct = base + kSmX, *sW = base + kSmX + kSmAct;
-    __shared__ __align__(8) unsigned long long bar_a, bar_w, bar_m;   // W1 image, weight buffer, MMAs
+    unsigned char *sX[2] = {base, base + kSmX};
+    unsigned char *sAct[2] = {base + 2 * kSmX, base + 2 * kSmX + kSmAct};
+    unsigned char *sW = base + 2 * kSmX + 2 * kSmAct;
+    __shared__ __align__(8) unsigned long long bar_full[2], bar_empty[2], bar_acc;
     __shared__ unsigned tmem_base;
-    __shared__ float s_bias[3 * kHid + kOut];                          // b1 | b2 | b3 | b4
     const int tid = threadIdx.x, warp = tid >> 5;
-    for (int i = tid; i < kHid; i += kFusedThreads) {
-        s_bias[i] = f.b1[i];
-        s_bias[kHid + i] = f.b2[i];
-        s_bias[2 * kHid + i] = f.b3[i];
-        if (i < kOut) s_bias[3 * kHid + i] = f.b4[i];
-    }
-    const int ntiles = (f.batch + kTM - 1) / kTM;
+    const int ntiles = (f.batch + kTM - 1) / kTM, npairs = (ntiles + 1) / 2;
+    const int my_pairs = (int)blockIdx.x < npairs ? (npairs - 1 - (int)blockIdx.x) / (int)gridDim.x + 1 : 0;
     if (warp == 0) {
         asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(su32(&tmem_base)),
-                     "r"(kHid)
+                     "r"(2 * kHid)
                      : "memory");
         asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
     }
     if (tid == 0) {
-        mbar_init1(&bar_a);
-        mbar_init1(&bar_w);
-        mbar_init1(&bar_m);
+        mbar_init1(&bar_full[0]);
+        mbar_init1(&bar_full[1]);
+        mbar_init1(&bar_empty[0]);
+        mbar_init1(&bar_empty[1]);
+        mbar_init1(&bar_acc);
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     }
     asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
@@ -557,23 +598,26 @@ __global__ void __launch_bounds__(kFusedThreads, 1) mlp_fused_fwd_kernel(const F
     const int quarter = warp & 3, cgroup = warp >> 2;
     const int row = quarter * 32 + (tid & 31);              // this thread's accumulator row
     const unsigned trow = tmem + ((unsigned)(quarter * 32) << 16);
-    unsigned pa = 0, pw = 0, pm = 0;          // phases of the three barriers
-    int a_out = 0, w_out = 0, m_out = 0;      // completions issued but not yet waited for
+    WeightStream ws;
+    ws.wt = f.wt;
+    ws.slot[0] = sW;
+    ws.slot[1] = sW + kSlot;
+    ws.full = bar_full;
+    ws.empty = bar_empty;
+    ws.total = my_pairs * kChunksPerPair;
+    if (tid == 0) ws.refill();
+    const float *bias[3] = {f.b1, f.b2, f.b3};
+    unsigned pacc = 0;                 // phase of bar_acc
+    int g = 0;                         // next chunk of the stream to consume (thread 0)
+    int acc_out = 0;                   // an accumulator commit issued but not waited for
     bool ok = true;
-    if (tid == 0 && (int)blockIdx.x < ntiles) {
-        load_image(sAct, f.wt + kWtOff1, kWtBytes1, &bar_a);
-        load_image(sW, f.wt + kWtOff2, kWtBytesH, &bar_w);
-    }
-    if ((int)blockIdx.x < ntiles) a_out = w_out = 1;
-    const unsigned char *wnext[3] = {f.wt + kWtOff3, f.wt + kWtOff4, nullptr};
-    const unsigned wbytes[3] = {kWtBytesH, kWtBytes4, 0};
-    const float *bias[3] = {s_bias, s_bias + kHid, s_bias + 2 * kHid};
-    const float *b4 = s_bias + 3 * kHid;
-    for (int t = blockIdx.x; t < ntiles && ok; t += gridDim.x) {
-        const int m0 = t * kTM;
-        // ---- input tile to BF16, K padded to 64: one (row, 8-column group) per thread and pass
-        for (int u = tid; u < kTM * (kInPad / 8); u += kFusedThreads) {
-            const int r = u % kTM, kg = u / kTM, m = m0 + r;
+    for (int pi = 0; pi < my_pairs && ok; pi++) {
+        const int pair = (int)blockIdx.x + pi * (int)gridDim.x;
+        const int m0 = pair * 2 * kTM;
+        const int nt = min(2, ntiles - 2 * pair);           // tiles in this pair (1 or 2)
+        // ---- input tiles to BF16, K padded to 64: one (row, 8-column group) per thread and pass
+        for (int u = tid; u < 2 * kTM * (kInPad / 8); u += kFusedThreads) {
+            const int r = u % (2 * kTM), kg = u / (2 * kTM), m = m0 + r;
             float xv[8] = {0.0f, 0.0f, 0.0f, 0.0f, 0.0f, 0.0f, 0.0f, 0.0f};
             if (m < f.batch && kg * 8 < kIn) {
                 const float4 *xr = reinterpret_cast<const float4 *>(f.x + (size_t)m * kIn + kg * 8);
@@ -596,91 +640,98 @@ __global__ void __launch_bounds__(kFusedThreads, 1) mlp_fused_fwd_kernel(const F
                 const __nv_bfloat162 h = __floats2bfloat162_rn(xv[2 * j], xv[2 * j + 1]);
                 w[j] = *reinterpret_cast<const unsigned *>(&h);
             }
-            *reinterpret_cast<uint4 *>(sX + cm_off(r, kg * 8)) = make_uint4(w[0], w[1], w[2], w[3]);
+            *reinterpret_cast<uint4 *>(sX[r >> 7] + cm_off(r & (kTM - 1), kg * 8)) = make_uint4(w[0], w[1], w[2], w[3]);
         }
         asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
         __syncthreads();
         // ---- layers 1..4
-        for (int l = 0; l < 4; l++) {
+        for (int l = 0; l < 4 && ok; l++) {
+            const int nch = l == 0 ? 1 : 4, N = l == 3 ? kOut : kHid;
             if (tid == 0) {
-                if (l == 0) {
-                    ok = ok && mbar_wait_bounded1(&bar_a, pa);
-                } else {
-                    ok = ok && mbar_wait_bounded1(&bar_w, pw);
-                }
-                if (ok) {
+                asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+                const unsigned idesc = instr_desc(N);
+                for (int c = 0; c < nch && ws.ok; c++, g++) {
+                    if (!mbar_wait_bounded1(&bar_full[g & 1], (unsigned)((g >> 1) & 1))) {
+                        ws.ok = false;
+                        break;
+                    }
                     asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-                    if (l == 0) layer_mma(tmem, sX, sAct, kHid, kInPad / 16);
-                    else layer_mma(tmem, sAct, sW, l == 3 ? kOut : kHid, kHid / 16);
-                    tc_commit(&bar_m);
-                    m_out = 1;
+                    const unsigned bw = su32(ws.slot[g & 1]);
+                    for (int t = 0; t < nt; t++) {
+                        const unsigned ab = l == 0 ? su32(sX[t]) : su32(sAct[t]) + (unsigned)(c * kTM * 128);
+                        for (int s = 0; s < 4; s++) {
+                            const unsigned long long da = smem_desc(ab + (unsigned)(s * 256), 128, 1024);
+                            const unsigned long long db = smem_desc(bw + (unsigned)(s * 256), 128, 1024);
+                            tc_mma(tmem + (unsigned)(t * kHid), da, db, idesc, (c > 0 || s > 0) ? 1u : 0u);
+                        }
+                    }
+                    tc_commit(&bar_empty[g & 1]);
+                    if (g >= 1) ws.free_through(g - 1);
+                    ws.refill();
+                }
+                if (ws.ok) {
+                    tc_commit(&bar_acc);        // arrives when every product issued so far is done
+                    acc_out = 1;
                 }
             }
-            if (l == 0) {
-                pa ^= 1u;
-                a_out = 0;
-            } else {
-                pw ^= 1u;
-                w_out = 0;
-            }
-            ok = !__syncthreads_or(!ok);
+            ok = !__syncthreads_or(tid == 0 && !ws.ok);
             if (!ok) break;
-            ok = mbar_wait_bounded1(&bar_m, pm);
-            pm ^= 1u;
-            m_out = 0;
+            ok = mbar_wait_bounded1(&bar_acc, pacc);
+            pacc ^= 1u;
+            acc_out = 0;
             asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
             if (__syncthreads_or(!ok)) {
                 ok = false;
                 break;
             }
-            // the MMAs are done with their operands: refill the freed buffers
-            if (l >= 1 && l <= 2) {
-                if (tid == 0) load_image(sW, wnext[l - 1], wbytes[l - 1], &bar_w);
-                w_out = 1;
+            // every product of the layer is done: free the last chunk's slot and start the
+            // next layer's copies under the epilogue
+            if (tid == 0) {
+                ws.free_through(g - 1);
+                ws.refill();
             }
-            if (l == 3 && t + (int)gridDim.x < ntiles) {
-                if (tid == 0) {
-                    load_image(sAct, f.wt + kWtOff1, kWtBytes1, &bar_a);
-                    load_image(sW, f.wt + kWtOff2, kWtBytesH, &bar_w);
-                }
-                a_out = w_out = 1;
-            }
-            if (l < 3) {
-                epi_hidden(trow, bias[l], sAct, row, cgroup * (kHid / kColGroups), (cgroup + 1) * (kHid / kColGroups));
-                asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-            } else {
-                const int m = m0 + row;
-                for (int nc = cgroup * (kOut / kColGroups); nc < (cgroup + 1) * (kOut / kColGroups); nc += 16) {
-                    float v[16];
-                    tc_ld16(trow + (unsigned)nc, v);
-                    if (m < f.batch) {
-                        float4 *yr = reinterpret_cast<float4 *>(f.y + (size_t)m * kOut + nc);
+            for (int t = 0; t < nt; t++) {
+                const unsigned tr = trow + (unsigned)(t * kHid);
+                if (l < 3) {
+                    epi_hidden(tr, bias[l], sAct[t], row, cgroup * (kHid / kColGroups),
+                               (cgroup + 1) * (kHid / kColGroups));
+                } else {
+                    const int m = m0 + t * kTM + row;
+                    for (int nc = cgroup * (kOut / kColGroups); nc < (cgroup + 1) * (kOut / kColGroups); nc += 16) {
+                        float v[16];
+                        tc_ld16(tr + (unsigned)nc, v);
+                        if (m < f.batch) {
+                            float4 *yr = reinterpret_cast<float4 *>(f.y + (size_t)m * kOut + nc);
 #pragma unroll
-                        for (int q = 0; q < 4; q++)
-                            yr[q] = make_float4(v[4 * q] + b4[nc + 4 * q], v[4 * q + 1] + b4[nc + 4 * q + 1],
-                                                v[4 * q + 2] + b4[nc + 4 * q + 2], v[4 * q + 3] + b4[nc + 4 * q + 3]);
+                            for (int q = 0; q < 4; q++)
+                                yr[q] = make_float4(v[4 * q] + __ldg(f.b4 + nc + 4 * q),
+                                                    v[4 * q + 1] + __ldg(f.b4 + nc + 4 * q + 1),
+                                                    v[4 * q + 2] + __ldg(f.b4 + nc + 4 * q + 2),
+                                                    v[4 * q + 3] + __ldg(f.b4 + nc + 4 * q + 3));
+                        }
                     }
                 }
             }
+            if (l < 3) asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
             asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
-            __syncthreads();
+            if (__syncthreads_or(tid == 0 && !ws.ok)) ok = false;
         }
     }
-    if (!ok) {
-        // a wait ran out: flag it, and let the copies and MMAs still in flight land
+    if (!ok || !ws.ok) {
+        // a wait ran out: flag it, and let the copies and products still in flight land
         // (bounded) before the tensor memory is released
         if (tid == 0) {
             if (f.err) atomicOr(f.err, 1);
-            if (a_out) mbar_wait_bounded1(&bar_a, pa);
-            if (w_out) mbar_wait_bounded1(&bar_w, pw);
-            if (m_out) mbar_wait_bounded1(&bar_m, pm);
+            for (int j = g; j < ws.issued; j++) mbar_wait_bounded1(&bar_full[j & 1], (unsigned)((j >> 1) & 1));
+            if (acc_out) mbar_wait_bounded1(&bar_acc, pacc);
+            for (int j = ws.freed; j < g; j++) mbar_wait_bounded1(&bar_empty[j & 1], (unsigned)((j >> 1) & 1));
         }
         __syncthreads();
     }
     asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
     __syncthreads();
     if (warp == 0) {
-        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(kHid) : "memory");
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(2 * kHid) : "memory");
     }
 }
 
@@ -862,8 +913,8 @@ cudaError_t fused_forward(asx_mlp *p, int B, const float *x, float *y)
         p->wt_dirty = false;
     }
     FusedArgs f{x, y, p->wt, p->w + oB1, p->w + oB2, p->w + oB3, p->w + oB4, B, p->err};
-    const int ntiles = (B + kTM - 1) / kTM;
-    const int grid = ntiles < p->n_sm ? ntiles : p->n_sm;
+    const int npairs = ((B + kTM - 1) / kTM + 1) / 2;
+    const int grid = npairs < p->n_sm ? npairs : p->n_sm;
     mlp_fused_fwd_kernel<<<grid, kFusedThreads, kFusedSmem, p->stream>>>(f);
     return cudaGetLastError();
 }

@@ -547,7 +547,7 @@ struct asx_ensemble {
     bool have_steps = false;
     StripMaps *maps = nullptr;              // per scenario: the strip kernel's tensor maps
     std::vector<char> maps_ok;              // scenario wide enough for strip tiles
-    int layout_rows = -1;                   // tile height of the strip layout in `dev`
+    long long layout_key = -1;              // strip layout in `dev`: tile height (and shape if per scenario)
     cudaGraphExec_t graph = nullptr;
     asx_ensemble_tuning graph_tuning{};
     std::string err;
@@ -572,7 +572,7 @@ bool tuning_valid(const asx_ensemble_tuning &t)
 {
     const bool c = t.cluster == 1 || t.cluster == 2 || t.cluster == 4 || t.cluster == kEnsMaxCluster;
     if (t.tile_rows != 0) {
-        const bool h = t.tile_rows == 8 || t.tile_rows == 16 || t.tile_rows == 32;
+        const bool h = t.tile_rows == 1 || t.tile_rows == 8 || t.tile_rows == 16 || t.tile_rows == 32;
         return c && h && (t.threads == 128 || t.threads == 256) && t.cells_per_thread == 1;
     }
     const bool n = t.threads == 128 || t.threads == 256 || t.threads == 512;
@@ -612,30 +612,79 @@ int resident_clusters(const asx_ensemble_tuning &t, int mode)
     return nc;
 }
 
-// The scenario table's strip layout (interior tiles and frame) for tile height H, if it
-// holds another (H = 0, the gather kernel, needs none).  Scenarios too narrow for a tile
-// (or without tensor maps) are all frame.
-cudaError_t ensure_layout(asx_ensemble *e, int H)
+// Strip layout of scenario i for tile height H (interior tiles and frame); scenarios too
+// narrow for a tile (or without tensor maps) are all frame, taken row by row.
+void scenario_layout(asx_ensemble *e, int i, int H)
 {
-    if (H == 0 || e->layout_rows == H) return cudaSuccess;
-    for (int i = 0; i < e->n; i++) {
-        StepArgs &a = e->host[i].a;
-        a.tile_rows = H;
-        step_strip_layout(a);
-        if (!e->maps_ok[i] || a.ntiles == 0) {
-            // no interior: every cell is a frame cell, taken row by row
-            const long long n = (long long)a.rows * a.cols;
-            a.nstrips = a.nrb = a.ntiles = 0;
-            a.cx_last = a.r_last = -1;
-            a.cxe = a.cx0;
-            a.rye = a.ry0;
-            a.frame_n = a.frame_a = n;
-            a.nblocks = (int)((n + kFrameCells - 1) / kFrameCells);
+    StepArgs &a = e->host[i].a;
+    a.tile_rows = H;
+    step_strip_layout(a);
+    if (!e->maps_ok[i] || a.ntiles == 0) {
+        const long long n = (long long)a.rows * a.cols;
+        a.nstrips = a.nrb = a.ntiles = 0;
+        a.cx_last = a.r_last = -1;
+        a.cxe = a.cx0;
+        a.rye = a.ry0;
+        a.frame_n = a.frame_a = n;
+        a.nblocks = (int)((n + kFrameCells - 1) / kFrameCells);
+    }
+}
+
+// Modelled duration of one step of scenario i's current layout on clusters of `csize`
+// CTAs of `nw` warps, in cell-updates of tile code: the units are dealt to the CTAs by
+// index modulo the cluster size and, within a CTA, taken in order by the first free warp.
+// A tile costs its rows with the two halo rows plus a ring start-up of ~100 cells; a
+// frame cell ~3 (gather code).
+double modelled_step(const asx_ensemble *e, int i, int csize, int nw)
+{
+    const StepArgs &a = e->host[i].a;
+    const double tile = (double)(a.tile_rows + 2) * kStripW + 100.0, frame = 3.0 * kFrameCells;
+    double worst = 0.0;
+    std::vector<double> load((size_t)nw);
+    for (int r = 0; r < csize; r++) {
+        std::fill(load.begin(), load.end(), 0.0);
+        for (int u = r; u < a.nblocks; u += csize) {
+            auto w = std::min_element(load.begin(), load.end());
+            *w += u < a.ntiles ? tile : frame;
         }
+        worst = std::max(worst, *std::max_element(load.begin(), load.end()));
+    }
+    return worst;
+}
+
+// The scenario table's strip layout for tile height H, if it holds another: H = 8, 16 or
+// 32 for every scenario, H = 1 the height of 8, 16, 32 whose modelled step is shortest on
+// clusters of `csize` CTAs of `nw` warps, per scenario (H = 0, the gather kernel, needs
+// none).
+cudaError_t ensure_layout(asx_ensemble *e, int H, int csize, int nw)
+{
+    const long long key = H == 1 ? 1 + 1000LL * csize + 100000LL * nw : H;
+    if (H == 0 || e->layout_key == key) return cudaSuccess;
+    for (int i = 0; i < e->n; i++) {
+        if (H != 1) {
+            scenario_layout(e, i, H);
+            continue;
+        }
+        int best = 32;
+        double best_t = 0.0;
+        for (int h : {32, 16, 8}) {
+            scenario_layout(e, i, h);
+            const double t = modelled_step(e, i, csize, nw);
+            if (h == 32 || t < best_t) {
+                best = h;
+                best_t = t;
+            }
+        }
+        scenario_layout(e, i, best);
     }
     cudaError_t x = cudaMemcpy(e->dev, e->host.data(), e->n * sizeof(EnsScenario), cudaMemcpyHostToDevice);
-    e->layout_rows = x == cudaSuccess ? H : -1;
+    e->layout_key = x == cudaSuccess ? key : -1;
     return x;
+}
+
+cudaError_t ensure_layout(asx_ensemble *e, const asx_ensemble_tuning &t)
+{
+    return ensure_layout(e, t.tile_rows, t.cluster, t.threads / 32);
 }
 
 cudaError_t launch_ensemble(asx_ensemble *e, const asx_ensemble_tuning &t, cudaStream_t s)
@@ -929,7 +978,7 @@ asx_status asx_ensemble_run(asx_ensemble *e, const asx_ensemble_tuning *tuning)
     ENS_CUDA(e, cudaSetDevice(e->device));
     ENS_CUDA(e, reset_state(e, e->stream));
     ENS_CUDA(e, cudaStreamSynchronize(e->stream));
-    ENS_CUDA(e, ensure_layout(e, t.tile_rows));
+    ENS_CUDA(e, ensure_layout(e, t));
     // one persistent launch, captured once per tuning in a CUDA graph and replayed
     if (!e->graph || std::memcmp(&e->graph_tuning, &t, sizeof(t)) != 0) {
         if (e->graph) {
@@ -1028,28 +1077,28 @@ asx_status asx_ensemble_autotune(asx_ensemble *e, int max_steps, asx_ensemble_tu
     ENS_CUDA(e, cudaEventCreate(&b));
     float best_ms = std::numeric_limits<float>::infinity();
     asx_ensemble_tuning best = e->tuning;
-    // the gather kernel's 36 shapes, then the strip kernel's 24 (cluster x tile workers
-    // per CTA x tile height)
+    // the gather kernel's 36 shapes, then the strip kernel's 32 (cluster x tile workers
+    // per CTA x tile height, or the height chosen per scenario)
     std::vector<asx_ensemble_tuning> shapes;
     for (int c : {1, 2, 4, 8}) {
         for (int t : {128, 256, 512})
             for (int k : {1, 2, 4}) shapes.push_back(asx_ensemble_tuning{c, t, k, 0});
         for (int t : {128, 256})
-            for (int h : {8, 16, 32}) shapes.push_back(asx_ensemble_tuning{c, t, 1, h});
+            for (int h : {1, 8, 16, 32}) shapes.push_back(asx_ensemble_tuning{c, t, 1, h});
     }
     asx_status st = ASX_OK;
     // one untimed launch first (first-launch costs), then the faster of two timings per
     // shape: a single short timing is noisy enough to rank shapes wrongly
     {
         cudaError_t x = reset_state(e, e->stream);
-        if (x == cudaSuccess) x = ensure_layout(e, e->tuning.tile_rows);
+        if (x == cudaSuccess) x = ensure_layout(e, e->tuning);
         if (x == cudaSuccess) x = launch_ensemble(e, e->tuning, e->stream);
         if (x == cudaSuccess) x = cudaStreamSynchronize(e->stream);
         if (x != cudaSuccess) st = efail(e, ASX_ECUDA, std::string("autotune: ") + cudaGetErrorString(x));
     }
     for (size_t si = 0; si < shapes.size() && st == ASX_OK; si++) {
                 const asx_ensemble_tuning t = shapes[si];
-                if (ensure_layout(e, t.tile_rows) != cudaSuccess) {
+                if (ensure_layout(e, t) != cudaSuccess) {
                     st = efail(e, ASX_ECUDA, "autotune: layout upload");
                     break;
                 }

@@ -432,29 +432,40 @@ constexpr unsigned kWtOff1 = 0, kWtOff2 = kWtBytes1, kWtOff3 = kWtOff2 + kWtByte
 constexpr unsigned kWtTotal = kWtOff4 + kWtBytes4;
 constexpr int kSmX = kTM * kInPad * 2;                        // 16 KB per tile
 constexpr int kSmAct = kTM * kHid * 2;                        // 64 KB per tile
-constexpr unsigned kSlot = (unsigned)kHid * kTK * 2;          // 32 KB: one K = 64 chunk of 256 rows
-constexpr int kChunksPerPair = 13;
-constexpr int kFusedSmem = 2 * kSmX + 2 * kSmAct + 2 * (int)kSlot + 128;
+#ifndef ASX_MLP_CK
+#define ASX_MLP_CK 64
+#endif
+#ifndef ASX_MLP_NSLOT
+#define ASX_MLP_NSLOT 2
+#endif
+constexpr int kCK = ASX_MLP_CK;                               // K columns of a weight chunk
+constexpr int kNSlot = ASX_MLP_NSLOT;                         // ring slots
+constexpr unsigned kSlot = (unsigned)kHid * kCK * 2;          // one chunk of 256 rows
+constexpr int kChunksPerPair = (kInPad + 3 * kHid) / kCK;     // W1, then W2, W3, W4 by K chunks
+constexpr int kFusedSmem = 2 * kSmX + 2 * kSmAct + kNSlot * (int)kSlot + 128;
+static_assert(kCK == 32 || kCK == 64, "chunk width");
+static_assert(kFusedSmem <= 232448, "shared memory per CTA");
 
-// Chunk jj (0..12) of a pair's weight stream: its layer, the chunk's index in the layer,
-// byte offset in the image (the image is laid out in stream order) and size.
+// Chunk jj of a pair's weight stream: its layer, the chunk's index in the layer, byte
+// offset in the image (the image is laid out in stream order) and size.
 __device__ __forceinline__ void weight_chunk(int jj, int &layer, int &c, unsigned &off, unsigned &bytes)
 {
-    if (jj == 0) {
+    constexpr int n1 = kInPad / kCK, nh = kHid / kCK;
+    if (jj < n1) {
         layer = 0;
-        c = 0;
-        off = kWtOff1;
-        bytes = kWtBytes1;
-    } else if (jj <= 8) {
-        layer = 1 + (jj - 1) / 4;
-        c = (jj - 1) % 4;
-        off = kWtOff2 + (unsigned)(jj - 1) * kSlot;
+        c = jj;
+        off = kWtOff1 + (unsigned)c * kSlot;
+        bytes = kSlot;
+    } else if (jj < n1 + 2 * nh) {
+        layer = 1 + (jj - n1) / nh;
+        c = (jj - n1) % nh;
+        off = kWtOff2 + (unsigned)(jj - n1) * kSlot;
         bytes = kSlot;
     } else {
         layer = 3;
-        c = jj - 9;
-        off = kWtOff4 + (unsigned)c * (kWtBytes4 / 4);
-        bytes = kWtBytes4 / 4;
+        c = jj - n1 - 2 * nh;
+        off = kWtOff4 + (unsigned)c * (unsigned)(kOut * kCK * 2);
+        bytes = (unsigned)(kOut * kCK * 2);
     }
 }
 
@@ -463,6 +474,14 @@ __device__ __forceinline__ void weight_chunk(int jj, int &layer, int &c, unsigne
 __device__ __forceinline__ unsigned cm_off_k(int R, int r, int k)
 {
     return (unsigned)((k >> 6) * R * 128) + cm_off(r, k & 63);
+}
+
+// The same for the weight image's chunks of kCK columns: chunk c at c * R * kCK * 2 bytes,
+// core matrices of 8 rows x 16 bytes, kCK / 8 of them along K per 8-row group.
+__device__ __forceinline__ unsigned cm_off_w(int R, int r, int k)
+{
+    const int c = k / kCK, kk = k % kCK;
+    return (unsigned)(c * R * kCK * 2 + ((r >> 3) * (kCK / 8) + (kk >> 3)) * 128 + (r & 7) * 16 + (kk & 7) * 2);
 }
 
 // The BF16 weights (row-major N x K, W1 | W2 | W3 | W4) into the image the fused kernel
@@ -478,7 +497,7 @@ __global__ void tile_weights_kernel(const __nv_bfloat16 *wb, unsigned char *wt)
         if (u < units) {
             const int r = (int)(u / (K / 8)), k = (int)(u % (K / 8)) * 8;
             const uint4 v = *reinterpret_cast<const uint4 *>(wb + src + (long long)r * K + k);
-            *reinterpret_cast<uint4 *>(wt + dst + cm_off_k(N, r, k)) = v;
+            *reinterpret_cast<uint4 *>(wt + dst + cm_off_w(N, r, k)) = v;
             return;
         }
         u -= units;
@@ -538,20 +557,20 @@ __device__ __forceinline__ void epi_hidden(unsigned trow, const float *__restric
 // j mod 13 of a pair's sequence, in ring slot j mod 2.
 struct WeightStream {
     const unsigned char *wt;
-    unsigned char *slot[2];
+    unsigned char *ring;
     unsigned long long *full, *empty;   // per slot: copy landed / products done with it
     int total;                          // chunks this CTA consumes
     int issued = 0, freed = 0;          // chunks copied / known to be free again
     bool ok = true;
 
-    // Copy every chunk whose slot is free, up to two ahead of the products.
+    // Copy every chunk whose slot is free, up to kNSlot ahead of the products.
     __device__ __forceinline__ void refill()
     {
-        while (issued < total && issued - freed < 2) {
+        while (issued < total && issued - freed < kNSlot) {
             int layer, c;
             unsigned off, bytes;
             weight_chunk(issued % kChunksPerPair, layer, c, off, bytes);
-            load_chunk(slot[issued & 1], wt + off, bytes, &full[issued & 1]);
+            load_chunk(ring + (issued % kNSlot) * kSlot, wt + off, bytes, &full[issued % kNSlot]);
             issued++;
         }
     }
@@ -559,7 +578,7 @@ struct WeightStream {
     __device__ __forceinline__ void free_through(int j)
     {
         while (ok && freed <= j) {
-            ok = mbar_wait_bounded1(&empty[freed & 1], (unsigned)((freed >> 1) & 1));
+            ok = mbar_wait_bounded1(&empty[freed % kNSlot], (unsigned)((freed / kNSlot) & 1));
             if (ok) freed++;
         }
     }
@@ -572,7 +591,7 @@ __global__ void __launch_bounds__(kFusedThreads, 1) mlp_fused_fwd_kernel(const F
     unsigned char *sX[2] = {base, base + kSmX};
     unsigned char *sAct[2] = {base + 2 * kSmX, base + 2 * kSmX + kSmAct};
     unsigned char *sW = base + 2 * kSmX + 2 * kSmAct;
-    __shared__ __align__(8) unsigned long long bar_full[2], bar_empty[2], bar_acc;
+    __shared__ __align__(8) unsigned long long bar_full[kNSlot], bar_empty[kNSlot], bar_acc;
     __shared__ unsigned tmem_base;
     const int tid = threadIdx.x, warp = tid >> 5;
     const int ntiles = (f.batch + kTM - 1) / kTM, npairs = (ntiles + 1) / 2;
@@ -584,10 +603,10 @@ __global__ void __launch_bounds__(kFusedThreads, 1) mlp_fused_fwd_kernel(const F
         asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
     }
     if (tid == 0) {
-        mbar_init1(&bar_full[0]);
-        mbar_init1(&bar_full[1]);
-        mbar_init1(&bar_empty[0]);
-        mbar_init1(&bar_empty[1]);
+        for (int k = 0; k < kNSlot; k++) {
+            mbar_init1(&bar_full[k]);
+            mbar_init1(&bar_empty[k]);
+        }
         mbar_init1(&bar_acc);
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     }
@@ -600,8 +619,7 @@ __global__ void __launch_bounds__(kFusedThreads, 1) mlp_fused_fwd_kernel(const F
     const unsigned trow = tmem + ((unsigned)(quarter * 32) << 16);
     WeightStream ws;
     ws.wt = f.wt;
-    ws.slot[0] = sW;
-    ws.slot[1] = sW + kSlot;
+    ws.ring = sW;
     ws.full = bar_full;
     ws.empty = bar_empty;
     ws.total = my_pairs * kChunksPerPair;
@@ -646,26 +664,29 @@ __global__ void __launch_bounds__(kFusedThreads, 1) mlp_fused_fwd_kernel(const F
         __syncthreads();
         // ---- layers 1..4
         for (int l = 0; l < 4 && ok; l++) {
-            const int nch = l == 0 ? 1 : 4, N = l == 3 ? kOut : kHid;
+            const int nch = (l == 0 ? kInPad : kHid) / kCK, N = l == 3 ? kOut : kHid;
             if (tid == 0) {
                 asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
                 const unsigned idesc = instr_desc(N);
                 for (int c = 0; c < nch && ws.ok; c++, g++) {
-                    if (!mbar_wait_bounded1(&bar_full[g & 1], (unsigned)((g >> 1) & 1))) {
+                    if (!mbar_wait_bounded1(&bar_full[g % kNSlot], (unsigned)((g / kNSlot) & 1))) {
                         ws.ok = false;
                         break;
                     }
                     asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-                    const unsigned bw = su32(ws.slot[g & 1]);
+                    const unsigned bw = su32(sW + (g % kNSlot) * kSlot);
                     for (int t = 0; t < nt; t++) {
-                        const unsigned ab = l == 0 ? su32(sX[t]) : su32(sAct[t]) + (unsigned)(c * kTM * 128);
-                        for (int s = 0; s < 4; s++) {
-                            const unsigned long long da = smem_desc(ab + (unsigned)(s * 256), 128, 1024);
-                            const unsigned long long db = smem_desc(bw + (unsigned)(s * 256), 128, 1024);
+                        const unsigned ab = su32(l == 0 ? sX[t] : sAct[t]);
+                        for (int s = 0; s < kCK / 16; s++) {
+                            // A: K columns c kCK + 16 s .. +15 of the tile's K/64-chunked operand
+                            const int k = c * kCK + 16 * s;
+                            const unsigned long long da =
+                                smem_desc(ab + (unsigned)((k >> 6) * kTM * 128 + ((k & 63) >> 3) * 128), 128, 1024);
+                            const unsigned long long db = smem_desc(bw + (unsigned)(s * 256), 128, kCK / 8 * 128);
                             tc_mma(tmem + (unsigned)(t * kHid), da, db, idesc, (c > 0 || s > 0) ? 1u : 0u);
                         }
                     }
-                    tc_commit(&bar_empty[g & 1]);
+                    tc_commit(&bar_empty[g % kNSlot]);
                     if (g >= 1) ws.free_through(g - 1);
                     ws.refill();
                 }
@@ -722,9 +743,11 @@ __global__ void __launch_bounds__(kFusedThreads, 1) mlp_fused_fwd_kernel(const F
         // (bounded) before the tensor memory is released
         if (tid == 0) {
             if (f.err) atomicOr(f.err, 1);
-            for (int j = g; j < ws.issued; j++) mbar_wait_bounded1(&bar_full[j & 1], (unsigned)((j >> 1) & 1));
+            for (int j = g; j < ws.issued; j++)
+                mbar_wait_bounded1(&bar_full[j % kNSlot], (unsigned)((j / kNSlot) & 1));
             if (acc_out) mbar_wait_bounded1(&bar_acc, pacc);
-            for (int j = ws.freed; j < g; j++) mbar_wait_bounded1(&bar_empty[j & 1], (unsigned)((j >> 1) & 1));
+            for (int j = ws.freed; j < g; j++)
+                mbar_wait_bounded1(&bar_empty[j % kNSlot], (unsigned)((j / kNSlot) & 1));
         }
         __syncthreads();
     }

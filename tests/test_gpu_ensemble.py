@@ -189,6 +189,32 @@ def test_strip_ensemble_launch_shapes_agree(asx, tuning):
     E.close()
 
 
+def test_strip_ensemble_tile_height_per_scenario(asx, monkeypatch):
+    """With the tile height chosen per scenario (tile_rows = 1), each scenario equals, bit
+    for bit and step for step, the single raster run by the strip kernel at one of the
+    heights 8, 16, 32."""
+    from paper_2406_14933_gb300.ensemble import Ensemble
+    from paper_2406_14933_gb300.raster import Raster
+    monkeypatch.delenv("ASX_STEP_KERNEL", raising=False)
+    scs = _strip_scenarios(t_end=30.0)
+    E = Ensemble(scs)
+    E.run((4, 256, 1, 1))
+    got = [(E.state(i), E.clock(i)) for i in range(len(scs))]
+    E.close()
+    for i, sc in enumerate(scs):
+        match = False
+        for h in (8, 16, 32):
+            monkeypatch.setenv("ASX_TILE_ROWS", str(h))
+            R = Raster(sc)
+            R.run_until(sc.t_end)
+            same = R.clock()[2] == got[i][1][1] and all(np.array_equal(a, b) for a, b in zip(R.state(), got[i][0]))
+            R.close()
+            if same:
+                match = True
+                break
+        assert match, f"scenario {i} matches no single-raster tile height"
+
+
 def test_strip_ensemble_against_oracle(asx, orc):
     """Two strip-ensemble scenarios (tiles and frame) against the FP64 oracle on their own
     time steps, to the stated tolerance, with closed budgets."""
@@ -212,7 +238,8 @@ def test_strip_ensemble_against_oracle(asx, orc):
     E.close()
 
 
-@pytest.mark.parametrize("tuning", [(2, 512, 1, 16), (2, 256, 2, 16), (2, 256, 1, 12), (3, 256, 1, 16)])
+@pytest.mark.parametrize("tuning", [(2, 512, 1, 16), (2, 256, 2, 16), (2, 256, 1, 12), (3, 256, 1, 16),
+                                    (2, 512, 1, 1), (2, 256, 1, 2)])
 def test_ensemble_rejects_bad_strip_shapes(asx, tuning):
     from paper_2406_14933_gb300.asx import AsxError, ASX_EINVAL
     from paper_2406_14933_gb300.ensemble import Ensemble

@@ -117,6 +117,23 @@ __device__ __forceinline__ void tc_ld16(unsigned taddr, float *v)
     for (int i = 0; i < 16; i++) v[i] = __uint_as_float(r[i]);
 }
 
+// 32 consecutive accumulator columns of this thread's TMEM lane, one wait.
+__device__ __forceinline__ void tc_ld32(unsigned taddr, float *v)
+{
+    unsigned r[32];
+    asm volatile(
+        "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,"
+        "%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%32];"
+        : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
+          "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15]),
+          "=r"(r[16]), "=r"(r[17]), "=r"(r[18]), "=r"(r[19]), "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]),
+          "=r"(r[24]), "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
+        : "r"(taddr));
+    asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+    for (int i = 0; i < 32; i++) v[i] = __uint_as_float(r[i]);
+}
+
 // ----------------------------------------------------------------- the GEMM
 
 struct GemmArgs {
@@ -533,24 +550,54 @@ __device__ __forceinline__ void load_chunk(unsigned char *dst, const unsigned ch
 }
 
 // Hidden-layer epilogue of accumulator row r (this thread's TMEM lane), columns
-// [c0, c1): + bias, ReLU, BF16 (round to nearest even), into the activation image.
+// [c0, c1) (a multiple of 32): + bias, ReLU, BF16 (round to nearest even), into the
+// activation image.
 __device__ __forceinline__ void epi_hidden(unsigned trow, const float *__restrict__ bias, unsigned char *act, int r,
                                            int c0, int c1)
 {
-    for (int nc = c0; nc < c1; nc += 16) {
-        float v[16];
-        tc_ld16(trow + (unsigned)nc, v);
-        unsigned w[8];
+    for (int nc = c0; nc < c1; nc += 32) {
+        float v[32];
+        tc_ld32(trow + (unsigned)nc, v);
+        unsigned w[16];
 #pragma unroll
-        for (int j = 0; j < 8; j++) {
-            const float a = fmaxf(v[2 * j] + __ldg(bias + nc + 2 * j), 0.0f);
-            const float b = fmaxf(v[2 * j + 1] + __ldg(bias + nc + 2 * j + 1), 0.0f);
-            const __nv_bfloat162 h = __floats2bfloat162_rn(a, b);
-            w[j] = *reinterpret_cast<const unsigned *>(&h);
+        for (int q = 0; q < 8; q++) {
+            const float4 b = __ldg(reinterpret_cast<const float4 *>(bias + nc) + q);
+            const __nv_bfloat162 h0 = __floats2bfloat162_rn(fmaxf(v[4 * q] + b.x, 0.0f), fmaxf(v[4 * q + 1] + b.y, 0.0f));
+            const __nv_bfloat162 h1 =
+                __floats2bfloat162_rn(fmaxf(v[4 * q + 2] + b.z, 0.0f), fmaxf(v[4 * q + 3] + b.w, 0.0f));
+            w[2 * q] = *reinterpret_cast<const unsigned *>(&h0);
+            w[2 * q + 1] = *reinterpret_cast<const unsigned *>(&h1);
         }
-        *reinterpret_cast<uint4 *>(act + cm_off_k(kTM, r, nc)) = make_uint4(w[0], w[1], w[2], w[3]);
-        *reinterpret_cast<uint4 *>(act + cm_off_k(kTM, r, nc + 8)) = make_uint4(w[4], w[5], w[6], w[7]);
+#pragma unroll
+        for (int g8 = 0; g8 < 4; g8++)
+            *reinterpret_cast<uint4 *>(act + cm_off_k(kTM, r, nc + 8 * g8)) =
+                make_uint4(w[4 * g8], w[4 * g8 + 1], w[4 * g8 + 2], w[4 * g8 + 3]);
     }
+}
+
+// Output epilogue of one tile: + bias, FP32, rows m0 .. m0 + 127 of y.  Each warp owns 32
+// rows (its TMEM lanes) x 32 columns: it passes them through a padded 32 x 33 block of
+// shared memory, so that each of its stores writes 32 consecutive floats of one row.
+__device__ __forceinline__ void epi_output(unsigned trow, const float *__restrict__ bias, float *stage, float *y,
+                                           int m0, int batch, int quarter, int cgroup)
+{
+    const int lane = threadIdx.x & 31, c0 = cgroup * 32;
+    float v[32];
+    tc_ld32(trow + (unsigned)c0, v);
+#pragma unroll
+    for (int q = 0; q < 8; q++) {
+        const float4 b = __ldg(reinterpret_cast<const float4 *>(bias + c0) + q);
+        stage[lane * 33 + 4 * q] = v[4 * q] + b.x;
+        stage[lane * 33 + 4 * q + 1] = v[4 * q + 1] + b.y;
+        stage[lane * 33 + 4 * q + 2] = v[4 * q + 2] + b.z;
+        stage[lane * 33 + 4 * q + 3] = v[4 * q + 3] + b.w;
+    }
+    __syncwarp();
+    for (int rr = 0; rr < 32; rr++) {
+        const int m = m0 + quarter * 32 + rr;
+        if (m < batch) y[(size_t)m * kOut + c0 + lane] = stage[rr * 33 + lane];
+    }
+    __syncwarp();
 }
 
 // The weight stream of one CTA (issued by one thread): chunk j of the stream is chunk
@@ -717,20 +764,9 @@ __global__ void __launch_bounds__(kFusedThreads, 1) mlp_fused_fwd_kernel(const F
                     epi_hidden(tr, bias[l], sAct[t], row, cgroup * (kHid / kColGroups),
                                (cgroup + 1) * (kHid / kColGroups));
                 } else {
-                    const int m = m0 + t * kTM + row;
-                    for (int nc = cgroup * (kOut / kColGroups); nc < (cgroup + 1) * (kOut / kColGroups); nc += 16) {
-                        float v[16];
-                        tc_ld16(tr + (unsigned)nc, v);
-                        if (m < f.batch) {
-                            float4 *yr = reinterpret_cast<float4 *>(f.y + (size_t)m * kOut + nc);
-#pragma unroll
-                            for (int q = 0; q < 4; q++)
-                                yr[q] = make_float4(v[4 * q] + __ldg(f.b4 + nc + 4 * q),
-                                                    v[4 * q + 1] + __ldg(f.b4 + nc + 4 * q + 1),
-                                                    v[4 * q + 2] + __ldg(f.b4 + nc + 4 * q + 2),
-                                                    v[4 * q + 3] + __ldg(f.b4 + nc + 4 * q + 3));
-                        }
-                    }
+                    // the activations are spent: their buffers hold each warp's 32 x 33 block
+                    epi_output(tr, f.b4, reinterpret_cast<float *>(sAct[0]) + warp * 32 * 33, f.y, m0 + t * kTM,
+                               f.batch, quarter, cgroup);
                 }
             }
             if (l < 3) asm volatile("fence.proxy.async.shared::cta;" ::: "memory");

@@ -441,6 +441,7 @@ namespace {
 // 2 x 16 KB inputs + 2 x 64 KB activations + 64 KB ring.
 
 constexpr int kFusedThreads = 512;     // 16 warps: warp w reads TMEM lanes 32 (w % 4) .. +31
+constexpr int kProducer = 32;          // the thread that issues the weight copies (warp 1, lane 0)
 constexpr int kColGroups = kFusedThreads / 128;   // ... and a quarter of the columns, w / 4
 constexpr unsigned kWtBytes1 = (unsigned)kHid * kInPad * 2;   // W1: 32 KB
 constexpr unsigned kWtBytesH = (unsigned)kHid * kHid * 2;     // W2, W3: 128 KB each
@@ -670,12 +671,12 @@ __global__ void __launch_bounds__(kFusedThreads, 1) mlp_fused_fwd_kernel(const F
     ws.full = bar_full;
     ws.empty = bar_empty;
     ws.total = my_pairs * kChunksPerPair;
-    if (tid == 0) ws.refill();
+    if (tid == kProducer) ws.refill();
     const float *bias[3] = {f.b1, f.b2, f.b3};
     unsigned pacc = 0;                 // phase of bar_acc
-    int g = 0;                         // next chunk of the stream to consume (thread 0)
+    int g = 0;                         // first chunk of the running layer (every thread)
     int acc_out = 0;                   // an accumulator commit issued but not waited for
-    bool ok = true;
+    bool ok = true, mma_ok = true;     // mma_ok: thread 0's waits for copies
     for (int pi = 0; pi < my_pairs && ok; pi++) {
         const int pair = (int)blockIdx.x + pi * (int)gridDim.x;
         const int m0 = pair * 2 * kTM;
@@ -713,15 +714,17 @@ __global__ void __launch_bounds__(kFusedThreads, 1) mlp_fused_fwd_kernel(const F
         for (int l = 0; l < 4 && ok; l++) {
             const int nch = (l == 0 ? kInPad : kHid) / kCK, N = l == 3 ? kOut : kHid;
             if (tid == 0) {
+                // products: each chunk as soon as its copy has landed
                 asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
                 const unsigned idesc = instr_desc(N);
-                for (int c = 0; c < nch && ws.ok; c++, g++) {
-                    if (!mbar_wait_bounded1(&bar_full[g % kNSlot], (unsigned)((g / kNSlot) & 1))) {
-                        ws.ok = false;
+                for (int c = 0; c < nch; c++) {
+                    const int gg = g + c;
+                    if (!mbar_wait_bounded1(&bar_full[gg % kNSlot], (unsigned)((gg / kNSlot) & 1))) {
+                        mma_ok = false;
                         break;
                     }
                     asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-                    const unsigned bw = su32(sW + (g % kNSlot) * kSlot);
+                    const unsigned bw = su32(sW + (gg % kNSlot) * kSlot);
                     for (int t = 0; t < nt; t++) {
                         const unsigned ab = su32(l == 0 ? sX[t] : sAct[t]);
                         for (int s = 0; s < kCK / 16; s++) {
@@ -733,16 +736,27 @@ __global__ void __launch_bounds__(kFusedThreads, 1) mlp_fused_fwd_kernel(const F
                             tc_mma(tmem + (unsigned)(t * kHid), da, db, idesc, (c > 0 || s > 0) ? 1u : 0u);
                         }
                     }
-                    tc_commit(&bar_empty[g % kNSlot]);
-                    if (g >= 1) ws.free_through(g - 1);
-                    ws.refill();
+                    tc_commit(&bar_empty[gg % kNSlot]);
                 }
-                if (ws.ok) {
+                if (mma_ok) {
                     tc_commit(&bar_acc);        // arrives when every product issued so far is done
                     acc_out = 1;
                 }
+            } else if (tid == kProducer) {
+                // copies: free each of the layer's chunks when its products are done and
+                // refill the ring, which ends with the next layer's first chunks in flight
+                for (int j = g; j < g + nch && ws.ok; j++) {
+                    ws.free_through(j);
+                    ws.refill();
+                }
+            } else if ((tid & 31) == 0 && l < 3) {
+                // the next epilogue's biases into L1 while the products run
+                const float *nb = l < 2 ? bias[l + 1] : f.b4;
+                const int span = l < 2 ? kHid : kOut;            // the bias vector's length
+                asm volatile("prefetch.global.L1 [%0];" ::"l"(nb + ((warp & 7) * 32) % span) : "memory");
             }
-            ok = !__syncthreads_or(tid == 0 && !ws.ok);
+            g += nch;
+            ok = !__syncthreads_or((tid == 0 && !mma_ok) || (tid == kProducer && !ws.ok));
             if (!ok) break;
             ok = mbar_wait_bounded1(&bar_acc, pacc);
             pacc ^= 1u;
@@ -751,12 +765,6 @@ __global__ void __launch_bounds__(kFusedThreads, 1) mlp_fused_fwd_kernel(const F
             if (__syncthreads_or(!ok)) {
                 ok = false;
                 break;
-            }
-            // every product of the layer is done: free the last chunk's slot and start the
-            // next layer's copies under the epilogue
-            if (tid == 0) {
-                ws.free_through(g - 1);
-                ws.refill();
             }
             for (int t = 0; t < nt; t++) {
                 const unsigned tr = trow + (unsigned)(t * kHid);
@@ -771,20 +779,21 @@ __global__ void __launch_bounds__(kFusedThreads, 1) mlp_fused_fwd_kernel(const F
             }
             if (l < 3) asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
             asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
-            if (__syncthreads_or(tid == 0 && !ws.ok)) ok = false;
+            __syncthreads();
         }
     }
-    if (!ok || !ws.ok) {
-        // a wait ran out: flag it, and let the copies and products still in flight land
+    if (!ok) {
+        // a wait ran out: flag it, and let the products and copies still in flight land
         // (bounded) before the tensor memory is released
         if (tid == 0) {
             if (f.err) atomicOr(f.err, 1);
-            for (int j = g; j < ws.issued; j++)
-                mbar_wait_bounded1(&bar_full[j % kNSlot], (unsigned)((j / kNSlot) & 1));
+            tc_commit(&bar_acc);                // arrives when every product issued is done
             if (acc_out) mbar_wait_bounded1(&bar_acc, pacc);
-            for (int j = ws.freed; j < g; j++)
-                mbar_wait_bounded1(&bar_empty[j % kNSlot], (unsigned)((j / kNSlot) & 1));
+            mbar_wait_bounded1(&bar_acc, pacc ^ (acc_out ? 1u : 0u));
         }
+        if (tid == kProducer)
+            for (int j = ws.freed; j < ws.issued; j++)
+                mbar_wait_bounded1(&bar_full[j % kNSlot], (unsigned)((j / kNSlot) & 1));
         __syncthreads();
     }
     asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");

@@ -434,7 +434,8 @@ def run_ensemble(args, stream):
                          "traffic": None, "peak_source": f"{kind} copy bandwidth",
                          "note": "32 B algorithmic per cell-update / ensemble wall time"},
             "tuning": {"cluster": tuning.cluster, "threads": tuning.threads,
-                       "cells_per_thread": tuning.cells_per_thread, "tile_rows": tuning.tile_rows},
+                       "cells_per_thread": tuning.cells_per_thread, "tile_rows": tuning.tile_rows,
+                       "split": tuning.split},
             "one_launch_per_scenario": {"scenarios_per_s": n / t_one, "seconds_estimate": t_one,
                                         "timed_subsample": sub, "subsample_seconds": t_sub,
                                         "scaling": "subsample time x (ensemble cell-updates / subsample cell-updates)"},

@@ -274,10 +274,14 @@ typedef struct {
  * 128 or 256 (4 or 8 tile workers), cells_per_thread 1.  tile_rows = 1: the strip kernel
  * with each scenario's tile height (8, 16 or 32) chosen on the host as the one whose
  * modelled step on this cluster is shortest (few, larger tiles for large rasters; more,
- * smaller ones where large tiles would leave warps idle). */
+ * smaller ones where large tiles would leave warps idle).  split = 0: every scenario runs
+ * on a whole cluster.  split > 0 (strip kernel, cluster >= 2): the `split` scenarios that
+ * come first in the queue (the largest) run on whole clusters, and once they are all
+ * taken each CTA runs the others alone; the results are the same either way. */
 typedef struct {
     int cluster, threads, cells_per_thread;
     int tile_rows;
+    int split;
 } asx_ensemble_tuning;
 
 /* Create an ensemble of n scenarios on `device`, work ordered on cuda_stream.  Allocates

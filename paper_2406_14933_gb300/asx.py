@@ -73,10 +73,11 @@ class asx_scenario_desc(C.Structure):
 
 
 class asx_ensemble_tuning(C.Structure):
-    _fields_ = [("cluster", C.c_int), ("threads", C.c_int), ("cells_per_thread", C.c_int), ("tile_rows", C.c_int)]
+    _fields_ = [("cluster", C.c_int), ("threads", C.c_int), ("cells_per_thread", C.c_int), ("tile_rows", C.c_int),
+                ("split", C.c_int)]
 
     def as_tuple(self):
-        return (self.cluster, self.threads, self.cells_per_thread, self.tile_rows)
+        return (self.cluster, self.threads, self.cells_per_thread, self.tile_rows, self.split)
 
 
 _vp = C.c_void_p

@@ -144,6 +144,24 @@ __device__ __forceinline__ void block_reduce(unsigned &cb, double &out, double &
     }
 }
 
+// The CTAs that run a scenario together: the whole cluster, or (solo) this CTA alone, which
+// then never touches a cluster barrier or another CTA's shared memory.
+struct Group {
+    cg::cluster_group cluster;
+    unsigned rank, size;
+    bool solo;
+    __device__ __forceinline__ void sync()
+    {
+        if (solo) __syncthreads();
+        else cluster.sync();
+    }
+    template <class T>
+    __device__ __forceinline__ T *peer(T *p, unsigned q)
+    {
+        return solo ? p : cluster.map_shared_rank(p, q);
+    }
+};
+
 // Shared-memory state of a CTA of either ensemble kernel.
 struct EnsShared {
     EnsScenario P;       // the running scenario's parameter image (P.a: its step arguments),
@@ -154,16 +172,15 @@ struct EnsShared {
 };
 
 // The cluster's next scenario from the queue (-1 when none is left).
-__device__ __forceinline__ int ens_pop(cg::cluster_group &cluster, unsigned rank, EnsShared &sh, const int *order,
-                                      int n_scen, unsigned *queue)
+__device__ __forceinline__ int ens_pop(Group &grp, EnsShared &sh, const int *order, int n_scen, unsigned *queue)
 {
-    if (rank == 0 && threadIdx.x == 0) {
+    if (grp.rank == 0 && threadIdx.x == 0) {
         const unsigned q = atomicAdd(queue, 1u);
         sh.s_idx = q < (unsigned)n_scen ? order[q] : -1;
     }
-    cluster.sync();
-    const int si = *cluster.map_shared_rank(&sh.s_idx, 0);
-    cluster.sync();              // every rank has read s_idx before rank 0 pops again
+    grp.sync();
+    const int si = *grp.peer(&sh.s_idx, 0);
+    grp.sync();                  // every rank has read s_idx before rank 0 pops again
     return si;
 }
 
@@ -171,8 +188,9 @@ __device__ __forceinline__ int ens_pop(cg::cluster_group &cluster, unsigned rank
 // (c_max and storage of the initial state over this CTA's row band [rb0, rb1)), the
 // cluster-wide reduction and the first time step.
 template <int NT>
-__device__ void ens_start(cg::cluster_group &cluster, unsigned csize, EnsShared &sh, int rb0, int rb1)
+__device__ void ens_start(Group &grp, EnsShared &sh, int rb0, int rb1)
 {
+    const unsigned csize = grp.size;
     const int tid = threadIdx.x;
     const EnsScenario &S = sh.P;
     const StepArgs &sa = sh.P.a;
@@ -190,12 +208,12 @@ __device__ void ens_start(cg::cluster_group &cluster, unsigned csize, EnsShared 
     }
     block_reduce<NT>(cb, out, cl, sto);
     if (tid == 0) sh.part[0] = EnsPartial{cb, 0u, 0.0, 0.0, sto};
-    cluster.sync();
+    grp.sync();
     if (tid == 0) {
         unsigned cm = 0u;
         double st = 0.0;
         for (unsigned q = 0; q < csize; q++) {
-            const EnsPartial p = *cluster.map_shared_rank(&sh.part[0], q);
+            const EnsPartial p = *grp.peer(&sh.part[0], q);
             cm = max(cm, p.cbits);
             st += p.sto;
         }
@@ -204,16 +222,17 @@ __device__ void ens_start(cg::cluster_group &cluster, unsigned csize, EnsShared 
         clk.storage0 = st * S.sigma;
         ens_prepare(S, clk);
     }
-    cluster.sync();              // part[0] is read by every rank before it is reused
+    grp.sync();                  // part[0] is read by every rank before it is reused
 }
 
 // Ends a step: block and cluster reductions of the new wave speed (bits cb), the
 // boundary and clamp sums and the error bits (err; *ctl_err is read after the block
 // barrier), then the clock, ledger, hydrograph sample and next time step.
 template <int NT>
-__device__ void ens_step_end(cg::cluster_group &cluster, unsigned rank, unsigned csize, EnsShared &sh, unsigned cb,
-                             double out, double cl, unsigned err, const int *ctl_err)
+__device__ void ens_step_end(Group &grp, EnsShared &sh, unsigned cb, double out, double cl, unsigned err,
+                             const int *ctl_err)
 {
+    const unsigned rank = grp.rank, csize = grp.size;
     const int tid = threadIdx.x;
     const EnsScenario &S = sh.P;
     EnsClock &clk = sh.clk;
@@ -227,12 +246,12 @@ __device__ void ens_step_end(cg::cluster_group &cluster, unsigned rank, unsigned
         __threadfence();
         sh.part[par] = EnsPartial{cb, eb, out, cl, 0.0};
     }
-    cluster.sync();              // the band is written and the partials are in place
+    grp.sync();                  // the band is written and the partials are in place
     if (tid == 0) {
         unsigned cm = 0u, eb = 0u;
         double o = 0.0, c = 0.0;
         for (unsigned q = 0; q < csize; q++) {
-            const EnsPartial p = *cluster.map_shared_rank(&sh.part[par], q);
+            const EnsPartial p = *grp.peer(&sh.part[par], q);
             cm = max(cm, p.cbits);
             eb |= p.err;
             o += p.out;
@@ -259,9 +278,9 @@ __device__ void ens_step_end(cg::cluster_group &cluster, unsigned rank, unsigned
 
 // Final storage of the scenario over this CTA's row band and the results (rank 0).
 template <int NT>
-__device__ void ens_finish(cg::cluster_group &cluster, unsigned rank, unsigned csize, EnsShared &sh, EnsScenario &S,
-                           int rb0, int rb1)
+__device__ void ens_finish(Group &grp, EnsShared &sh, EnsScenario &S, int rb0, int rb1)
 {
+    const unsigned rank = grp.rank, csize = grp.size;
     const int tid = threadIdx.x;
     const StepArgs &sa = sh.P.a;
     const EnsClock &clk = sh.clk;
@@ -275,10 +294,10 @@ __device__ void ens_finish(cg::cluster_group &cluster, unsigned rank, unsigned c
     }
     block_reduce<NT>(cb, out, cl, sto);
     if (tid == 0) sh.part[0] = EnsPartial{0u, 0u, 0.0, 0.0, sto};
-    cluster.sync();
+    grp.sync();
     if (rank == 0 && tid == 0) {
         double st = 0.0;
-        for (unsigned q = 0; q < csize; q++) st += cluster.map_shared_rank(&sh.part[0], q)->sto;
+        for (unsigned q = 0; q < csize; q++) st += grp.peer(&sh.part[0], q)->sto;
         S.t = clk.t;
         S.steps = clk.steps;
         S.rain_in = clk.rain_in;
@@ -290,7 +309,7 @@ __device__ void ens_finish(cg::cluster_group &cluster, unsigned rank, unsigned c
         S.err = clk.err;
         S.parity = clk.parity;
     }
-    cluster.sync();
+    grp.sync();
 }
 
 // Zero clock of a newly taken scenario (one thread).
@@ -314,13 +333,14 @@ __global__ void __launch_bounds__(NT, 1024 / NT) ensemble_kernel(EnsScenario *sc
                                                                  unsigned *queue)
 {
     cg::cluster_group cluster = cg::this_cluster();
-    const unsigned rank = cluster.block_rank(), csize = cluster.num_blocks();
+    Group grp{cluster, cluster.block_rank(), cluster.num_blocks(), false};
+    const unsigned rank = grp.rank, csize = grp.size;
     __shared__ EnsShared sh;
     const StepArgs &sa = sh.P.a;
     EnsClock &clk = sh.clk;
     const int tid = threadIdx.x;
     for (;;) {
-        const int si = ens_pop(cluster, rank, sh, order, n_scen, queue);
+        const int si = ens_pop(grp, sh, order, n_scen, queue);
         if (si < 0) return;
         EnsScenario &S = scen[si];
         if (tid == 0) {
@@ -332,7 +352,7 @@ __global__ void __launch_bounds__(NT, 1024 / NT) ensemble_kernel(EnsScenario *sc
         const int rb0 = (int)(((long long)rows * rank) / csize);
         const int rb1 = (int)(((long long)rows * (rank + 1)) / csize);
         const int band = (rb1 - rb0) * cols;
-        ens_start<NT>(cluster, csize, sh, rb0, rb1);
+        ens_start<NT>(grp, sh, rb0, rb1);
         __syncthreads();
         // ---- time loop
         while (clk.active) {
@@ -354,29 +374,32 @@ __global__ void __launch_bounds__(NT, 1024 / NT) ensemble_kernel(EnsScenario *sc
                         gather_cell<(MODE >= 2), (MODE >= 1)>(sa, sc, rb0 + i / cols, i % cols, cb, outd, clq);
                 }
             }
-            ens_step_end<NT>(cluster, rank, csize, sh, cb, outd.value(), clq.value(), 0u, nullptr);
+            ens_step_end<NT>(grp, sh, cb, outd.value(), clq.value(), 0u, nullptr);
         }
-        ens_finish<NT>(cluster, rank, csize, sh, S, rb0, rb1);
+        ens_finish<NT>(grp, sh, S, rb0, rb1);
     }
 }
 
 // The persistent strip ensemble kernel: NW warps per CTA, each a strip tile worker with
 // its own TMA ring (strip_tile.cuh).  Per step the scenario's units (tiles of 128 columns
 // x tile_rows rows, then the frame in blocks of kFrameCells cells: the units the single
-// raster's strip kernel gives its CTAs) are dealt to the cluster's CTAs by index modulo the
-// cluster size, and within a CTA each warp takes the next one when it is free; every cell
+// raster's strip kernel gives its CTAs) are dealt to the group's CTAs by index modulo the
+// group size, and within a CTA each warp takes the next one when it is free; every cell
 // is computed by the same code, hence to the same bits, as in a single raster with the
-// same tile height.  The tile code reads the step's scalars and
-// reports copy errors through a control block in shared memory; tensor maps per scenario
-// live in global memory.  Each thread fences its stores to the async proxy before the
-// cluster barrier that ends the step, so the next step's tensor loads see them.
+// same tile height.  The tile code reads the step's scalars and reports copy errors
+// through a control block in shared memory; tensor maps per scenario live in global
+// memory.  Each thread fences its stores to the async proxy before the barrier that ends
+// the step, so the next step's tensor loads see them.
+// Two phases: the first n_big scenarios of `order` run on whole clusters (popped from
+// queue[0]); once they are all taken, every CTA of the cluster runs the remaining
+// scenarios alone (popped from queue[1]), with CTA barriers only.
 template <int NW, bool EXT>
 __global__ void __launch_bounds__(NW * 32, 16 / NW) ensemble_strip_kernel(EnsScenario *scen, const StripMaps *maps,
-                                                                          const int *order, int n_scen, unsigned *queue)
+                                                                          const int *order, int n_scen, int n_big,
+                                                                          unsigned *queue)
 {
     constexpr int NT = NW * 32;
     cg::cluster_group cluster = cg::this_cluster();
-    const unsigned rank = cluster.block_rank(), csize = cluster.num_blocks();
     extern __shared__ __align__(128) unsigned char smem_raw[];
     StripSmem<false> *rings =
         reinterpret_cast<StripSmem<false> *>(smem_raw + ((128u - (smem_u32(smem_raw) & 127u)) & 127u));
@@ -385,109 +408,126 @@ __global__ void __launch_bounds__(NW * 32, 16 / NW) ensemble_strip_kernel(EnsSce
     __shared__ int s_cur;                            // index of the running scenario
     __shared__ float s_cls[3][kMaxClasses];          // class tables (unused: per-cell theta)
     __shared__ int s_next;                           // next unit of this CTA in the running step
+    __shared__ unsigned s_grank, s_gsize;            // this CTA's rank and size of its group
+    __shared__ int s_solo;                           // the group is this CTA alone
+    // the group, rebuilt from shared memory where it is needed (not held in registers
+    // through the tile code)
+    auto group = [&]() { return Group{cluster, s_grank, s_gsize, s_solo != 0}; };
     StepArgs &sa = sh.P.a;
     EnsClock &clk = sh.clk;
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     StripSmem<false> &R = rings[warp];
     bool ring_used = false;              // this warp's ring barriers hold a previous tile's phases
-    for (;;) {
-        {
-            const int si = ens_pop(cluster, rank, sh, order, n_scen, queue);
-            if (si < 0) return;
-            if (tid == 0) {
-                sh.P = scen[si];
-                sa.ctl = &sctl;
-                sctl.err = 0;
-                s_cur = si;
-                ens_clock_zero(clk);
-            }
-            __syncthreads();
-            // the initial scan over this CTA's row band
-            ens_start<NT>(cluster, csize, sh, (int)(((long long)sa.rows * rank) / csize),
-                          (int)(((long long)sa.rows * (rank + 1)) / csize));
-            __syncthreads();
+    for (int phase = 0; phase < 2; phase++) {
+        if (tid == 0) {
+            s_solo = phase;
+            s_grank = phase ? 0u : cluster.block_rank();
+            s_gsize = phase ? 1u : cluster.num_blocks();
         }
-        // the scenario index lives in shared memory, not in registers, through the time loop
-        const StripMaps &M = maps[s_cur];
-        const int ns = sa.nstrips + (sa.cx_last >= 0 ? 1 : 0);
-        if (lane == 0 && sa.ntiles > 0) {
-            // the scenario's maps, written to global memory by the host, for this warp's
-            // tensor copies
-            for (int p = 0; p < 2; p++) {
-                tensormap_acquire(&M.mhi[p]);
-                tensormap_acquire(&M.v1[p]);
-                tensormap_acquire(&M.v2[p]);
-                tensormap_acquire(&M.mlo[p]);
-            }
-            tensormap_acquire(&M.z);
-            tensormap_acquire(&M.th);
-        }
-        // ---- time loop
-        while (clk.active) {
-            if (tid == 0) {
-                sctl.parity = clk.parity;
-                sctl.kappa = clk.kappa;
-                sctl.qr = clk.qr;
-                sctl.dtf = clk.dtf;
-                s_next = 0;
-            }
-            __syncthreads();
-            // one worker per warp and step, moved from tile to tile; its reductions
-            // collect the frame units' too
-            Tile<false, EXT> T(sa, R, s_cls, M, sa.cx0, sa.ry0, sa.cx0, sa.ry0);
-            unsigned err = 0u;
-            // this CTA's units are rank, rank + csize, ...: its warps take them in order (the
-            // tiles, then the cheaper frame blocks) as they become free
-            for (;;) {
-                int j = 0;
-                if (lane == 0) j = atomicAdd(&s_next, 1);
-                j = __shfl_sync(0xffffffffu, j, 0);
-                const int u = (int)rank + j * (int)csize;
-                if (u >= sa.nblocks) break;
-                if (u < sa.ntiles) {
-                    const int strip = u % ns, rblk = u / ns;
-                    const int c0 = strip < sa.nstrips ? sa.cx0 + strip * kSW : sa.cx_last;
-                    const int own_c = strip < sa.nstrips ? c0 : sa.cx0 + sa.nstrips * kSW;
-                    const int r0 = rblk < sa.nrb ? sa.ry0 + rblk * sa.tile_rows : sa.r_last;
-                    const int own_r = rblk < sa.nrb ? r0 : sa.ry0 + sa.nrb * sa.tile_rows;
-                    if ((r0 & 1) == 0) {     // the layout puts every tile on an odd first row
-                        err = kErrTimeout;
-                        break;
-                    }
-                    // the previous tile's ring reads are done before new copies land in it,
-                    // and its barriers (every copy waited for) are reset for the new tile
-                    __syncwarp();
-                    if (ring_used && lane == 0)
-                        for (int k = 0; k < kNC; k++) mbar_inval(&R.bar[k]);
-                    ring_used = true;
-                    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-                    T.place(c0, r0, own_c, own_r);
-                    T.run();
-                    if (__any_sync(0xffffffffu, T.timed_out)) {
-                        // a tensor copy did not arrive in time: wait (bounded) for the
-                        // copies still in flight and stop the scenario with an error
-                        if (lane == 0)
-                            for (int k = max(0, T.n_issued - kNC); k < T.n_issued; k++)
-                                mbar_wait_bounded(&R.bar[k % kNC], (unsigned)((k / kNC) & 1));
-                        err = kErrTimeout;
-                        break;
-                    }
-                } else {
-                    frame_cells<EXT>(sa, (long long)(u - sa.ntiles) * kFrameCells, T.cwb, T.outd, T.clq);
+        __syncthreads();
+        for (;;) {
+            {
+                Group grp = group();
+                const int si = phase == 0 ? ens_pop(grp, sh, order, n_big, queue)
+                                          : ens_pop(grp, sh, order + n_big, n_scen - n_big, queue + 1);
+                if (si < 0) break;
+                if (tid == 0) {
+                    sh.P = scen[si];
+                    sa.ctl = &sctl;
+                    sctl.err = 0;
+                    s_cur = si;
+                    ens_clock_zero(clk);
                 }
+                __syncthreads();
+                // the initial scan over this CTA's row band
+                ens_start<NT>(grp, sh, (int)(((long long)sa.rows * grp.rank) / grp.size),
+                              (int)(((long long)sa.rows * (grp.rank + 1)) / grp.size));
+                __syncthreads();
             }
-            const unsigned cb = T.cwb;
-            const double out = T.outd.value(), cl = T.clq.value();
-            asm volatile("fence.proxy.async.global;" ::: "memory");
-            ens_step_end<NT>(cluster, rank, csize, sh, cb, out, cl, err, &sctl.err);
+            // the scenario index lives in shared memory, not in registers, through the time loop
+            const StripMaps &M = maps[s_cur];
+            const int ns = sa.nstrips + (sa.cx_last >= 0 ? 1 : 0);
+            if (lane == 0 && sa.ntiles > 0) {
+                // the scenario's maps, written to global memory by the host, for this warp's
+                // tensor copies
+                for (int p = 0; p < 2; p++) {
+                    tensormap_acquire(&M.mhi[p]);
+                    tensormap_acquire(&M.v1[p]);
+                    tensormap_acquire(&M.v2[p]);
+                    tensormap_acquire(&M.mlo[p]);
+                }
+                tensormap_acquire(&M.z);
+                tensormap_acquire(&M.th);
+            }
+            // ---- time loop
+            while (clk.active) {
+                if (tid == 0) {
+                    sctl.parity = clk.parity;
+                    sctl.kappa = clk.kappa;
+                    sctl.qr = clk.qr;
+                    sctl.dtf = clk.dtf;
+                    s_next = 0;
+                }
+                __syncthreads();
+                // one worker per warp and step, moved from tile to tile; its reductions
+                // collect the frame units' too
+                Tile<false, EXT> T(sa, R, s_cls, M, sa.cx0, sa.ry0, sa.cx0, sa.ry0);
+                unsigned err = 0u;
+                // this CTA's units are rank, rank + size, ...: its warps take them in order
+                // (the tiles, then the cheaper frame blocks) as they become free
+                for (;;) {
+                    int j = 0;
+                    if (lane == 0) j = atomicAdd(&s_next, 1);
+                    j = __shfl_sync(0xffffffffu, j, 0);
+                    const int u = (int)s_grank + j * (int)s_gsize;
+                    if (u >= sa.nblocks) break;
+                    if (u < sa.ntiles) {
+                        const int strip = u % ns, rblk = u / ns;
+                        const int c0 = strip < sa.nstrips ? sa.cx0 + strip * kSW : sa.cx_last;
+                        const int own_c = strip < sa.nstrips ? c0 : sa.cx0 + sa.nstrips * kSW;
+                        const int r0 = rblk < sa.nrb ? sa.ry0 + rblk * sa.tile_rows : sa.r_last;
+                        const int own_r = rblk < sa.nrb ? r0 : sa.ry0 + sa.nrb * sa.tile_rows;
+                        if ((r0 & 1) == 0) {     // the layout puts every tile on an odd first row
+                            err = kErrTimeout;
+                            break;
+                        }
+                        // the previous tile's ring reads are done before new copies land in it,
+                        // and its barriers (every copy waited for) are reset for the new tile
+                        __syncwarp();
+                        if (ring_used && lane == 0)
+                            for (int k = 0; k < kNC; k++) mbar_inval(&R.bar[k]);
+                        ring_used = true;
+                        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+                        T.place(c0, r0, own_c, own_r);
+                        T.run();
+                        if (__any_sync(0xffffffffu, T.timed_out)) {
+                            // a tensor copy did not arrive in time: wait (bounded) for the
+                            // copies still in flight and stop the scenario with an error
+                            if (lane == 0)
+                                for (int k = max(0, T.n_issued - kNC); k < T.n_issued; k++)
+                                    mbar_wait_bounded(&R.bar[k % kNC], (unsigned)((k / kNC) & 1));
+                            err = kErrTimeout;
+                            break;
+                        }
+                    } else {
+                        frame_cells<EXT>(sa, (long long)(u - sa.ntiles) * kFrameCells, T.cwb, T.outd, T.clq);
+                    }
+                }
+                const unsigned cb = T.cwb;
+                const double out = T.outd.value(), cl = T.clq.value();
+                asm volatile("fence.proxy.async.global;" ::: "memory");
+                Group grp = group();
+                ens_step_end<NT>(grp, sh, cb, out, cl, err, &sctl.err);
+            }
+            Group grp = group();
+            ens_finish<NT>(grp, sh, scen[s_cur], (int)(((long long)sa.rows * grp.rank) / grp.size),
+                           (int)(((long long)sa.rows * (grp.rank + 1)) / grp.size));
         }
-        ens_finish<NT>(cluster, rank, csize, sh, scen[s_cur], (int)(((long long)sa.rows * rank) / csize),
-                       (int)(((long long)sa.rows * (rank + 1)) / csize));
     }
 }
 
 using EnsKernel = void (*)(EnsScenario *, const int *, int, unsigned *);
-using EnsStripKernel = void (*)(EnsScenario *, const StripMaps *, const int *, int, unsigned *);
+using EnsStripKernel = void (*)(EnsScenario *, const StripMaps *, const int *, int, int, unsigned *);
 
 template <int NT, int K, int MODE>
 EnsKernel ens_kernel_ptr()
@@ -548,6 +588,7 @@ struct asx_ensemble {
     StripMaps *maps = nullptr;              // per scenario: the strip kernel's tensor maps
     std::vector<char> maps_ok;              // scenario wide enough for strip tiles
     long long layout_key = -1;              // strip layout in `dev`: tile height (and shape if per scenario)
+    std::vector<int> order_host;            // the queue order uploaded to `order`
     cudaGraphExec_t graph = nullptr;
     asx_ensemble_tuning graph_tuning{};
     std::string err;
@@ -571,6 +612,7 @@ asx_status efail(asx_ensemble *e, asx_status st, const std::string &m)
 bool tuning_valid(const asx_ensemble_tuning &t)
 {
     const bool c = t.cluster == 1 || t.cluster == 2 || t.cluster == 4 || t.cluster == kEnsMaxCluster;
+    if (t.split < 0 || (t.split > 0 && (t.tile_rows == 0 || t.cluster < 2))) return false;
     if (t.tile_rows != 0) {
         const bool h = t.tile_rows == 1 || t.tile_rows == 8 || t.tile_rows == 16 || t.tile_rows == 32;
         return c && h && (t.threads == 128 || t.threads == 256) && t.cells_per_thread == 1;
@@ -656,20 +698,24 @@ double modelled_step(const asx_ensemble *e, int i, int csize, int nw)
 // 32 for every scenario, H = 1 the height of 8, 16, 32 whose modelled step is shortest on
 // clusters of `csize` CTAs of `nw` warps, per scenario (H = 0, the gather kernel, needs
 // none).
-cudaError_t ensure_layout(asx_ensemble *e, int H, int csize, int nw)
+cudaError_t ensure_layout(asx_ensemble *e, int H, int csize, int nw, int split)
 {
-    const long long key = H == 1 ? 1 + 1000LL * csize + 100000LL * nw : H;
+    const long long key = H == 1 ? 1 + 1000LL * csize + 100000LL * nw + 100000000LL * split : H;
     if (H == 0 || e->layout_key == key) return cudaSuccess;
+    std::vector<int> pos(e->n);
+    for (int q = 0; q < e->n; q++) pos[e->order_host[q]] = q;
     for (int i = 0; i < e->n; i++) {
         if (H != 1) {
             scenario_layout(e, i, H);
             continue;
         }
+        // the group that runs scenario i: a whole cluster, or one CTA after the split
+        const int gs = split > 0 && pos[i] >= split ? 1 : csize;
         int best = 32;
         double best_t = 0.0;
         for (int h : {32, 16, 8}) {
             scenario_layout(e, i, h);
-            const double t = modelled_step(e, i, csize, nw);
+            const double t = modelled_step(e, i, gs, nw);
             if (h == 32 || t < best_t) {
                 best = h;
                 best_t = t;
@@ -684,7 +730,7 @@ cudaError_t ensure_layout(asx_ensemble *e, int H, int csize, int nw)
 
 cudaError_t ensure_layout(asx_ensemble *e, const asx_ensemble_tuning &t)
 {
-    return ensure_layout(e, t.tile_rows, t.cluster, t.threads / 32);
+    return ensure_layout(e, t.tile_rows, t.cluster, t.threads / 32, t.split);
 }
 
 cudaError_t launch_ensemble(asx_ensemble *e, const asx_ensemble_tuning &t, cudaStream_t s)
@@ -704,14 +750,15 @@ cudaError_t launch_ensemble(asx_ensemble *e, const asx_ensemble_tuning &t, cudaS
     cfg.stream = s;
     cfg.attrs = at;
     cfg.numAttrs = 1;
-    cudaError_t x = cudaMemsetAsync(e->queue, 0, sizeof(unsigned), s);
+    cudaError_t x = cudaMemsetAsync(e->queue, 0, 2 * sizeof(unsigned), s);
     if (x != cudaSuccess) return x;
     (void)f;
     if (t.tile_rows == 0)
         return cudaLaunchKernelEx(&cfg, ens_kernel(t.threads, t.cells_per_thread, e->mode), e->dev,
                                   (const int *)e->order, e->n, e->queue);
+    const int n_big = t.split > 0 ? std::min(t.split, e->n) : e->n;
     return cudaLaunchKernelEx(&cfg, ens_strip_kernel(t.threads, e->mode), e->dev, (const StripMaps *)e->maps,
-                              (const int *)e->order, e->n, e->queue);
+                              (const int *)e->order, e->n, n_big, e->queue);
 }
 
 // Restores every scenario's initial state and clock (the state lives in parity 0 and a
@@ -784,7 +831,7 @@ asx_status asx_create_ensemble(int n, const asx_scenario_desc *descs, void *cuda
     if (x == cudaSuccess) x = cudaMalloc(&e->samples, total_samples * sizeof(double));
     if (x == cudaSuccess) x = cudaMalloc(&e->dev, n * sizeof(EnsScenario));
     if (x == cudaSuccess) x = cudaMalloc(&e->order, n * sizeof(int));
-    if (x == cudaSuccess) x = cudaMalloc(&e->queue, sizeof(unsigned));
+    if (x == cudaSuccess) x = cudaMalloc(&e->queue, 2 * sizeof(unsigned));
     if (x == cudaSuccess) x = cudaMalloc(&e->maps, n * sizeof(StripMaps));
     if (x == cudaSuccess) x = cudaMemsetAsync(e->buf, 0, total * sizeof(float), e->stream);
     if (x != cudaSuccess) {
@@ -881,6 +928,7 @@ asx_status asx_create_ensemble(int n, const asx_scenario_desc *descs, void *cuda
         const double wq = (double)descs[q].rows * descs[q].cols * descs[q].t_end / descs[q].edge_m;
         return wp > wq;
     });
+    e->order_host = ord;
     x = cudaMemcpyAsync(e->order, ord.data(), n * sizeof(int), cudaMemcpyHostToDevice, e->stream);
     if (x == cudaSuccess)
         x = cudaMemcpyAsync(e->dev, e->host.data(), n * sizeof(EnsScenario), cudaMemcpyHostToDevice, e->stream);
@@ -1041,6 +1089,8 @@ asx_status asx_ensemble_run(asx_ensemble *e, const asx_ensemble_tuning *tuning)
         auto work = [&](int i) { return (double)e->desc[i].rows * e->desc[i].cols * (double)e->work_steps[i]; };
         std::stable_sort(ord.begin(), ord.end(), [&](int p, int q) { return work(p) > work(q); });
         ENS_CUDA(e, cudaMemcpy(e->order, ord.data(), e->n * sizeof(int), cudaMemcpyHostToDevice));
+        if (ord != e->order_host) e->layout_key = -1;   // per-scenario layouts follow the order
+        e->order_host = ord;
     }
     return ASX_OK;
 }
@@ -1077,15 +1127,18 @@ asx_status asx_ensemble_autotune(asx_ensemble *e, int max_steps, asx_ensemble_tu
     ENS_CUDA(e, cudaEventCreate(&b));
     float best_ms = std::numeric_limits<float>::infinity();
     asx_ensemble_tuning best = e->tuning;
-    // the gather kernel's 36 shapes, then the strip kernel's 32 (cluster x tile workers
-    // per CTA x tile height, or the height chosen per scenario)
+    // the gather kernel's 36 shapes, the strip kernel's 32 (cluster x tile workers per
+    // CTA x tile height, or the height chosen per scenario), and 8 split shapes
     std::vector<asx_ensemble_tuning> shapes;
     for (int c : {1, 2, 4, 8}) {
         for (int t : {128, 256, 512})
-            for (int k : {1, 2, 4}) shapes.push_back(asx_ensemble_tuning{c, t, k, 0});
+            for (int k : {1, 2, 4}) shapes.push_back(asx_ensemble_tuning{c, t, k, 0, 0});
         for (int t : {128, 256})
-            for (int h : {1, 8, 16, 32}) shapes.push_back(asx_ensemble_tuning{c, t, 1, h});
+            for (int h : {1, 8, 16, 32}) shapes.push_back(asx_ensemble_tuning{c, t, 1, h, 0});
     }
+    // the largest scenarios on whole clusters, the rest on single CTAs
+    for (int c : {4, 8})
+        for (int sp : {8, 16, 32, 64}) shapes.push_back(asx_ensemble_tuning{c, 256, 1, 1, sp});
     asx_status st = ASX_OK;
     // one untimed launch first (first-launch costs), then the faster of two timings per
     // shape: a single short timing is noisy enough to rank shapes wrongly

@@ -377,7 +377,7 @@ def pipeline(n: int = 256, l: float = 2.0, n_train: int = 20000, n_held: int = 1
     say = log or (lambda *_: None)
     tuning = autotune(n, l)
     say(f"autotuned: cluster {tuning.cluster} threads {tuning.threads} cells/thread {tuning.cells_per_thread} "
-        f"tile rows {tuning.tile_rows}")
+        f"tile rows {tuning.tile_rows} split {tuning.split}")
     st_train = SolveStats()
     X, Y = dataset(TRAIN_SEED0, n_train, n, l, workers, chunk, st_train, tuning)
     say(f"training runs: {n_train} in {st_train.wall:.1f} s ({st_train.hydrographs_per_s:.1f} hydrographs/s)")
@@ -425,7 +425,7 @@ def pipeline(n: int = 256, l: float = 2.0, n_train: int = 20000, n_held: int = 1
                              final_loss=fit["history"][-1][1] if fit["history"] else None),
                   held_out=held, serve=serve,
                   tuning=dict(cluster=tuning.cluster, threads=tuning.threads, cells_per_thread=tuning.cells_per_thread,
-                              tile_rows=tuning.tile_rows))
+                              tile_rows=tuning.tile_rows, split=tuning.split))
     return report, model
 
 

@@ -78,7 +78,7 @@ def test_ensemble_autotune_and_oracle(asx, orc):
     E = Ensemble(scs)
     t = E.autotune(max_steps=20)
     assert t.cluster in (1, 2, 4, 8) and t.threads in (128, 256, 512) and t.cells_per_thread in (1, 2, 4)
-    assert t.tile_rows in (0, 8, 16, 32)
+    assert t.tile_rows in (0, 1, 8, 16, 32) and t.split >= 0
     E.run()
     for i in (1, 4):
         sc = scs[i]
@@ -111,7 +111,7 @@ def test_ensemble_tuning_after_a_complete_run(asx):
     assert all(c[0] == sc.t_end for (_, c, _), sc in zip(ref, scs))
     t = E.autotune(max_steps=5)
     assert t.cluster in (1, 2, 4, 8) and t.threads in (128, 256, 512) and t.cells_per_thread in (1, 2, 4)
-    assert t.tile_rows in (0, 8, 16, 32)
+    assert t.tile_rows in (0, 1, 8, 16, 32) and t.split >= 0
     E.run((2, 256, 2))
     for i in range(len(scs)):
         st, clk, out = ref[i]
@@ -173,10 +173,12 @@ def test_strip_ensemble_matches_single_rasters_bitwise(asx, monkeypatch, tile_ro
     E.close()
 
 
-@pytest.mark.parametrize("tuning", [(1, 128, 1, 16), (4, 128, 1, 16), (8, 256, 1, 16)])
+@pytest.mark.parametrize("tuning", [(1, 128, 1, 16), (4, 128, 1, 16), (8, 256, 1, 16), (4, 256, 1, 16, 2),
+                                    (8, 128, 1, 16, 5)])
 def test_strip_ensemble_launch_shapes_agree(asx, tuning):
-    """Cluster size and tile workers per CTA change which warp computes a tile, not what:
-    the states are identical for every strip launch shape of one tile height."""
+    """Cluster size, tile workers per CTA and the split (the largest scenarios on whole
+    clusters, the rest on single CTAs) change which warp computes a tile, not what: the
+    states are identical for every strip launch shape of one tile height."""
     from paper_2406_14933_gb300.ensemble import Ensemble
     scs = _strip_scenarios(t_end=40.0)
     E = Ensemble(scs)
@@ -189,16 +191,17 @@ def test_strip_ensemble_launch_shapes_agree(asx, tuning):
     E.close()
 
 
-def test_strip_ensemble_tile_height_per_scenario(asx, monkeypatch):
-    """With the tile height chosen per scenario (tile_rows = 1), each scenario equals, bit
-    for bit and step for step, the single raster run by the strip kernel at one of the
-    heights 8, 16, 32."""
+@pytest.mark.parametrize("tuning", [(4, 256, 1, 1), (4, 256, 1, 1, 2)])
+def test_strip_ensemble_tile_height_per_scenario(asx, monkeypatch, tuning):
+    """With the tile height chosen per scenario (tile_rows = 1; with and without a split),
+    each scenario equals, bit for bit and step for step, the single raster run by the strip
+    kernel at one of the heights 8, 16, 32."""
     from paper_2406_14933_gb300.ensemble import Ensemble
     from paper_2406_14933_gb300.raster import Raster
     monkeypatch.delenv("ASX_STEP_KERNEL", raising=False)
     scs = _strip_scenarios(t_end=30.0)
     E = Ensemble(scs)
-    E.run((4, 256, 1, 1))
+    E.run(tuning)
     got = [(E.state(i), E.clock(i)) for i in range(len(scs))]
     E.close()
     for i, sc in enumerate(scs):
@@ -239,7 +242,8 @@ def test_strip_ensemble_against_oracle(asx, orc):
 
 
 @pytest.mark.parametrize("tuning", [(2, 512, 1, 16), (2, 256, 2, 16), (2, 256, 1, 12), (3, 256, 1, 16),
-                                    (2, 512, 1, 1), (2, 256, 1, 2)])
+                                    (2, 512, 1, 1), (2, 256, 1, 2), (2, 256, 1, 16, -1), (1, 256, 1, 16, 2),
+                                    (2, 256, 2, 0, 2)])
 def test_ensemble_rejects_bad_strip_shapes(asx, tuning):
     from paper_2406_14933_gb300.asx import AsxError, ASX_EINVAL
     from paper_2406_14933_gb300.ensemble import Ensemble

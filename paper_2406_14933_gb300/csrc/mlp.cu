@@ -550,53 +550,75 @@ __device__ __forceinline__ void load_chunk(unsigned char *dst, const unsigned ch
                  : "memory");
 }
 
-// Hidden-layer epilogue of accumulator row r (this thread's TMEM lane), columns
-// [c0, c1) (a multiple of 32): + bias, ReLU, BF16 (round to nearest even), into the
-// activation image.
-__device__ __forceinline__ void epi_hidden(unsigned trow, const float *__restrict__ bias, unsigned char *act, int r,
-                                           int c0, int c1)
+// BF16 pair of ReLU(a + b) (element 0 in the low half): a packed float32 add (each
+// component rounded as the scalar add), round to nearest even, then the maximum with zero
+// on the BF16 pair (rounding is monotone and keeps zero, so this is ReLU before rounding).
+__device__ __forceinline__ unsigned bias_relu_bf16x2(float a0, float a1, float b0, float b1)
+{
+    unsigned r;
+    asm("{\n\t.reg .b64 ra, rb, rd;\n\t.reg .f32 s0, s1;\n\t.reg .b32 h, z;\n\t"
+        "mov.b64 ra, {%1, %2};\n\tmov.b64 rb, {%3, %4};\n\tadd.rn.f32x2 rd, ra, rb;\n\t"
+        "mov.b64 {s0, s1}, rd;\n\tcvt.rn.bf16x2.f32 h, s1, s0;\n\tmov.b32 z, 0;\n\t"
+        "max.bf16x2 %0, h, z;\n\t}"
+        : "=r"(r)
+        : "f"(a0), "f"(a1), "f"(b0), "f"(b1));
+    return r;
+}
+
+// Hidden-layer epilogue of accumulator row r (this thread's TMEM lane) of the nt tiles,
+// columns [c0, c1) (a multiple of 32): + bias, ReLU, BF16 (round to nearest even), into
+// each tile's activation image.  The biases are loaded once for the tiles.
+__device__ __forceinline__ void epi_hidden(unsigned trow, int nt, const float *__restrict__ bias,
+                                           unsigned char *const *act, int r, int c0, int c1)
 {
     for (int nc = c0; nc < c1; nc += 32) {
-        float v[32];
-        tc_ld32(trow + (unsigned)nc, v);
-        unsigned w[16];
+        float bv[32];
 #pragma unroll
         for (int q = 0; q < 8; q++) {
             const float4 b = __ldg(reinterpret_cast<const float4 *>(bias + nc) + q);
-            const __nv_bfloat162 h0 = __floats2bfloat162_rn(fmaxf(v[4 * q] + b.x, 0.0f), fmaxf(v[4 * q + 1] + b.y, 0.0f));
-            const __nv_bfloat162 h1 =
-                __floats2bfloat162_rn(fmaxf(v[4 * q + 2] + b.z, 0.0f), fmaxf(v[4 * q + 3] + b.w, 0.0f));
-            w[2 * q] = *reinterpret_cast<const unsigned *>(&h0);
-            w[2 * q + 1] = *reinterpret_cast<const unsigned *>(&h1);
+            bv[4 * q] = b.x;
+            bv[4 * q + 1] = b.y;
+            bv[4 * q + 2] = b.z;
+            bv[4 * q + 3] = b.w;
         }
+        for (int t = 0; t < nt; t++) {
+            float v[32];
+            tc_ld32(trow + (unsigned)(t * kHid + nc), v);
+            unsigned w[16];
 #pragma unroll
-        for (int g8 = 0; g8 < 4; g8++)
-            *reinterpret_cast<uint4 *>(act + cm_off_k(kTM, r, nc + 8 * g8)) =
-                make_uint4(w[4 * g8], w[4 * g8 + 1], w[4 * g8 + 2], w[4 * g8 + 3]);
+            for (int j = 0; j < 16; j++) w[j] = bias_relu_bf16x2(v[2 * j], v[2 * j + 1], bv[2 * j], bv[2 * j + 1]);
+#pragma unroll
+            for (int g8 = 0; g8 < 4; g8++)
+                *reinterpret_cast<uint4 *>(act[t] + cm_off_k(kTM, r, nc + 8 * g8)) =
+                    make_uint4(w[4 * g8], w[4 * g8 + 1], w[4 * g8 + 2], w[4 * g8 + 3]);
+        }
     }
 }
 
 // Output epilogue of one tile: + bias, FP32, rows m0 .. m0 + 127 of y.  Each warp owns 32
-// rows (its TMEM lanes) x 32 columns: it passes them through a padded 32 x 33 block of
-// shared memory, so that each of its stores writes 32 consecutive floats of one row.
+// rows (its TMEM lanes) x 32 columns: it passes them through a 32 x 36 block of shared
+// memory (rows 144 bytes apart: 16-byte accesses of eight lanes hit 32 distinct banks), so
+// that each store instruction writes four rows of 32 consecutive floats.
+constexpr int kStageLd = 36;
 __device__ __forceinline__ void epi_output(unsigned trow, const float *__restrict__ bias, float *stage, float *y,
                                            int m0, int batch, int quarter, int cgroup)
 {
     const int lane = threadIdx.x & 31, c0 = cgroup * 32;
     float v[32];
     tc_ld32(trow + (unsigned)c0, v);
+    float4 *srow = reinterpret_cast<float4 *>(stage + lane * kStageLd);
 #pragma unroll
     for (int q = 0; q < 8; q++) {
         const float4 b = __ldg(reinterpret_cast<const float4 *>(bias + c0) + q);
-        stage[lane * 33 + 4 * q] = v[4 * q] + b.x;
-        stage[lane * 33 + 4 * q + 1] = v[4 * q + 1] + b.y;
-        stage[lane * 33 + 4 * q + 2] = v[4 * q + 2] + b.z;
-        stage[lane * 33 + 4 * q + 3] = v[4 * q + 3] + b.w;
+        srow[q] = make_float4(v[4 * q] + b.x, v[4 * q + 1] + b.y, v[4 * q + 2] + b.z, v[4 * q + 3] + b.w);
     }
     __syncwarp();
-    for (int rr = 0; rr < 32; rr++) {
+#pragma unroll
+    for (int i = 0; i < 8; i++) {
+        const int rr = 4 * i + (lane >> 3), q = lane & 7;
         const int m = m0 + quarter * 32 + rr;
-        if (m < batch) y[(size_t)m * kOut + c0 + lane] = stage[rr * 33 + lane];
+        const float4 val = reinterpret_cast<const float4 *>(stage + rr * kStageLd)[q];
+        if (m < batch) reinterpret_cast<float4 *>(y + (size_t)m * kOut + c0)[q] = val;
     }
     __syncwarp();
 }
@@ -766,16 +788,15 @@ __global__ void __launch_bounds__(kFusedThreads, 1) mlp_fused_fwd_kernel(const F
                 ok = false;
                 break;
             }
-            for (int t = 0; t < nt; t++) {
-                const unsigned tr = trow + (unsigned)(t * kHid);
-                if (l < 3) {
-                    epi_hidden(tr, bias[l], sAct[t], row, cgroup * (kHid / kColGroups),
-                               (cgroup + 1) * (kHid / kColGroups));
-                } else {
-                    // the activations are spent: their buffers hold each warp's 32 x 33 block
-                    epi_output(tr, f.b4, reinterpret_cast<float *>(sAct[0]) + warp * 32 * 33, f.y, m0 + t * kTM,
-                               f.batch, quarter, cgroup);
-                }
+            if (l < 3) {
+                epi_hidden(trow, nt, bias[l], sAct, row, cgroup * (kHid / kColGroups),
+                           (cgroup + 1) * (kHid / kColGroups));
+            } else {
+                // the activations are spent: their buffers hold each warp's 32 x 36 block
+                for (int t = 0; t < nt; t++)
+                    epi_output(trow + (unsigned)(t * kHid), f.b4,
+                               reinterpret_cast<float *>(sAct[0]) + warp * 32 * kStageLd, f.y, m0 + t * kTM, f.batch,
+                               quarter, cgroup);
             }
             if (l < 3) asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
             asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");

@@ -218,6 +218,40 @@ def test_strip_ensemble_tile_height_per_scenario(asx, monkeypatch, tuning):
         assert match, f"scenario {i} matches no single-raster tile height"
 
 
+@pytest.mark.parametrize("tuning", [(2, 256, 1, 16), (4, 128, 1, 8, 1)])
+def test_strip_ensemble_optional_terms_and_inflow(asx, monkeypatch, tuning):
+    """The strip ensemble kernel with the optional terms compiled in (artificial viscosity,
+    linear resistance, dry threshold) and a given-flux inflow side (frame code): each
+    scenario equals the single raster run by the strip kernel at the same tile height, bit
+    for bit, and its ledger books the inflow."""
+    from paper_2406_14933_gb300.ensemble import Ensemble
+    from paper_2406_14933_gb300.raster import Raster
+    monkeypatch.delenv("ASX_STEP_KERNEL", raising=False)
+    monkeypatch.setenv("ASX_TILE_ROWS", str(tuning[3]))
+    scs = []
+    for i, n in enumerate((200, 150, 261)):
+        sc = inputs.ensemble_member(40 + i, n_override=n, t_end=40.0)
+        sc.sample_dt = 10.0
+        sc.viscosity = True
+        sc.tau = 0.02
+        sc.h_dry = 1.0e-4
+        scs.append(sc)
+    scs[0].bc = (inputs.FLUX, inputs.FREE, inputs.WALL, inputs.WALL)
+    scs[0].bc_q = (0.01, 0.0, 0.0, 0.0)
+    E = Ensemble(scs)
+    E.run(tuning)
+    for i, sc in enumerate(scs):
+        R = Raster(sc)
+        R.run_until(sc.t_end)
+        assert E.clock(i)[1] == R.clock()[2]
+        for a, b in zip(E.state(i), R.state()):
+            assert np.array_equal(a, b)
+        assert E.ledger(i).defect_rel <= 1e-10
+        R.close()
+    assert E.ledger(0).outflow < 0.0           # the inflow side feeds more than leaves
+    E.close()
+
+
 def test_strip_ensemble_against_oracle(asx, orc):
     """Two strip-ensemble scenarios (tiles and frame) against the FP64 oracle on their own
     time steps, to the stated tolerance, with closed budgets."""

@@ -440,9 +440,12 @@ namespace {
 // chunks load during the epilogue.  CTAs are persistent over the pairs.  Shared memory:
 // 2 x 16 KB inputs + 2 x 64 KB activations + 64 KB ring.
 
-constexpr int kFusedThreads = 512;     // 16 warps: warp w reads TMEM lanes 32 (w % 4) .. +31
-constexpr int kProducer = 32;          // the thread that issues the weight copies (warp 1, lane 0)
-constexpr int kColGroups = kFusedThreads / 128;   // ... and a quarter of the columns, w / 4
+// 18 warps: warp 0 issues the products, warp 1 the weight copies, warps 2..17 stage the
+// inputs and run the epilogues; warp w reads TMEM lanes 32 (w % 4) .. +31 (the hardware's
+// lane quarter of a warp) and a quarter of the columns, (w - 2) / 4.
+constexpr int kEpiWarps = 16;
+constexpr int kFusedThreads = 32 * (2 + kEpiWarps);
+constexpr int kColGroups = 4;
 constexpr unsigned kWtBytes1 = (unsigned)kHid * kInPad * 2;   // W1: 32 KB
 constexpr unsigned kWtBytesH = (unsigned)kHid * kHid * 2;     // W2, W3: 128 KB each
 constexpr unsigned kWtBytes4 = (unsigned)kOut * kHid * 2;     // W4: 64 KB
@@ -450,18 +453,11 @@ constexpr unsigned kWtOff1 = 0, kWtOff2 = kWtBytes1, kWtOff3 = kWtOff2 + kWtByte
 constexpr unsigned kWtTotal = kWtOff4 + kWtBytes4;
 constexpr int kSmX = kTM * kInPad * 2;                        // 16 KB per tile
 constexpr int kSmAct = kTM * kHid * 2;                        // 64 KB per tile
-#ifndef ASX_MLP_CK
-#define ASX_MLP_CK 64
-#endif
-#ifndef ASX_MLP_NSLOT
-#define ASX_MLP_NSLOT 2
-#endif
-constexpr int kCK = ASX_MLP_CK;                               // K columns of a weight chunk
-constexpr int kNSlot = ASX_MLP_NSLOT;                         // ring slots
-constexpr unsigned kSlot = (unsigned)kHid * kCK * 2;          // one chunk of 256 rows
-constexpr int kChunksPerPair = (kInPad + 3 * kHid) / kCK;     // W1, then W2, W3, W4 by K chunks
+constexpr int kCK = 64;                                       // K columns of a weight chunk
+constexpr int kNSlot = 2;                                     // ring slots
+constexpr unsigned kSlot = (unsigned)kHid * kCK * 2;          // 32 KB: one chunk of 256 rows
+constexpr int kChunksPerPair = (kInPad + 3 * kHid) / kCK;     // 13: W1, then W2, W3, W4 by K chunks
 constexpr int kFusedSmem = 2 * kSmX + 2 * kSmAct + kNSlot * (int)kSlot + 128;
-static_assert(kCK == 32 || kCK == 64, "chunk width");
 static_assert(kFusedSmem <= 232448, "shared memory per CTA");
 
 // Chunk jj of a pair's weight stream: its layer, the chunk's index in the layer, byte
@@ -596,31 +592,47 @@ __device__ __forceinline__ void epi_hidden(unsigned trow, int nt, const float *_
 }
 
 // Output epilogue of one tile: + bias, FP32, rows m0 .. m0 + 127 of y.  Each warp owns 32
-// rows (its TMEM lanes) x 32 columns: it passes them through a 32 x 36 block of shared
-// memory (rows 144 bytes apart: 16-byte accesses of eight lanes hit 32 distinct banks), so
-// that each store instruction writes four rows of 32 consecutive floats.
-constexpr int kStageLd = 36;
+// rows (its TMEM lanes) x 32 columns: it passes them through a 32 x 32 block of shared
+// memory (4 KB; 16-byte chunk q of row r stored at chunk q ^ (r & 7), so that eight lanes'
+// 16-byte accesses hit 32 distinct banks), and each store instruction writes four rows of
+// 32 consecutive floats.
 __device__ __forceinline__ void epi_output(unsigned trow, const float *__restrict__ bias, float *stage, float *y,
                                            int m0, int batch, int quarter, int cgroup)
 {
     const int lane = threadIdx.x & 31, c0 = cgroup * 32;
     float v[32];
     tc_ld32(trow + (unsigned)c0, v);
-    float4 *srow = reinterpret_cast<float4 *>(stage + lane * kStageLd);
+    float4 *srow = reinterpret_cast<float4 *>(stage + lane * 32);
 #pragma unroll
     for (int q = 0; q < 8; q++) {
         const float4 b = __ldg(reinterpret_cast<const float4 *>(bias + c0) + q);
-        srow[q] = make_float4(v[4 * q] + b.x, v[4 * q + 1] + b.y, v[4 * q + 2] + b.z, v[4 * q + 3] + b.w);
+        srow[q ^ (lane & 7)] = make_float4(v[4 * q] + b.x, v[4 * q + 1] + b.y, v[4 * q + 2] + b.z, v[4 * q + 3] + b.w);
     }
     __syncwarp();
 #pragma unroll
     for (int i = 0; i < 8; i++) {
         const int rr = 4 * i + (lane >> 3), q = lane & 7;
         const int m = m0 + quarter * 32 + rr;
-        const float4 val = reinterpret_cast<const float4 *>(stage + rr * kStageLd)[q];
+        const float4 val = reinterpret_cast<const float4 *>(stage + rr * 32)[q ^ (rr & 7)];
         if (m < batch) reinterpret_cast<float4 *>(y + (size_t)m * kOut + c0)[q] = val;
     }
     __syncwarp();
+}
+
+__device__ __forceinline__ void mbar_arrive1(unsigned long long *bar)
+{
+    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(su32(bar)) : "memory");
+}
+
+// Bounded wait that also gives up when another role has failed (*fail set).
+__device__ __forceinline__ bool wait_or_fail(unsigned long long *bar, unsigned parity, volatile int *fail)
+{
+    if (mbar_try(bar, parity)) return true;
+    const unsigned long long t0 = global_ns();
+    for (;;) {
+        if (mbar_try(bar, parity)) return true;
+        if (*fail || global_ns() - t0 > kWaitLimitNs) return false;
+    }
 }
 
 // The weight stream of one CTA (issued by one thread): chunk j of the stream is chunk
@@ -661,9 +673,13 @@ __global__ void __launch_bounds__(kFusedThreads, 1) mlp_fused_fwd_kernel(const F
     unsigned char *sX[2] = {base, base + kSmX};
     unsigned char *sAct[2] = {base + 2 * kSmX, base + 2 * kSmX + kSmAct};
     unsigned char *sW = base + 2 * kSmX + 2 * kSmAct;
-    __shared__ __align__(8) unsigned long long bar_full[kNSlot], bar_empty[kNSlot], bar_acc;
+    // full / empty: the weight ring; acc[t]: tile t's products of a layer are done;
+    // epi[t]: tile t's hidden epilogue is done (16 arrivals); xrdy: a pair's inputs are
+    // staged (16 arrivals)
+    __shared__ __align__(8) unsigned long long bar_full[kNSlot], bar_empty[kNSlot], bar_acc[2], bar_epi[2], bar_x;
     __shared__ unsigned tmem_base;
-    const int tid = threadIdx.x, warp = tid >> 5;
+    __shared__ int s_fail;
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     const int ntiles = (f.batch + kTM - 1) / kTM, npairs = (ntiles + 1) / 2;
     const int my_pairs = (int)blockIdx.x < npairs ? (npairs - 1 - (int)blockIdx.x) / (int)gridDim.x + 1 : 0;
     if (warp == 0) {
@@ -677,149 +693,170 @@ __global__ void __launch_bounds__(kFusedThreads, 1) mlp_fused_fwd_kernel(const F
             mbar_init1(&bar_full[k]);
             mbar_init1(&bar_empty[k]);
         }
-        mbar_init1(&bar_acc);
+        for (int t = 0; t < 2; t++) {
+            mbar_init1(&bar_acc[t]);
+            asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(su32(&bar_epi[t])), "r"(kEpiWarps) : "memory");
+        }
+        asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(su32(&bar_x)), "r"(kEpiWarps) : "memory");
+        s_fail = 0;
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     }
     asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
     __syncthreads();
     asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
     const unsigned tmem = tmem_base;
-    const int quarter = warp & 3, cgroup = warp >> 2;
-    const int row = quarter * 32 + (tid & 31);              // this thread's accumulator row
-    const unsigned trow = tmem + ((unsigned)(quarter * 32) << 16);
-    WeightStream ws;
-    ws.wt = f.wt;
-    ws.ring = sW;
-    ws.full = bar_full;
-    ws.empty = bar_empty;
-    ws.total = my_pairs * kChunksPerPair;
-    if (tid == kProducer) ws.refill();
-    const float *bias[3] = {f.b1, f.b2, f.b3};
-    unsigned pacc = 0;                 // phase of bar_acc
-    int g = 0;                         // first chunk of the running layer (every thread)
-    int acc_out = 0;                   // an accumulator commit issued but not waited for
-    bool ok = true, mma_ok = true;     // mma_ok: thread 0's waits for copies
-    for (int pi = 0; pi < my_pairs && ok; pi++) {
-        const int pair = (int)blockIdx.x + pi * (int)gridDim.x;
-        const int m0 = pair * 2 * kTM;
-        const int nt = min(2, ntiles - 2 * pair);           // tiles in this pair (1 or 2)
-        // ---- input tiles to BF16, K padded to 64: one (row, 8-column group) per thread and pass
-        for (int u = tid; u < 2 * kTM * (kInPad / 8); u += kFusedThreads) {
-            const int r = u % (2 * kTM), kg = u / (2 * kTM), m = m0 + r;
-            float xv[8] = {0.0f, 0.0f, 0.0f, 0.0f, 0.0f, 0.0f, 0.0f, 0.0f};
-            if (m < f.batch && kg * 8 < kIn) {
-                const float4 *xr = reinterpret_cast<const float4 *>(f.x + (size_t)m * kIn + kg * 8);
-                const float4 a4 = xr[0];
-                xv[0] = a4.x;
-                xv[1] = a4.y;
-                xv[2] = a4.z;
-                xv[3] = a4.w;
-                if (kg * 8 + 4 < kIn) {
-                    const float4 b4v = xr[1];
-                    xv[4] = b4v.x;
-                    xv[5] = b4v.y;
-                    xv[6] = b4v.z;
-                    xv[7] = b4v.w;
-                }
-            }
-            unsigned w[4];
-#pragma unroll
-            for (int j = 0; j < 4; j++) {
-                const __nv_bfloat162 h = __floats2bfloat162_rn(xv[2 * j], xv[2 * j + 1]);
-                w[j] = *reinterpret_cast<const unsigned *>(&h);
-            }
-            *reinterpret_cast<uint4 *>(sX[r >> 7] + cm_off(r & (kTM - 1), kg * 8)) = make_uint4(w[0], w[1], w[2], w[3]);
-        }
-        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-        __syncthreads();
-        // ---- layers 1..4
-        for (int l = 0; l < 4 && ok; l++) {
-            const int nch = (l == 0 ? kInPad : kHid) / kCK, N = l == 3 ? kOut : kHid;
-            if (tid == 0) {
-                // products: each chunk as soon as its copy has landed
-                asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-                const unsigned idesc = instr_desc(N);
-                for (int c = 0; c < nch; c++) {
-                    const int gg = g + c;
-                    if (!mbar_wait_bounded1(&bar_full[gg % kNSlot], (unsigned)((gg / kNSlot) & 1))) {
-                        mma_ok = false;
-                        break;
-                    }
-                    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-                    const unsigned bw = su32(sW + (gg % kNSlot) * kSlot);
-                    for (int t = 0; t < nt; t++) {
-                        const unsigned ab = su32(l == 0 ? sX[t] : sAct[t]);
-                        for (int s = 0; s < kCK / 16; s++) {
-                            // A: K columns c kCK + 16 s .. +15 of the tile's K/64-chunked operand
-                            const int k = c * kCK + 16 * s;
-                            const unsigned long long da =
-                                smem_desc(ab + (unsigned)((k >> 6) * kTM * 128 + ((k & 63) >> 3) * 128), 128, 1024);
-                            const unsigned long long db = smem_desc(bw + (unsigned)(s * 256), 128, kCK / 8 * 128);
-                            tc_mma(tmem + (unsigned)(t * kHid), da, db, idesc, (c > 0 || s > 0) ? 1u : 0u);
+    volatile int *fail = &s_fail;
+    if (warp == 0) {
+        // ---- products (one thread)
+        if (lane == 0) {
+            int g = 0;                         // first chunk of the running layer
+            unsigned px = 0, pe[2] = {0, 0};   // phases of bar_x and bar_epi
+            bool ok = true;
+            for (int pi = 0; pi < my_pairs && ok; pi++) {
+                const int nt = min(2, ntiles - 2 * ((int)blockIdx.x + pi * (int)gridDim.x));
+                ok = wait_or_fail(&bar_x, px, fail);            // this pair's inputs are staged
+                px ^= 1u;
+                for (int l = 0; l < 4 && ok; l++) {
+                    const int nch = (l == 0 ? kInPad : kHid) / kCK;
+                    const unsigned idesc = instr_desc(l == 3 ? kOut : kHid);
+                    for (int c = 0; c < nch && ok; c++) {
+                        const int gg = g + c;
+                        ok = wait_or_fail(&bar_full[gg % kNSlot], (unsigned)((gg / kNSlot) & 1), fail);
+                        if (!ok) break;
+                        asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+                        const unsigned bw = su32(sW + (gg % kNSlot) * kSlot);
+                        for (int t = 0; t < nt && ok; t++) {
+                            if (c == 0 && l > 0) {
+                                // tile t's operand and accumulator are free once its previous
+                                // epilogue is done; the other tile's epilogue may still run
+                                ok = wait_or_fail(&bar_epi[t], pe[t], fail);
+                                pe[t] ^= 1u;
+                                if (!ok) break;
+                                asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+                            }
+                            const unsigned ab = su32(l == 0 ? sX[t] : sAct[t]);
+                            for (int s = 0; s < kCK / 16; s++) {
+                                // A: K columns c kCK + 16 s .. +15 of the tile's K/64-chunked operand
+                                const int k = c * kCK + 16 * s;
+                                const unsigned long long da = smem_desc(
+                                    ab + (unsigned)((k >> 6) * kTM * 128 + ((k & 63) >> 3) * 128), 128, 1024);
+                                const unsigned long long db = smem_desc(bw + (unsigned)(s * 256), 128, kCK / 8 * 128);
+                                tc_mma(tmem + (unsigned)(t * kHid), da, db, idesc, (c > 0 || s > 0) ? 1u : 0u);
+                            }
+                            if (c == nch - 1) tc_commit(&bar_acc[t]);   // tile t's layer is done
                         }
+                        if (ok) tc_commit(&bar_empty[gg % kNSlot]);
                     }
-                    tc_commit(&bar_empty[gg % kNSlot]);
+                    g += nch;
                 }
-                if (mma_ok) {
-                    tc_commit(&bar_acc);        // arrives when every product issued so far is done
-                    acc_out = 1;
+            }
+            if (!ok) {
+                // let every product issued land before the tensor memory is released
+                *fail = 1;
+                tc_commit(&bar_empty[0]);
+                mbar_wait_bounded1(&bar_empty[0], 0u);
+                mbar_wait_bounded1(&bar_empty[0], 1u);
+            }
+        }
+    } else if (warp == 1) {
+        // ---- weight copies (one thread): free each chunk's slot when its products are
+        // done and refill the ring
+        if (lane == 0) {
+            WeightStream ws;
+            ws.wt = f.wt;
+            ws.ring = sW;
+            ws.full = bar_full;
+            ws.empty = bar_empty;
+            ws.total = my_pairs * kChunksPerPair;
+            ws.refill();
+            for (int j = 0; j < ws.total && ws.ok && !*fail; j++) {
+                ws.free_through(j);
+                ws.refill();
+            }
+            if (!ws.ok || *fail) {
+                *fail = 1;
+                for (int j = ws.freed; j < ws.issued; j++)
+                    mbar_wait_bounded1(&bar_full[j % kNSlot], (unsigned)((j / kNSlot) & 1));
+            }
+        }
+    } else {
+        // ---- input staging and epilogues (warps 2..17)
+        const int quarter = warp & 3, cgroup = (warp - 2) >> 2;
+        const int row = quarter * 32 + lane;                  // this thread's accumulator row
+        const unsigned trow = tmem + ((unsigned)(quarter * 32) << 16);
+        const float *bias[3] = {f.b1, f.b2, f.b3};
+        unsigned pa[2] = {0, 0};                              // phases of bar_acc
+        bool ok = true;
+        for (int pi = 0; pi < my_pairs && ok; pi++) {
+            const int pair = (int)blockIdx.x + pi * (int)gridDim.x;
+            const int m0 = pair * 2 * kTM;
+            const int nt = min(2, ntiles - 2 * pair);
+            // input tiles to BF16, K padded to 64: one (row, 8-column group) per thread and pass
+            for (int u = tid - 64; u < 2 * kTM * (kInPad / 8); u += 32 * kEpiWarps) {
+                const int r = u % (2 * kTM), kg = u / (2 * kTM), m = m0 + r;
+                float xv[8] = {0.0f, 0.0f, 0.0f, 0.0f, 0.0f, 0.0f, 0.0f, 0.0f};
+                if (m < f.batch && kg * 8 < kIn) {
+                    const float4 *xr = reinterpret_cast<const float4 *>(f.x + (size_t)m * kIn + kg * 8);
+                    const float4 a4 = xr[0];
+                    xv[0] = a4.x;
+                    xv[1] = a4.y;
+                    xv[2] = a4.z;
+                    xv[3] = a4.w;
+                    if (kg * 8 + 4 < kIn) {
+                        const float4 b4v = xr[1];
+                        xv[4] = b4v.x;
+                        xv[5] = b4v.y;
+                        xv[6] = b4v.z;
+                        xv[7] = b4v.w;
+                    }
                 }
-            } else if (tid == kProducer) {
-                // copies: free each of the layer's chunks when its products are done and
-                // refill the ring, which ends with the next layer's first chunks in flight
-                for (int j = g; j < g + nch && ws.ok; j++) {
-                    ws.free_through(j);
-                    ws.refill();
+                unsigned w[4];
+#pragma unroll
+                for (int j = 0; j < 4; j++) {
+                    const __nv_bfloat162 h = __floats2bfloat162_rn(xv[2 * j], xv[2 * j + 1]);
+                    w[j] = *reinterpret_cast<const unsigned *>(&h);
                 }
-            } else if ((tid & 31) == 0 && l < 3) {
-                // the next epilogue's biases into L1 while the products run
-                const float *nb = l < 2 ? bias[l + 1] : f.b4;
-                const int span = l < 2 ? kHid : kOut;            // the bias vector's length
-                asm volatile("prefetch.global.L1 [%0];" ::"l"(nb + ((warp & 7) * 32) % span) : "memory");
+                *reinterpret_cast<uint4 *>(sX[r >> 7] + cm_off(r & (kTM - 1), kg * 8)) =
+                    make_uint4(w[0], w[1], w[2], w[3]);
             }
-            g += nch;
-            ok = !__syncthreads_or((tid == 0 && !mma_ok) || (tid == kProducer && !ws.ok));
-            if (!ok) break;
-            ok = mbar_wait_bounded1(&bar_acc, pacc);
-            pacc ^= 1u;
-            acc_out = 0;
-            asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-            if (__syncthreads_or(!ok)) {
-                ok = false;
-                break;
-            }
-            if (l < 3) {
-                epi_hidden(trow, nt, bias[l], sAct, row, cgroup * (kHid / kColGroups),
-                           (cgroup + 1) * (kHid / kColGroups));
-            } else {
-                // the activations are spent: their buffers hold each warp's 32 x 36 block
-                for (int t = 0; t < nt; t++)
-                    epi_output(trow + (unsigned)(t * kHid), f.b4,
-                               reinterpret_cast<float *>(sAct[0]) + warp * 32 * kStageLd, f.y, m0 + t * kTM, f.batch,
-                               quarter, cgroup);
-            }
-            if (l < 3) asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+            // this warp's share of the inputs (and of the previous pair's output epilogue,
+            // which read the accumulators the first products overwrite) is done
+            asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
             asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
-            __syncthreads();
+            __syncwarp();
+            if (lane == 0) mbar_arrive1(&bar_x);
+            for (int l = 0; l < 4 && ok; l++) {
+                for (int t = 0; t < nt && ok; t++) {
+                    ok = wait_or_fail(&bar_acc[t], pa[t], fail);
+                    pa[t] ^= 1u;
+                    if (!ok) break;
+                    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+                    if (l < 3) {
+                        unsigned char *act[1] = {sAct[t]};
+                        epi_hidden(trow + (unsigned)(t * kHid), 1, bias[l], act, row, cgroup * (kHid / kColGroups),
+                                   (cgroup + 1) * (kHid / kColGroups));
+                        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+                        asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+                        __syncwarp();
+                        if (lane == 0) mbar_arrive1(&bar_epi[t]);
+                    } else {
+                        // the tile's activations are spent: their buffer holds the warps'
+                        // 32 x 32 output blocks
+                        epi_output(trow + (unsigned)(t * kHid), f.b4,
+                                   reinterpret_cast<float *>(sAct[t]) + (warp - 2) * 32 * 32, f.y, m0 + t * kTM, f.batch,
+                                   quarter, cgroup);
+                    }
+                }
+            }
         }
+        if (!ok) *fail = 1;
     }
-    if (!ok) {
-        // a wait ran out: flag it, and let the products and copies still in flight land
-        // (bounded) before the tensor memory is released
-        if (tid == 0) {
-            if (f.err) atomicOr(f.err, 1);
-            tc_commit(&bar_acc);                // arrives when every product issued is done
-            if (acc_out) mbar_wait_bounded1(&bar_acc, pacc);
-            mbar_wait_bounded1(&bar_acc, pacc ^ (acc_out ? 1u : 0u));
-        }
-        if (tid == kProducer)
-            for (int j = ws.freed; j < ws.issued; j++)
-                mbar_wait_bounded1(&bar_full[j % kNSlot], (unsigned)((j / kNSlot) & 1));
-        __syncthreads();
-    }
+    __syncthreads();
+    if (s_fail && tid == 0 && f.err) atomicOr(f.err, 1);
     asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
     __syncthreads();
     if (warp == 0) {
+        __syncwarp();
         asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(2 * kHid) : "memory");
     }
 }

@@ -726,9 +726,10 @@ __global__ void __launch_bounds__(kFusedThreads, 1) mlp_fused_fwd_kernel(const F
                         asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
                         const unsigned bw = su32(sW + (gg % kNSlot) * kSlot);
                         for (int t = 0; t < nt && ok; t++) {
-                            if (c == 0 && l > 0) {
+                            if (c == 0 && (l > 0 || pi > 0)) {
                                 // tile t's operand and accumulator are free once its previous
-                                // epilogue is done; the other tile's epilogue may still run
+                                // epilogue (the last pair's output, for the first layer) is
+                                // done; the other tile's epilogue may still run
                                 ok = wait_or_fail(&bar_epi[t], pe[t], fail);
                                 pe[t] ^= 1u;
                                 if (!ok) break;
@@ -787,11 +788,10 @@ __global__ void __launch_bounds__(kFusedThreads, 1) mlp_fused_fwd_kernel(const F
         const float *bias[3] = {f.b1, f.b2, f.b3};
         unsigned pa[2] = {0, 0};                              // phases of bar_acc
         bool ok = true;
-        for (int pi = 0; pi < my_pairs && ok; pi++) {
-            const int pair = (int)blockIdx.x + pi * (int)gridDim.x;
-            const int m0 = pair * 2 * kTM;
-            const int nt = min(2, ntiles - 2 * pair);
-            // input tiles to BF16, K padded to 64: one (row, 8-column group) per thread and pass
+        // input tiles of pair pi to BF16, K padded to 64: one (row, 8-column group) per
+        // thread and pass; then this warp's share is announced on bar_x
+        auto stage_inputs = [&](int pi) {
+            const int m0 = ((int)blockIdx.x + pi * (int)gridDim.x) * 2 * kTM;
             for (int u = tid - 64; u < 2 * kTM * (kInPad / 8); u += 32 * kEpiWarps) {
                 const int r = u % (2 * kTM), kg = u / (2 * kTM), m = m0 + r;
                 float xv[8] = {0.0f, 0.0f, 0.0f, 0.0f, 0.0f, 0.0f, 0.0f, 0.0f};
@@ -819,12 +819,15 @@ __global__ void __launch_bounds__(kFusedThreads, 1) mlp_fused_fwd_kernel(const F
                 *reinterpret_cast<uint4 *>(sX[r >> 7] + cm_off(r & (kTM - 1), kg * 8)) =
                     make_uint4(w[0], w[1], w[2], w[3]);
             }
-            // this warp's share of the inputs (and of the previous pair's output epilogue,
-            // which read the accumulators the first products overwrite) is done
             asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-            asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
             __syncwarp();
             if (lane == 0) mbar_arrive1(&bar_x);
+        };
+        if (my_pairs > 0) stage_inputs(0);
+        for (int pi = 0; pi < my_pairs && ok; pi++) {
+            const int pair = (int)blockIdx.x + pi * (int)gridDim.x;
+            const int m0 = pair * 2 * kTM;
+            const int nt = min(2, ntiles - 2 * pair);
             for (int l = 0; l < 4 && ok; l++) {
                 for (int t = 0; t < nt && ok; t++) {
                     ok = wait_or_fail(&bar_acc[t], pa[t], fail);
@@ -836,9 +839,6 @@ __global__ void __launch_bounds__(kFusedThreads, 1) mlp_fused_fwd_kernel(const F
                         epi_hidden(trow + (unsigned)(t * kHid), 1, bias[l], act, row, cgroup * (kHid / kColGroups),
                                    (cgroup + 1) * (kHid / kColGroups));
                         asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-                        asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
-                        __syncwarp();
-                        if (lane == 0) mbar_arrive1(&bar_epi[t]);
                     } else {
                         // the tile's activations are spent: their buffer holds the warps'
                         // 32 x 32 output blocks
@@ -846,7 +846,14 @@ __global__ void __launch_bounds__(kFusedThreads, 1) mlp_fused_fwd_kernel(const F
                                    reinterpret_cast<float *>(sAct[t]) + (warp - 2) * 32 * 32, f.y, m0 + t * kTM, f.batch,
                                    quarter, cgroup);
                     }
+                    // tile t's accumulator is read (and, below the output layer, its next
+                    // operand written)
+                    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+                    __syncwarp();
+                    if (lane == 0) mbar_arrive1(&bar_epi[t]);
                 }
+                // the first layer's products are done with the inputs: stage the next pair's
+                if (l == 0 && ok && pi + 1 < my_pairs) stage_inputs(pi + 1);
             }
         }
         if (!ok) *fail = 1;

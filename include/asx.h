@@ -271,7 +271,7 @@ typedef struct {
  * 32: the strip kernel (each warp a TMA-fed tile worker over tiles of 128 columns x
  * tile_rows rows, the cells along the sides gathered; the same per-cell code, hence the
  * same bits, as a single raster's strip kernel with that tile height), threads per CTA
- * 128 or 256 (4 or 8 tile workers), cells_per_thread 1.  tile_rows = 1: the strip kernel
+ * 128, 256 or 512 (4, 8 or 16 tile workers), cells_per_thread 1.  tile_rows = 1: the strip kernel
  * with each scenario's tile height (8, 16 or 32) chosen on the host as the one whose
  * modelled step on this cluster is shortest (few, larger tiles for large rasters; more,
  * smaller ones where large tiles would leave warps idle).  split = 0: every scenario runs

@@ -394,7 +394,7 @@ __global__ void __launch_bounds__(NT, 1024 / NT) ensemble_kernel(EnsScenario *sc
 // queue[0]); once they are all taken, every CTA of the cluster runs the remaining
 // scenarios alone (popped from queue[1]), with CTA barriers only.
 template <int NW, bool EXT>
-__global__ void __launch_bounds__(NW * 32, 16 / NW) ensemble_strip_kernel(EnsScenario *scen, const StripMaps *maps,
+__global__ void __launch_bounds__(NW * 32, NW <= 16 ? 16 / NW : 1) ensemble_strip_kernel(EnsScenario *scen, const StripMaps *maps,
                                                                           const int *order, int n_scen, int n_big,
                                                                           unsigned *queue)
 {
@@ -550,12 +550,15 @@ EnsKernel ens_kernel(int nt, int k, int mode)
     return mode >= 2 ? ens_kernel_m<2>(nt, k) : mode == 1 ? ens_kernel_m<1>(nt, k) : ens_kernel_m<0>(nt, k);
 }
 
-// Strip kernel of `threads` threads (128: 4 tile workers, 256: 8) with or without the
+// Strip kernel of `threads` threads (128: 4 tile workers, 256: 8, 512: 16) with or without the
 // optional terms; inflow sides are frame cells, whose gather code always has them.
 EnsStripKernel ens_strip_kernel(int threads, int mode)
 {
-    if (mode >= 2) return threads == 128 ? ensemble_strip_kernel<4, true> : ensemble_strip_kernel<8, true>;
-    return threads == 128 ? ensemble_strip_kernel<4, false> : ensemble_strip_kernel<8, false>;
+    if (mode >= 2)
+        return threads == 128 ? ensemble_strip_kernel<4, true>
+                              : threads == 256 ? ensemble_strip_kernel<8, true> : ensemble_strip_kernel<16, true>;
+    return threads == 128 ? ensemble_strip_kernel<4, false>
+                          : threads == 256 ? ensemble_strip_kernel<8, false> : ensemble_strip_kernel<16, false>;
 }
 
 size_t ens_strip_smem(int threads) { return (size_t)(threads / 32) * sizeof(StripSmem<false>) + 128; }
@@ -615,7 +618,7 @@ bool tuning_valid(const asx_ensemble_tuning &t)
     if (t.split < 0 || (t.split > 0 && (t.tile_rows == 0 || t.cluster < 2))) return false;
     if (t.tile_rows != 0) {
         const bool h = t.tile_rows == 1 || t.tile_rows == 8 || t.tile_rows == 16 || t.tile_rows == 32;
-        return c && h && (t.threads == 128 || t.threads == 256) && t.cells_per_thread == 1;
+        return c && h && (t.threads == 128 || t.threads == 256 || t.threads == 512) && t.cells_per_thread == 1;
     }
     const bool n = t.threads == 128 || t.threads == 256 || t.threads == 512;
     const bool k = t.cells_per_thread == 1 || t.cells_per_thread == 2 || t.cells_per_thread == 4;
@@ -1127,13 +1130,13 @@ asx_status asx_ensemble_autotune(asx_ensemble *e, int max_steps, asx_ensemble_tu
     ENS_CUDA(e, cudaEventCreate(&b));
     float best_ms = std::numeric_limits<float>::infinity();
     asx_ensemble_tuning best = e->tuning;
-    // the gather kernel's 36 shapes, the strip kernel's 32 (cluster x tile workers per
+    // the gather kernel's 36 shapes, the strip kernel's 48 (cluster x tile workers per
     // CTA x tile height, or the height chosen per scenario), and 8 split shapes
     std::vector<asx_ensemble_tuning> shapes;
     for (int c : {1, 2, 4, 8}) {
         for (int t : {128, 256, 512})
             for (int k : {1, 2, 4}) shapes.push_back(asx_ensemble_tuning{c, t, k, 0, 0});
-        for (int t : {128, 256})
+        for (int t : {128, 256, 512})
             for (int h : {1, 8, 16, 32}) shapes.push_back(asx_ensemble_tuning{c, t, 1, h, 0});
     }
     // the largest scenarios on whole clusters, the rest on single CTAs

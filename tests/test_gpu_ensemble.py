@@ -174,7 +174,7 @@ def test_strip_ensemble_matches_single_rasters_bitwise(asx, monkeypatch, tile_ro
 
 
 @pytest.mark.parametrize("tuning", [(1, 128, 1, 16), (4, 128, 1, 16), (8, 256, 1, 16), (4, 256, 1, 16, 2),
-                                    (8, 128, 1, 16, 5)])
+                                    (8, 128, 1, 16, 5), (2, 512, 1, 16)])
 def test_strip_ensemble_launch_shapes_agree(asx, tuning):
     """Cluster size, tile workers per CTA and the split (the largest scenarios on whole
     clusters, the rest on single CTAs) change which warp computes a tile, not what: the
@@ -275,8 +275,8 @@ def test_strip_ensemble_against_oracle(asx, orc):
     E.close()
 
 
-@pytest.mark.parametrize("tuning", [(2, 512, 1, 16), (2, 256, 2, 16), (2, 256, 1, 12), (3, 256, 1, 16),
-                                    (2, 512, 1, 1), (2, 256, 1, 2), (2, 256, 1, 16, -1), (1, 256, 1, 16, 2),
+@pytest.mark.parametrize("tuning", [(2, 1024, 1, 16), (2, 256, 2, 16), (2, 256, 1, 12), (3, 256, 1, 16),
+                                    (2, 1024, 1, 1), (2, 256, 1, 2), (2, 256, 1, 16, -1), (1, 256, 1, 16, 2),
                                     (2, 256, 2, 0, 2)])
 def test_ensemble_rejects_bad_strip_shapes(asx, tuning):
     from paper_2406_14933_gb300.asx import AsxError, ASX_EINVAL

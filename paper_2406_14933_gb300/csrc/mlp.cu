@@ -33,7 +33,7 @@ namespace {
 
 constexpr int kTM = 128;       // tile rows (TMEM lanes)
 constexpr int kTK = 64;        // K chunk staged per round
-constexpr int kGemmThreads = 128;
+constexpr int kGemmThreads = 256;   // two warps per TMEM lane quarter
 
 // ----------------------------------------------------------------- PTX wrappers
 
@@ -136,8 +136,15 @@ __device__ __forceinline__ void tc_ld32(unsigned taddr, float *v)
 
 // ----------------------------------------------------------------- the GEMM
 
+// Staging of one GEMM operand: 0 = element by element through its strides (any layout);
+// 1 = TMA tiles of an operand whose K index is contiguous; 2 = TMA tiles of an operand
+// whose row (M or N) index is contiguous.
+enum GemmStage : int { kStageStrided = 0, kStageKMajor = 1, kStageMNMajor = 2 };
+
 struct GemmArgs {
+    CUtensorMap ma, mb;            // tensor maps of A and B (staging 1 and 2)
     int M, N, K;
+    int amode, bmode;              // GemmStage of A and B
     const __nv_bfloat16 *A;
     long long sam, sak;            // A(m, k) = A[m sam + k sak]
     const __nv_bfloat16 *B;
@@ -159,23 +166,97 @@ __device__ __forceinline__ unsigned cm_off(int r, int k)
     return (unsigned)(((r >> 3) * (kTK / 8) + (k >> 3)) * 128 + (r & 7) * 16 + (k & 7) * 2);
 }
 
+// Bytes of one K chunk of both operands (A: 128 rows, B: BN rows, 64 BF16 columns each).
+template <int BN>
+constexpr int gemm_stage_bytes()
+{
+    return kTM * kTK * 2 + BN * kTK * 2;
+}
+
+// Two core-matrix images the tensor core reads and two TMA landing tiles.
 template <int BN>
 constexpr int gemm_smem_bytes()
 {
-    return kTM * kTK * 2 + BN * kTK * 2 + 128;
+    return 4 * gemm_stage_bytes<BN>() + 128;
 }
 
-template <int BN>
-__global__ void __launch_bounds__(kGemmThreads) gemm_tc_kernel(const GemmArgs g)
+__device__ __forceinline__ void mbar_expect_tx1(unsigned long long *bar, unsigned bytes)
 {
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(su32(bar)), "r"(bytes) : "memory");
+}
+
+// One box of a 2-D tensor map (x: the contiguous coordinate) into shared memory.
+__device__ __forceinline__ void tma_tile(void *dst, const CUtensorMap *map, int x, int y, unsigned long long *bar)
+{
+    asm volatile(
+        "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes"
+        " [%0], [%1, {%2, %3}], [%4];" ::"r"(su32(dst)),
+        "l"(reinterpret_cast<unsigned long long>(map)), "r"(x), "r"(y), "r"(su32(bar))
+        : "memory");
+}
+
+// One K chunk of an operand P(r, k) (R rows from r0, 64 columns from k0; zero outside the
+// nr x nk matrix) into the core-matrix image `cm`, from the TMA tile `raw` (modes 1 and
+// 2) or from global memory (mode 0).
+template <int R>
+__device__ __forceinline__ void stage_operand(int mode, const unsigned char *raw, unsigned char *cm,
+                                              const __nv_bfloat16 *P, long long s_r, long long s_k, int r0, int k0,
+                                              int nr, int nk)
+{
+    const int tid = threadIdx.x;
+    if (mode == kStageKMajor) {
+        // raw: R rows of 64 elements (128 bytes); its 16-byte piece (r, q) is row r of core
+        // matrix (r / 8, q).  The eight threads of a shared-memory phase take rows r mod 8 =
+        // 0..7 at eight rotations of q, so that both the read and the write touch eight
+        // distinct 16-byte bank groups.
+        for (int i = tid; i < R * 8; i += kGemmThreads) {
+            const int j = i & 7, grp = i >> 3;
+            const int r = (grp % (R / 8)) * 8 + j, q = (j + grp / (R / 8)) & 7;
+            const uint4 v = *reinterpret_cast<const uint4 *>(raw + r * 128 + q * 16);
+            *reinterpret_cast<uint4 *>(cm + cm_off(r, q * 8)) = v;
+        }
+    } else if (mode == kStageMNMajor) {
+        // raw: 64 rows (k) of R elements; piece (r, q) gathers elements k = 8q..8q+7 of row r
+        const unsigned short *rw = reinterpret_cast<const unsigned short *>(raw);
+        for (int i = tid; i < R * 8; i += kGemmThreads) {
+            const int r = i % R, q = i / R;
+            unsigned w[4];
+#pragma unroll
+            for (int j = 0; j < 4; j++)
+                w[j] = (unsigned)rw[(8 * q + 2 * j) * R + r] | ((unsigned)rw[(8 * q + 2 * j + 1) * R + r] << 16);
+            *reinterpret_cast<uint4 *>(cm + cm_off(r, q * 8)) = make_uint4(w[0], w[1], w[2], w[3]);
+        }
+    } else {
+        for (int i = tid; i < R * kTK; i += kGemmThreads) {
+            const int r = i / kTK, k = i % kTK;
+            const int rr = r0 + r, kk = k0 + k;
+            __nv_bfloat16 v = __float2bfloat16(0.0f);
+            if (rr < nr && kk < nk) v = P[(long long)rr * s_r + (long long)kk * s_k];
+            *reinterpret_cast<__nv_bfloat16 *>(cm + cm_off(r, k)) = v;
+        }
+    }
+}
+
+// D = A B^T for one 128 x BN tile per CTA, 64 columns of K per chunk.  Thread 0 keeps the
+// TMA copies of the next two chunks in flight (landing tiles raw[c mod 2], completing on
+// full[c mod 2]); the four warps rearrange each landed chunk into the core-matrix image
+// cm[c mod 2] (operands in mode 0 are read from global memory instead), and thread 0
+// issues the chunk's four tcgen05 products, which commit to done[c mod 2] and so release
+// the image two chunks later.  Every wait is bounded; after a failed wait the copies and
+// products in flight are waited for (bounded) before TMEM is released, and *err is set.
+template <int BN>
+__global__ void __launch_bounds__(kGemmThreads) gemm_tc_kernel(const __grid_constant__ GemmArgs g)
+{
+    constexpr int kA = kTM * kTK * 2, kStage = gemm_stage_bytes<BN>();
     extern __shared__ __align__(128) unsigned char gsm[];
     unsigned char *base = gsm + ((128u - (su32(gsm) & 127u)) & 127u);
-    unsigned char *sA = base;                       // 128 x 64 BF16, core-matrix layout
-    unsigned char *sB = base + kTM * kTK * 2;       // BN x 64 BF16
-    __shared__ __align__(8) unsigned long long bar;
+    __shared__ __align__(8) unsigned long long full[2], done[2];
     __shared__ unsigned tmem_base;
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     const int m0 = blockIdx.x * kTM, n0 = blockIdx.y * BN;
+    const unsigned tx = (g.amode != kStageStrided ? (unsigned)kA : 0u) +
+                        (g.bmode != kStageStrided ? (unsigned)(BN * kTK * 2) : 0u);
+    const int nchunks = (g.K + kTK - 1) / kTK;
     if (warp == 0) {
         asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(su32(&tmem_base)),
                      "r"(BN)
@@ -183,7 +264,10 @@ __global__ void __launch_bounds__(kGemmThreads) gemm_tc_kernel(const GemmArgs g)
         asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
     }
     if (tid == 0) {
-        mbar_init1(&bar);
+        for (int s = 0; s < 2; s++) {
+            mbar_init1(&full[s]);
+            mbar_init1(&done[s]);
+        }
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     }
     asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
@@ -191,64 +275,97 @@ __global__ void __launch_bounds__(kGemmThreads) gemm_tc_kernel(const GemmArgs g)
     asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
     const unsigned tmem = tmem_base;
     const unsigned idesc = instr_desc(BN);
-    bool ok = true;
-    int phase = 0;
-    const int nchunks = (g.K + kTK - 1) / kTK;
-    for (int c = 0; c < nchunks; c++) {
-        const int k0 = c * kTK;
-        // ---- stage A (128 x 64) and B (BN x 64) chunks, zero outside the matrices
-        for (int i = tid; i < kTM * kTK; i += kGemmThreads) {
-            const int r = i / kTK, k = i % kTK;
-            const int m = m0 + r, kk = k0 + k;
-            __nv_bfloat16 v = __float2bfloat16(0.0f);
-            if (m < g.M && kk < g.K) v = g.A[(long long)m * g.sam + (long long)kk * g.sak];
-            *reinterpret_cast<__nv_bfloat16 *>(sA + cm_off(r, k)) = v;
+    auto cm_of = [&](int s) { return base + s * kStage; };
+    auto raw_of = [&](int s) { return base + (2 + s) * kStage; };
+    auto issue = [&](int c) {      // thread 0: chunk c's tiles into raw[c mod 2]
+        const int s = c & 1, k0 = c * kTK;
+        mbar_expect_tx1(&full[s], tx);
+        if (g.amode == kStageKMajor) tma_tile(raw_of(s), &g.ma, k0, m0, &full[s]);
+        if (g.amode == kStageMNMajor) tma_tile(raw_of(s), &g.ma, m0, k0, &full[s]);
+        if (g.bmode == kStageKMajor) tma_tile(raw_of(s) + kA, &g.mb, k0, n0, &full[s]);
+        if (g.bmode == kStageMNMajor) tma_tile(raw_of(s) + kA, &g.mb, n0, k0, &full[s]);
+    };
+    int issued = 0, committed = 0, c = 0;
+    if (tx != 0u && tid == 0)
+        for (; issued < 2 && issued < nchunks; issued++) issue(issued);
+    bool failed = false;
+    for (; c < nchunks; c++) {
+        const int s = c & 1;
+        bool ok = true;
+        // the image is free once chunk c - 2's products are done; the tiles have landed
+        if (c >= 2) ok = mbar_wait_bounded1(&done[s], (unsigned)(((c - 2) >> 1) & 1));
+        if (ok && tx != 0u) ok = mbar_wait_bounded1(&full[s], (unsigned)((c >> 1) & 1));
+        if (__syncthreads_or(!ok)) {
+            failed = true;
+            break;
         }
-        for (int i = tid; i < BN * kTK; i += kGemmThreads) {
-            const int r = i / kTK, k = i % kTK;
-            const int n = n0 + r, kk = k0 + k;
-            __nv_bfloat16 v = __float2bfloat16(0.0f);
-            if (n < g.N && kk < g.K) v = g.B[(long long)n * g.sbn + (long long)kk * g.sbk];
-            *reinterpret_cast<__nv_bfloat16 *>(sB + cm_off(r, k)) = v;
-        }
-        // the tensor core reads shared memory through the async proxy
+        stage_operand<kTM>(g.amode, raw_of(s), cm_of(s), g.A, g.sam, g.sak, m0, c * kTK, g.M, g.K);
+        stage_operand<BN>(g.bmode, raw_of(s) + kA, cm_of(s) + kA, g.B, g.sbn, g.sbk, n0, c * kTK, g.N, g.K);
+        // the tensor core and the next copies reach shared memory through the async proxy
         asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
         __syncthreads();
         if (tid == 0) {
             asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+            const unsigned char *sA = cm_of(s), *sB = cm_of(s) + kA;
 #pragma unroll
-            for (int s = 0; s < kTK / 16; s++) {
-                const unsigned long long da = smem_desc(su32(sA) + s * 256, 128, (kTK / 8) * 128);
-                const unsigned long long db = smem_desc(su32(sB) + s * 256, 128, (kTK / 8) * 128);
-                tc_mma(tmem, da, db, idesc, (c > 0 || s > 0) ? 1u : 0u);
+            for (int k = 0; k < kTK / 16; k++) {
+                const unsigned long long da = smem_desc(su32(sA) + k * 256, 128, (kTK / 8) * 128);
+                const unsigned long long db = smem_desc(su32(sB) + k * 256, 128, (kTK / 8) * 128);
+                tc_mma(tmem, da, db, idesc, (c > 0 || k > 0) ? 1u : 0u);
             }
-            tc_commit(&bar);
+            tc_commit(&done[s]);
+            committed = c + 1;
+            if (tx != 0u && issued < nchunks) issue(issued++);   // chunk c + 2 into raw[s]
         }
-        // wait for the MMAs before the chunk buffers are overwritten (and at the end)
-        if (!mbar_wait_bounded1(&bar, (unsigned)phase)) ok = false;
-        phase ^= 1;
-        asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-        __syncthreads();
     }
-    if (!ok && tid == 0 && g.err) atomicOr(g.err, 1);
-    // ---- epilogue: warp w holds rows 32w..32w+31 of the tile, one row per lane
-    const int m = m0 + warp * 32 + lane;
-    for (int nc = 0; nc < BN; nc += 16) {
-        float v[16];
-        tc_ld16(tmem + ((unsigned)(warp * 32) << 16) + (unsigned)nc, v);
-        if (m < g.M) {
+    // the last commit covers every product issued before it
+    if (!failed && !mbar_wait_bounded1(&done[(nchunks - 1) & 1], (unsigned)(((nchunks - 1) >> 1) & 1))) failed = true;
+    failed = __syncthreads_or(failed) != 0;
+    if (failed && tid == 0) {
+        for (int k = c; k < issued; k++) mbar_wait_bounded1(&full[k & 1], (unsigned)((k >> 1) & 1));
+        for (int k = c >= 2 ? c - 2 : 0; k < committed; k++) mbar_wait_bounded1(&done[k & 1], (unsigned)((k >> 1) & 1));
+        if (g.err) atomicOr(g.err, 1);
+    }
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    // ---- epilogue: warp w reads TMEM lane quarter w mod 4 (tile rows 32 (w mod 4) ..
+    // + 31) and the 32-column blocks w / 4, w / 4 + 2, ...  Each block passes through a
+    // padded 32 x 33 float block of the spent staging memory, so that bias, ReLU, mask
+    // and stores run along rows: lane j takes column j, and each store instruction
+    // writes 32 consecutive columns of one row.  The block's mask values are loaded
+    // before any of its stores.
+    const int quarter = warp & 3, rbase = m0 + quarter * 32;
+    float *blk = reinterpret_cast<float *>(base) + warp * (32 * 33);
+    for (int nc = (warp >> 2) * 32; nc < BN && !failed; nc += 64) {
+        float v[32];
+        tc_ld32(tmem + ((unsigned)(quarter * 32) << 16) + (unsigned)nc, v);
 #pragma unroll
-            for (int j = 0; j < 16; j++) {
-                const int n = n0 + nc + j;
-                if (n >= g.N) break;
-                float x = v[j];
-                if (g.bias) x += g.bias[n];
-                if (g.relu) x = fmaxf(x, 0.0f);
-                if (g.mask && !(__bfloat162float(g.mask[(long long)m * g.ldm + n]) > 0.0f)) x = 0.0f;
-                if (g.outf) g.outf[(long long)m * g.ldo + n] = x;
-                if (g.outb) g.outb[(long long)m * g.ldo + n] = __float2bfloat16(x);
+        for (int j = 0; j < 32; j++) blk[lane * 33 + j] = v[j];
+        __syncwarp();
+        const int n = n0 + nc + lane;
+        if (n < g.N) {
+            const float bn = g.bias ? g.bias[n] : 0.0f;
+            unsigned keep = 0xffffffffu;          // bit rr: row rbase + rr passes the mask
+            if (g.mask) {
+                keep = 0u;
+#pragma unroll
+                for (int rr = 0; rr < 32; rr++)
+                    if (rbase + rr < g.M && __bfloat162float(g.mask[(long long)(rbase + rr) * g.ldm + n]) > 0.0f)
+                        keep |= 1u << rr;
+            }
+#pragma unroll
+            for (int rr = 0; rr < 32; rr++) {
+                if (rbase + rr < g.M) {
+                    float x = blk[rr * 33 + lane];
+                    if (g.bias) x += bn;
+                    if (g.relu) x = fmaxf(x, 0.0f);
+                    if (!((keep >> rr) & 1u)) x = 0.0f;
+                    const long long o = (long long)(rbase + rr) * g.ldo + n;
+                    if (g.outf) g.outf[o] = x;
+                    if (g.outb) g.outb[o] = __float2bfloat16(x);
+                }
             }
         }
+        __syncwarp();
     }
     asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
     __syncthreads();
@@ -259,14 +376,26 @@ __global__ void __launch_bounds__(kGemmThreads) gemm_tc_kernel(const GemmArgs g)
 
 // ----------------------------------------------------------------- small kernels
 
-// db[n] = sum_m dZ[m][n] (FP32 from the BF16 gradient).
-__global__ void bias_grad_kernel(const __nv_bfloat16 *dz, int M, int N, float *db)
+// db[n] = sum_m dZ[m][n] (FP32 from the BF16 gradient).  A block of 32 x 32 threads takes
+// 32 columns: thread (x, y) sums rows y, y + 32, y + 64, ... of column x in that order and
+// the threads of row 0 add the 32 partial sums in order of y, a fixed order, so the
+// result is the same on every run.  Launched with kBiasGradThreads threads per block.
+constexpr int kBiasGradThreads = 1024;
+__global__ void __launch_bounds__(kBiasGradThreads) bias_grad_kernel(const __nv_bfloat16 *dz, int M, int N, float *db)
 {
-    const int n = blockIdx.x * blockDim.x + threadIdx.x;
-    if (n >= N) return;
+    __shared__ float part[32][33];
+    const int x = threadIdx.x & 31, y = threadIdx.x >> 5;
+    const int n = blockIdx.x * 32 + x;
     float s = 0.0f;
-    for (int m = 0; m < M; m++) s += __bfloat162float(dz[(long long)m * N + n]);
-    db[n] = s;
+    if (n < N)
+        for (int m = y; m < M; m += 32) s += __bfloat162float(dz[(long long)m * N + n]);
+    part[y][x] = s;
+    __syncthreads();
+    if (y == 0 && n < N) {
+        float t = 0.0f;
+        for (int k = 0; k < 32; k++) t += part[k][x];
+        db[n] = t;
+    }
 }
 
 // Mean-squared error over a batch and its gradient dY = 2 (Y - T) / (M N) as BF16.
@@ -356,8 +485,22 @@ __global__ void hydro_check_kernel(int batch, int n_check, int len, const int *_
 }
 }  // namespace
 
+// Staging of an operand P(r, k) = P[r s_r + k s_k] of R rows and K columns: TMA tiles of
+// box_r rows x 64 columns where its layout allows them (16-byte aligned base, one unit
+// stride, the other a multiple of 8 elements and at least the contiguous extent), with
+// the tensor map in *map; element by element otherwise.
+int stage_mode(CUtensorMap *map, const __nv_bfloat16 *P, long long s_r, long long s_k, int R, int K, int box_r)
+{
+    if ((reinterpret_cast<uintptr_t>(P) & 15u) != 0) return kStageStrided;
+    if (s_k == 1 && s_r % 8 == 0 && s_r >= K && make_tensor_map_bf16(map, P, R, K, s_r, kTK, box_r))
+        return kStageKMajor;
+    if (s_r == 1 && s_k % 8 == 0 && s_k >= R && make_tensor_map_bf16(map, P, K, R, s_k, box_r, kTK))
+        return kStageMNMajor;
+    return kStageStrided;
+}
+
 template <int BN>
-cudaError_t launch_gemm_bn(const GemmArgs &g, cudaStream_t s)
+cudaError_t launch_gemm_bn(const GemmArgs &g0, cudaStream_t s)
 {
     static bool configured = false;
     if (!configured) {
@@ -366,15 +509,22 @@ cudaError_t launch_gemm_bn(const GemmArgs &g, cudaStream_t s)
         if (e != cudaSuccess) return e;
         configured = true;
     }
+    GemmArgs g = g0;
+    g.amode = stage_mode(&g.ma, g.A, g.sam, g.sak, g.M, g.K, kTM);
+    g.bmode = stage_mode(&g.mb, g.B, g.sbn, g.sbk, g.N, g.K, BN);
     dim3 grid((g.M + kTM - 1) / kTM, (g.N + BN - 1) / BN);
     gemm_tc_kernel<BN><<<grid, kGemmThreads, gemm_smem_bytes<BN>(), s>>>(g);
     return cudaGetLastError();
 }
 
-cudaError_t launch_gemm_tc(const GemmArgs &g, int bn, cudaStream_t s)
+// Tile width: 256 (or 128 for N <= 128) where the grid of such tiles already gives about
+// one CTA per SM, else 64, for up to four times the CTAs: a small GEMM is bound by the
+// latency of each CTA's staging and epilogue, not by the tensor pipe.
+cudaError_t launch_gemm_tc(const GemmArgs &g, cudaStream_t s)
 {
-    if (bn == 256) return launch_gemm_bn<256>(g, s);
-    if (bn == 128) return launch_gemm_bn<128>(g, s);
+    const long long mt = (g.M + kTM - 1) / kTM;
+    if (g.N > 128 && mt * ((g.N + 255) / 256) >= 128) return launch_gemm_bn<256>(g, s);
+    if (g.N > 64 && mt * ((g.N + 127) / 128) >= 128) return launch_gemm_bn<128>(g, s);
     return launch_gemm_bn<64>(g, s);
 }
 
@@ -400,8 +550,7 @@ extern "C" asx_status asx_gemm_bf16(int M, int N, int K, const void *A, long lon
     g.sbk = sbk;
     g.outf = D;
     g.ldo = ldd;
-    const int bn = N >= 256 ? 256 : N > 64 ? 128 : 64;
-    return launch_gemm_tc(g, bn, static_cast<cudaStream_t>(cuda_stream)) == cudaSuccess ? ASX_OK : ASX_ECUDA;
+    return launch_gemm_tc(g, static_cast<cudaStream_t>(cuda_stream)) == cudaSuccess ? ASX_OK : ASX_ECUDA;
 }
 
 // ------------------------------------------------------------------ the MLP
@@ -935,7 +1084,7 @@ cudaError_t forward(asx_mlp *p, int B)
     g.relu = 1;
     g.outb = p->a1;
     g.ldo = kHid;
-    cudaError_t e = launch_gemm_tc(g, 256, p->stream);
+    cudaError_t e = launch_gemm_tc(g, p->stream);
     if (e != cudaSuccess) return e;
     const __nv_bfloat16 *in[2] = {p->a1, p->a2};
     __nv_bfloat16 *out[2] = {p->a2, p->a3};
@@ -946,14 +1095,14 @@ cudaError_t forward(asx_mlp *p, int B)
         g.relu = 1;
         g.outb = out[l];
         g.ldo = kHid;
-        e = launch_gemm_tc(g, 256, p->stream);
+        e = launch_gemm_tc(g, p->stream);
         if (e != cudaSuccess) return e;
     }
     g = gemm(B, kOut, kHid, p->a3, kHid, 1, wb_of(p, 3), kHid, 1, p->err);
     g.bias = p->w + oB4;
     g.outf = p->y;
     g.ldo = kOut;
-    return launch_gemm_tc(g, 128, p->stream);
+    return launch_gemm_tc(g, p->stream);
 }
 
 // Gradients of the mean-squared error of the last forward pass against targets p->tin
@@ -968,14 +1117,14 @@ cudaError_t backward(asx_mlp *p, int B)
     GemmArgs g = gemm(kOut, kHid, B, p->dy, 1, kOut, p->a3, 1, kHid, p->err);   // dW4 = dY^T A3
     g.outf = p->g + oW4;
     g.ldo = kHid;
-    if ((e = launch_gemm_tc(g, 256, p->stream)) != cudaSuccess) return e;
-    bias_grad_kernel<<<1, kOut, 0, p->stream>>>(p->dy, B, kOut, p->g + oB4);
+    if ((e = launch_gemm_tc(g, p->stream)) != cudaSuccess) return e;
+    bias_grad_kernel<<<(kOut + 31) / 32, kBiasGradThreads, 0, p->stream>>>(p->dy, B, kOut, p->g + oB4);
     g = gemm(B, kHid, kOut, p->dy, kOut, 1, wb_of(p, 3), 1, kHid, p->err);      // dZ3 = (dY W4) r'(z3)
     g.mask = p->a3;
     g.ldm = kHid;
     g.outb = p->dz;
     g.ldo = kHid;
-    if ((e = launch_gemm_tc(g, 256, p->stream)) != cudaSuccess) return e;
+    if ((e = launch_gemm_tc(g, p->stream)) != cudaSuccess) return e;
     // layers 3 and 2
     const __nv_bfloat16 *act_in[2] = {p->a2, p->a1};
     const long long ow[2] = {oW3, oW2}, ob[2] = {oB3, oB2};
@@ -984,14 +1133,14 @@ cudaError_t backward(asx_mlp *p, int B)
         g = gemm(kHid, kHid, B, cur, 1, kHid, act_in[l], 1, kHid, p->err);       // dW = dZ^T A_in
         g.outf = p->g + ow[l];
         g.ldo = kHid;
-        if ((e = launch_gemm_tc(g, 256, p->stream)) != cudaSuccess) return e;
-        bias_grad_kernel<<<1, kHid, 0, p->stream>>>(cur, B, kHid, p->g + ob[l]);
+        if ((e = launch_gemm_tc(g, p->stream)) != cudaSuccess) return e;
+        bias_grad_kernel<<<(kHid + 31) / 32, kBiasGradThreads, 0, p->stream>>>(cur, B, kHid, p->g + ob[l]);
         g = gemm(B, kHid, kHid, cur, kHid, 1, wb_of(p, 2 - l), 1, kHid, p->err);  // dZ_in = (dZ W) r'
         g.mask = act_in[l];
         g.ldm = kHid;
         g.outb = nxt;
         g.ldo = kHid;
-        if ((e = launch_gemm_tc(g, 256, p->stream)) != cudaSuccess) return e;
+        if ((e = launch_gemm_tc(g, p->stream)) != cudaSuccess) return e;
         __nv_bfloat16 *t = cur;
         cur = nxt;
         nxt = t;
@@ -1000,8 +1149,8 @@ cudaError_t backward(asx_mlp *p, int B)
     g = gemm(kHid, kInPad, B, cur, 1, kHid, p->x0, 1, kInPad, p->err);           // dW1 = dZ1^T X
     g.outf = p->g + oW1;
     g.ldo = kInPad;
-    if ((e = launch_gemm_tc(g, 64, p->stream)) != cudaSuccess) return e;
-    bias_grad_kernel<<<1, kHid, 0, p->stream>>>(cur, B, kHid, p->g + oB1);
+    if ((e = launch_gemm_tc(g, p->stream)) != cudaSuccess) return e;
+    bias_grad_kernel<<<(kHid + 31) / 32, kBiasGradThreads, 0, p->stream>>>(cur, B, kHid, p->g + oB1);
     return cudaGetLastError();
 }
 

@@ -60,6 +60,20 @@ bool make_tensor_map_2d(CUtensorMap *m, void *base, bool u8, int rows, int cols,
     return make_map(m, base, u8, rows, cols, pitch, box_x, box_y);
 }
 
+bool make_tensor_map_bf16(CUtensorMap *m, const void *base, long long rows, long long cols, long long ld, int box_x,
+                          int box_y)
+{
+    EncodeTiledFn enc = encode_fn();
+    if (!enc) return false;
+    cuuint64_t dims[2] = {(cuuint64_t)cols, (cuuint64_t)rows};
+    cuuint64_t strides[1] = {(cuuint64_t)ld * 2};
+    cuuint32_t box[2] = {(cuuint32_t)box_x, (cuuint32_t)box_y};
+    cuuint32_t estr[2] = {1, 1};
+    return enc(m, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, const_cast<void *>(base), dims, strides, box, estr,
+               CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+               CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+}
+
 bool make_strip_maps(StripMaps &m, const StepArgs &a, int rows, int cols, int pitch)
 {
     bool ok = true;

@@ -346,11 +346,15 @@ __global__ void __launch_bounds__(kGemmThreads) gemm_tc_kernel(const __grid_cons
             const float bn = g.bias ? g.bias[n] : 0.0f;
             unsigned keep = 0xffffffffu;          // bit rr: row rbase + rr passes the mask
             if (g.mask) {
+                // all 32 loads unconditional (rows past the matrix read its last row), so
+                // that they are in flight together
+                __nv_bfloat16 mk[32];
+#pragma unroll
+                for (int rr = 0; rr < 32; rr++) mk[rr] = g.mask[(long long)min(rbase + rr, g.M - 1) * g.ldm + n];
                 keep = 0u;
 #pragma unroll
                 for (int rr = 0; rr < 32; rr++)
-                    if (rbase + rr < g.M && __bfloat162float(g.mask[(long long)(rbase + rr) * g.ldm + n]) > 0.0f)
-                        keep |= 1u << rr;
+                    if (rbase + rr < g.M && __bfloat162float(mk[rr]) > 0.0f) keep |= 1u << rr;
             }
 #pragma unroll
             for (int rr = 0; rr < 32; rr++) {
@@ -414,12 +418,32 @@ __global__ void mse_grad_kernel(const float *y, const float *t, int n_elem, floa
     if ((threadIdx.x & 31) == 0 && l != 0.0f) atomicAdd(loss_acc, l * scale);
 }
 
-// Adam on FP32 master weights, refreshing the BF16 copy.
-__global__ void adam_kernel(float *w, const float *grad, float *mo, float *ve, __nv_bfloat16 *wb, int n, float lr,
-                            float b1, float b2, float eps, float c1, float c2, float wd)
+// Adam on FP32 master weights over up to kAdamSegs segments in one launch (element i of
+// the launch belongs to the segment s with start[s] <= i < start[s + 1]), refreshing the
+// BF16 copy where a segment has one; decay wd per segment.
+constexpr int kAdamSegs = 8;
+struct AdamArgs {
+    float *w[kAdamSegs];
+    const float *grad[kAdamSegs];
+    float *mo[kAdamSegs], *ve[kAdamSegs];
+    __nv_bfloat16 *wb[kAdamSegs];
+    float wd[kAdamSegs];
+    int start[kAdamSegs + 1];
+    int nseg;
+    float lr, b1, b2, eps, c1, c2;
+};
+
+__global__ void adam_kernel(const AdamArgs a)
 {
-    const int i = blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= n) return;
+    const int t = blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= a.start[a.nseg]) return;
+    int sg = 0;
+    while (t >= a.start[sg + 1]) sg++;
+    const int i = t - a.start[sg];
+    float *w = a.w[sg], *mo = a.mo[sg], *ve = a.ve[sg];
+    const float *grad = a.grad[sg];
+    __nv_bfloat16 *wb = a.wb[sg];
+    const float wd = a.wd[sg], lr = a.lr, b1 = a.b1, b2 = a.b2, eps = a.eps, c1 = a.c1, c2 = a.c2;
     const float gi = grad[i] + wd * w[i];
     const float m = b1 * mo[i] + (1.0f - b1) * gi;
     const float v = b2 * ve[i] + (1.0f - b2) * gi * gi;
@@ -1414,13 +1438,26 @@ asx_status asx_mlp_train_step(asx_mlp *p, int batch, const float *x, const float
     const long long segs[8][3] = {{oW1, (long long)kHid * kInPad, 0}, {oB1, kHid, -1}, {oW2, (long long)kHid * kHid, 1},
                                   {oB2, kHid, -1}, {oW3, (long long)kHid * kHid, 2}, {oB3, kHid, -1},
                                   {oW4, (long long)kOut * kHid, 3}, {oB4, kOut, -1}};
+    AdamArgs aa{};
+    aa.nseg = 8;
+    aa.lr = lr;
+    aa.b1 = b1;
+    aa.b2 = b2;
+    aa.eps = 1e-8f;
+    aa.c1 = c1;
+    aa.c2 = c2;
     for (int s = 0; s < 8; s++) {
         const long long o = segs[s][0], n = segs[s][1];
         const int l = (int)segs[s][2];
-        adam_kernel<<<(unsigned)((n + 255) / 256), 256, 0, p->stream>>>(
-            p->w + o, p->g + o, p->m + o, p->v + o, l >= 0 ? wb_of(p, l) : nullptr, (int)n, lr, b1, b2, 1e-8f, c1, c2,
-            l >= 0 ? weight_decay : 0.0f);
+        aa.w[s] = p->w + o;
+        aa.grad[s] = p->g + o;
+        aa.mo[s] = p->m + o;
+        aa.ve[s] = p->v + o;
+        aa.wb[s] = l >= 0 ? wb_of(p, l) : nullptr;
+        aa.wd[s] = l >= 0 ? weight_decay : 0.0f;
+        aa.start[s + 1] = aa.start[s] + (int)n;
     }
+    adam_kernel<<<(unsigned)((aa.start[8] + 255) / 256), 256, 0, p->stream>>>(aa);
     MLP_CUDA(p, cudaGetLastError());
     p->wt_dirty = true;
     if (loss) {

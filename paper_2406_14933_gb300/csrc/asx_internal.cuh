@@ -155,11 +155,6 @@ struct StripMaps {
 // 2-D tensor map over a pitched rows x cols plane (float32, or uint8 if u8); elements
 // outside the plane read as zero.  False if the driver refuses the map.
 bool make_tensor_map_2d(CUtensorMap *m, void *base, bool u8, int rows, int cols, int pitch, int box_x, int box_y);
-// 2-D tensor map over a BF16 matrix of `rows` rows of `cols` elements, `ld` elements
-// apart (16-byte aligned base, ld a multiple of 8); boxes of box_x x box_y elements;
-// out-of-range elements read as zero.  False if the driver refuses the map.
-bool make_tensor_map_bf16(CUtensorMap *m, const void *base, long long rows, long long cols, long long ld, int box_x,
-                          int box_y);
 // The strip kernel's maps of a raster's planes (a.cls non-null: class boxes, else theta).
 bool make_strip_maps(StripMaps &m, const StepArgs &a, int rows, int cols, int pitch);
 

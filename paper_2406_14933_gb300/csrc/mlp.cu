@@ -29,6 +29,14 @@
 #include "asx_internal.cuh"
 
 namespace asx {
+
+// 2-D tensor map over a BF16 matrix of `rows` rows of `cols` elements, `ld` elements
+// apart (16-byte aligned base, ld a multiple of 8); boxes of box_x x box_y elements;
+// out-of-range elements read as zero.  False if the driver refuses the map.  Defined in
+// runtime.cu beside the other tensor-map builders.
+bool make_tensor_map_bf16(CUtensorMap *m, const void *base, long long rows, long long cols, long long ld, int box_x,
+                          int box_y);
+
 namespace {
 
 constexpr int kTM = 128;       // tile rows (TMEM lanes)

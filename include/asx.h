@@ -330,8 +330,12 @@ const char *asx_ensemble_last_error(const asx_ensemble *e);
  * accumulation in tensor memory): the product the surrogate MLP is made of (not in the
  * paper; the learned hydrograph surrogate is this library's addition).  A(m, k) =
  * A[m*sam + k*sak] and B(n, k) = B[n*sbn + k*sbk] are BF16 device arrays read through
- * these element strides; D is FP32, row stride ldd >= N.  Asynchronous on cuda_stream.
- * ASX_EINVAL on non-positive sizes, null pointers or ldd < N. */
+ * these element strides; D is FP32, row stride ldd >= N.  An operand whose base is
+ * 16-byte aligned, with one stride 1 and the other a multiple of 8 that is at least the
+ * contiguous extent (K, or M / N), is staged by TMA tile copies; any other operand is
+ * read element by element (same results either way).  Asynchronous on cuda_stream.
+ * ASX_EINVAL on non-positive sizes, null pointers or ldd < N; ASX_ECUDA if the launch
+ * fails. */
 asx_status asx_gemm_bf16(int M, int N, int K, const void *A, long long sam, long long sak, const void *B,
                          long long sbn, long long sbk, float *D, long long ldd, void *cuda_stream);
 

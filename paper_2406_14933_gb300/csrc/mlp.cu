@@ -18,6 +18,7 @@
 // weight gradient are all this one kernel.
 #include <cuda_bf16.h>
 
+#include <algorithm>
 #include <cmath>
 #include <cstdlib>
 #include <cstdint>
@@ -1065,6 +1066,20 @@ struct asx_mlp {
     float *y = nullptr, *xin = nullptr, *tin = nullptr, *loss = nullptr;
     int *err = nullptr;
     long long adam_t = 0;
+    // The training step's kernels after its input copies, as a CUDA graph per batch size:
+    // captured (on the private stream cap) at the second step with that batch size, the
+    // first having run them eagerly; exec null where capture was not possible.  Each
+    // launch first sets the Adam node's scalars.
+    struct TrainGraph {
+        int batch;
+        cudaGraph_t graph;             // kept: the Adam node's handle belongs to it
+        cudaGraphExec_t exec;
+        cudaGraphNode_t adam;
+        cudaKernelNodeParams kp;
+    };
+    std::vector<TrainGraph> graphs;
+    std::vector<int> seen;
+    cudaStream_t cap = nullptr;
     std::string error;
 };
 
@@ -1252,6 +1267,83 @@ asx_status stage_inputs(asx_mlp *p, int B, const float *x, const float *t, int k
     return ASX_OK;
 }
 
+// The two input copies of a training step into p->xin and p->tin.
+asx_status copy_inputs(asx_mlp *p, int B, const float *x, const float *t, int kind)
+{
+    const cudaMemcpyKind mk = kind == ASX_PTR_HOST ? cudaMemcpyHostToDevice : cudaMemcpyDeviceToDevice;
+    MLP_CUDA(p, cudaMemcpyAsync(p->xin, x, sizeof(float) * (size_t)B * kIn, mk, p->stream));
+    MLP_CUDA(p, cudaMemcpyAsync(p->tin, t, sizeof(float) * (size_t)B * kOut, mk, p->stream));
+    return ASX_OK;
+}
+
+// The kernels of a training step on the inputs in p->xin / p->tin: padding, forward
+// pass, gradients and the Adam update with the scalars in aa.
+cudaError_t train_kernels(asx_mlp *p, int B, const AdamArgs &aa)
+{
+    const long long n = (long long)B * kInPad;
+    pad_input_kernel<<<(unsigned)((n + 255) / 256), 256, 0, p->stream>>>(p->xin, B, kIn, kInPad, p->x0);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    if ((e = forward(p, B)) != cudaSuccess) return e;
+    if ((e = backward(p, B)) != cudaSuccess) return e;
+    adam_kernel<<<(unsigned)((aa.start[aa.nseg] + 255) / 256), 256, 0, p->stream>>>(aa);
+    return cudaGetLastError();
+}
+
+// The graph of batch size B's step (see asx_mlp::TrainGraph), or nullptr while the step
+// is to run eagerly.
+asx_mlp::TrainGraph *train_graph(asx_mlp *p, int B, const AdamArgs &aa)
+{
+    for (auto &g : p->graphs)
+        if (g.batch == B) return &g;
+    if (std::find(p->seen.begin(), p->seen.end(), B) == p->seen.end()) {
+        p->seen.push_back(B);
+        return nullptr;
+    }
+    asx_mlp::TrainGraph tg{B, nullptr, nullptr, nullptr, cudaKernelNodeParams{}};
+    cudaGraph_t graph = nullptr;
+    if (p->cap || cudaStreamCreateWithFlags(&p->cap, cudaStreamNonBlocking) == cudaSuccess) {
+        const cudaStream_t user = p->stream;
+        p->stream = p->cap;
+        cudaError_t e = cudaStreamBeginCapture(p->cap, cudaStreamCaptureModeThreadLocal);
+        if (e == cudaSuccess) {
+            e = train_kernels(p, B, aa);
+            const cudaError_t e2 = cudaStreamEndCapture(p->cap, &graph);
+            if (e == cudaSuccess) e = e2;
+        }
+        p->stream = user;
+        if (e != cudaSuccess && graph) {
+            cudaGraphDestroy(graph);
+            graph = nullptr;
+        }
+    }
+    if (graph) {
+        size_t n = 0;
+        std::vector<cudaGraphNode_t> nodes;
+        if (cudaGraphGetNodes(graph, nullptr, &n) == cudaSuccess) {
+            nodes.resize(n);
+            if (cudaGraphGetNodes(graph, nodes.data(), &n) != cudaSuccess) nodes.clear();
+        }
+        for (cudaGraphNode_t nd : nodes) {
+            cudaGraphNodeType ty;
+            cudaKernelNodeParams kp{};
+            if (cudaGraphNodeGetType(nd, &ty) == cudaSuccess && ty == cudaGraphNodeTypeKernel &&
+                cudaGraphKernelNodeGetParams(nd, &kp) == cudaSuccess && kp.func == reinterpret_cast<void *>(adam_kernel)) {
+                tg.adam = nd;
+                tg.kp = kp;
+            }
+        }
+        if (tg.adam && cudaGraphInstantiate(&tg.exec, graph, 0) != cudaSuccess) tg.exec = nullptr;
+        if (tg.exec)
+            tg.graph = graph;
+        else
+            cudaGraphDestroy(graph);
+    }
+    cudaGetLastError();                // a refused capture leaves no error behind: the step runs eagerly
+    p->graphs.push_back(tg);
+    return &p->graphs.back();
+}
+
 asx_status check_err(asx_mlp *p)
 {
     int h = 0;
@@ -1324,6 +1416,11 @@ asx_status asx_mlp_destroy(asx_mlp *p)
     if (!p) return ASX_OK;
     cudaSetDevice(p->device);
     if (p->stream) cudaStreamSynchronize(p->stream);
+    for (auto &g : p->graphs) {
+        if (g.exec) cudaGraphExecDestroy(g.exec);
+        if (g.graph) cudaGraphDestroy(g.graph);
+    }
+    if (p->cap) cudaStreamDestroy(p->cap);
     void *ptrs[] = {p->w, p->g, p->m, p->v, p->wb, p->wt, p->x0, p->a1, p->a2, p->a3, p->dy, p->dz, p->dz2,
                     p->y, p->xin, p->tin, p->loss, p->err};
     for (void *q : ptrs) cudaFree(q);
@@ -1434,10 +1531,8 @@ asx_status asx_mlp_train_step(asx_mlp *p, int batch, const float *x, const float
     if (!(lr > 0.0f) || !(weight_decay >= 0.0f)) return mfail(p, ASX_EINVAL, "bad learning rate");
     if (kind != ASX_PTR_HOST && kind != ASX_PTR_DEVICE) return mfail(p, ASX_EINVAL, "bad ptr_kind");
     MLP_CUDA(p, cudaSetDevice(p->device));
-    asx_status st = stage_inputs(p, batch, x, t, kind);
+    asx_status st = copy_inputs(p, batch, x, t, kind);
     if (st) return st;
-    MLP_CUDA(p, forward(p, batch));
-    MLP_CUDA(p, backward(p, batch));
     p->adam_t += 1;
     const float b1 = 0.9f, b2 = 0.999f;
     const float c1 = 1.0f - (float)std::pow((double)b1, (double)p->adam_t);
@@ -1465,8 +1560,17 @@ asx_status asx_mlp_train_step(asx_mlp *p, int batch, const float *x, const float
         aa.wd[s] = l >= 0 ? weight_decay : 0.0f;
         aa.start[s + 1] = aa.start[s] + (int)n;
     }
-    adam_kernel<<<(unsigned)((aa.start[8] + 255) / 256), 256, 0, p->stream>>>(aa);
-    MLP_CUDA(p, cudaGetLastError());
+    asx_mlp::TrainGraph *tg = train_graph(p, batch, aa);
+    if (tg && tg->exec) {
+        void *args[] = {(void *)&aa};
+        cudaKernelNodeParams kp = tg->kp;
+        kp.kernelParams = args;
+        kp.extra = nullptr;
+        MLP_CUDA(p, cudaGraphExecKernelNodeSetParams(tg->exec, tg->adam, &kp));
+        MLP_CUDA(p, cudaGraphLaunch(tg->exec, p->stream));
+    } else {
+        MLP_CUDA(p, train_kernels(p, batch, aa));
+    }
     p->wt_dirty = true;
     if (loss) {
         MLP_CUDA(p, cudaMemcpyAsync(loss, p->loss, sizeof(float), cudaMemcpyDeviceToHost, p->stream));

@@ -100,9 +100,13 @@ def test_gradients_match_reference(asx, batch):
     A.asx_mlp_destroy(p)
 
 
+@pytest.mark.parametrize("batches", [[256] * 5, [64, 100, 64, 100, 64, 100, 64]], ids=["fixed", "alternating"])
 @pytest.mark.parametrize("wd", [0.0, 1e-2])
-def test_adam_step_matches_reference(asx, wd):
-    """Five Adam steps of asx_mlp_train_step, each parameter update against the oracle's
+def test_adam_step_matches_reference(asx, wd, batches):
+    """Adam steps of asx_mlp_train_step (the first step at a batch size runs its kernels
+    eagerly, the second captures them in a CUDA graph, later ones replay it with new
+    scalars; the alternating schedule keeps a graph per batch size), each parameter
+    update against the oracle's
     FP64 Adam step from the same parameters, moments and gradient (the gradient read back
     with asx_mlp_gradients, which the train step computes bit for bit the same).  FP32
     arithmetic leaves each updated parameter within a few units in its last place of the
@@ -114,9 +118,8 @@ def test_adam_step_matches_reference(asx, wd):
     After the steps the forward pass uses the refreshed BF16 copies of the new weights."""
     from paper_2406_14933_gb300 import asx as A
     rng = np.random.default_rng(17)
-    batch = 256
     theta = ref.init_params(rng).astype(np.float32)
-    p = A.asx_mlp_create(max_batch=batch)
+    p = A.asx_mlp_create(max_batch=max(batches))
     A.asx_mlp_set_params(p, theta)
     m = np.zeros(ref.N_PARAMS)
     v = np.zeros(ref.N_PARAMS)
@@ -125,7 +128,7 @@ def test_adam_step_matches_reference(asx, wd):
     wmask = ref.weight_mask()
     dmax = np.zeros(ref.N_PARAMS)       # largest rounding of g' so far, per parameter
     gmax = np.zeros(ref.N_PARAMS)       # largest |g'| so far
-    for step in range(1, 6):
+    for step, batch in enumerate(batches, 1):
         x = rng.uniform(-1, 1, (batch, 36)).astype(np.float32)
         t = rng.uniform(0, 1, (batch, 128)).astype(np.float32)
         g = np.empty(ref.N_PARAMS, np.float32)

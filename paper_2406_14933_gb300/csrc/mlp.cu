@@ -248,7 +248,7 @@ __device__ __forceinline__ void stage_operand(int mode, const unsigned char *raw
 
 // D = A B^T for one 128 x BN tile per CTA, 64 columns of K per chunk.  Thread 0 keeps the
 // TMA copies of the next two chunks in flight (landing tiles raw[c mod 2], completing on
-// full[c mod 2]); the four warps rearrange each landed chunk into the core-matrix image
+// full[c mod 2]); the eight warps rearrange each landed chunk into the core-matrix image
 // cm[c mod 2] (operands in mode 0 are read from global memory instead), and thread 0
 // issues the chunk's four tcgen05 products, which commit to done[c mod 2] and so release
 // the image two chunks later.  Every wait is bounded; after a failed wait the copies and

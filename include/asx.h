@@ -369,7 +369,10 @@ asx_status asx_mlp_forward(asx_mlp *p, int batch, const float *x, float *y, int 
 asx_status asx_mlp_gradients(asx_mlp *p, int batch, const float *x, const float *t, float *grad, float *loss,
                              int ptr_kind);
 /* One Adam step (beta 0.9 / 0.999, eps 1e-8, decoupled-free L2 weight decay on the weight
- * matrices); *loss (may be NULL) receives the batch loss before the step. */
+ * matrices); *loss (may be NULL) receives the batch loss before the step (and then the
+ * call waits for the stream).  From the second step at a batch size the step's kernels
+ * replay as a CUDA graph held by the handle (one per batch size; the same results), so
+ * x and t are copied into the handle's buffers on the stream before it runs. */
 asx_status asx_mlp_train_step(asx_mlp *p, int batch, const float *x, const float *t, float lr,
                               float weight_decay, float *loss, int ptr_kind);
 const char *asx_mlp_last_error(const asx_mlp *p);

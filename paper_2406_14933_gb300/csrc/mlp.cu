@@ -1291,12 +1291,15 @@ cudaError_t train_kernels(asx_mlp *p, int B, const AdamArgs &aa)
 }
 
 // The graph of batch size B's step (see asx_mlp::TrainGraph), or nullptr while the step
-// is to run eagerly.
+// is to run eagerly (also for every batch size after the first kMaxTrainGraphs).
+constexpr size_t kMaxTrainGraphs = 8;
 asx_mlp::TrainGraph *train_graph(asx_mlp *p, int B, const AdamArgs &aa)
 {
     for (auto &g : p->graphs)
         if (g.batch == B) return &g;
+    if (p->graphs.size() >= kMaxTrainGraphs) return nullptr;
     if (std::find(p->seen.begin(), p->seen.end(), B) == p->seen.end()) {
+        if (p->seen.size() >= 4 * kMaxTrainGraphs) return nullptr;
         p->seen.push_back(B);
         return nullptr;
     }

@@ -1305,6 +1305,7 @@ asx_mlp::TrainGraph *train_graph(asx_mlp *p, int B, const AdamArgs &aa)
     }
     asx_mlp::TrainGraph tg{B, nullptr, nullptr, nullptr, cudaKernelNodeParams{}};
     cudaGraph_t graph = nullptr;
+    bool refused = true;               // some step of the capture failed
     if (p->cap || cudaStreamCreateWithFlags(&p->cap, cudaStreamNonBlocking) == cudaSuccess) {
         const cudaStream_t user = p->stream;
         p->stream = p->cap;
@@ -1337,12 +1338,14 @@ asx_mlp::TrainGraph *train_graph(asx_mlp *p, int B, const AdamArgs &aa)
             }
         }
         if (tg.adam && cudaGraphInstantiate(&tg.exec, graph, 0) != cudaSuccess) tg.exec = nullptr;
-        if (tg.exec)
+        if (tg.exec) {
             tg.graph = graph;
-        else
+            refused = false;
+        } else {
             cudaGraphDestroy(graph);
+        }
     }
-    cudaGetLastError();                // a refused capture leaves no error behind: the step runs eagerly
+    if (refused) cudaGetLastError();   // the capture's own error is not the step's: it runs eagerly
     p->graphs.push_back(tg);
     return &p->graphs.back();
 }

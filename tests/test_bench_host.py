@@ -1,6 +1,7 @@
 """Host arithmetic of bench.py that needs no GPU: the exact rain integral the whole-storm
 record compares the applied rain with (Appendix C's triangular hyetograph, whose volume
-per unit area is i_a T_d / 2, and the catchment's double-peak storm by hand)."""
+per unit area is i_a T_d / 2, and the catchment's double-peak storm by hand), and the
+step kernel's traffic record (scaling and its lapse when the kernel's sources change)."""
 import os
 import sys
 
@@ -39,3 +40,32 @@ def test_rain_integral_outside_the_table_is_zero():
     assert bench.rain_integral([100.0, 200.0], [1.0, 1.0], 50.0) == 0.0
     assert bench.rain_integral([100.0, 200.0], [1.0, 3.0], 1e9) == pytest.approx(200.0)
 
+
+
+def test_traffic_record_scales_by_cells_and_lapses_when_a_source_changes(tmp_path, monkeypatch):
+    """The step kernel's DRAM traffic comes from a committed record of one ncu capture,
+    keyed by a hash of the kernel's sources: per cell (read + write) / cells, times the
+    cells of the timed window; null once any of those sources differs from the hashed
+    ones, or when the record is missing."""
+    import hashlib
+    for src in bench.TRAFFIC_SOURCES:
+        dst = tmp_path / src
+        dst.parent.mkdir(parents=True, exist_ok=True)
+        dst.write_bytes((src + " v1\n").encode())
+    h = hashlib.sha256()
+    for src in bench.TRAFFIC_SOURCES:
+        h.update((tmp_path / src).read_bytes())
+    (tmp_path / "profiles").mkdir()
+    (tmp_path / "profiles" / "step_strip_kernel__traffic.txt").write_text(
+        "# a record\n"
+        f"kernel_sources_sha256 {h.hexdigest()}\n"
+        "cells 1000\n"
+        "dram_bytes_read 30000\n"
+        "dram_bytes_write 8800\n")
+    monkeypatch.setattr(bench, "ROOT", str(tmp_path))
+    assert bench._read_traffic(1000) == pytest.approx(38800.0)
+    assert bench._read_traffic(16777216) == pytest.approx(38.8 * 16777216)
+    (tmp_path / bench.TRAFFIC_SOURCES[-1]).write_bytes(b"a changed header\n")
+    assert bench._read_traffic(1000) is None
+    (tmp_path / "profiles" / "step_strip_kernel__traffic.txt").unlink()
+    assert bench._read_traffic(1000) is None
